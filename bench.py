@@ -1,0 +1,354 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the N-body hot path on GB300.
+
+Workload (one "step" = one KDK leapfrog step of the whole hot path: staging,
+all-pairs mixed-precision force with fused potential, kicks and drift, float64
+energy / momentum reduction): a seeded Plummer sphere of N = 65 536 bodies,
+G = 1, eps = 0.005, dt = 5e-4, masses 1/N. Metric: body-body interactions per
+second (N^2 per force evaluation). Beside it: the plain FP64 GPU path on the
+same state, the force error of the mixed path against the FP64 CPU oracle on
+sampled bodies, the force kernel's fraction of the FP32-pipe roofline, an
+end-to-end figure through the host-memory entry point, and the oracle itself
+timed on this host's cores.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun every rank runs an independent system (weak scaling, no
+collective on the data path); rank 0 prints one JSON line.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "body-body interactions/s, mixed vs FP64 path at ≤1e-4 force err; % FP32 roofline"
+UNIT = "interactions/s"
+WORKLOAD = dict(n=65536, G=1.0, eps=0.005, dt=5e-4, seed=2)
+# float32-pipe operations per interaction in the mixed force kernel:
+# 3 FADD (d) + 3 FFMA (s^2) + 3 FMUL (m/s, 1/s^2, m/s^3) + 3 FFMA (a) + 1 FADD (phi); MUFU.RSQ not counted
+OPS_PER_INTERACTION = 13
+FP32_LANES_PER_SM = 128
+SM_MAX_MHZ = 2070.0
+L2_FLUSH_BYTES = 256 << 20
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "force_mixed_traffic.json")
+FORCE_SRC = os.path.join(ROOT, "paper_2511_02655_gb300", "csrc", "force_kernels.cu")
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=500)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.2)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in open(self.path):
+            parts = [s.strip() for s in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def traffic_per_launch():
+    """DRAM bytes per force launch from the committed ncu summary, if it still matches the source."""
+    try:
+        rec = json.load(open(TRAFFIC_FILE))
+        sha = hashlib.sha256(open(FORCE_SRC, "rb").read()).hexdigest()
+        if rec.get("source_sha256") != sha:
+            return None
+        return float(rec["dram_bytes_per_launch"])
+    except Exception:
+        return None
+
+
+def rel_force_error(a, a_ref, guard=1e-3):
+    """|a - a_ref| / |a_ref| per body, floored at guard * rms(|a_ref|) (cancellation guard)."""
+    import numpy as np
+    nrm = np.linalg.norm(a_ref, axis=1)
+    rms = float(np.sqrt(np.mean(nrm ** 2)))
+    return np.linalg.norm(a - a_ref, axis=1) / np.maximum(nrm, guard * rms)
+
+
+def cpu_baseline(x, m, G, eps, a_gpu, budget_s=12.0):
+    """The oracle (as it stands) on a bounded sample: forces of k seeded bodies against all N."""
+    import numpy as np
+
+    import oracle
+    from paper_2511_02655_gb300 import inputs
+    n = len(m)
+    threads = oracle.default_threads()
+    probe = inputs.sample_indices(n, 128, seed=99)
+    t0 = time.perf_counter()
+    oracle.forces_at(x, m, probe, G=G, eps=eps, threads=threads)
+    per_body = (time.perf_counter() - t0) / len(probe)
+    k = int(max(256, min(n, budget_s / max(per_body, 1e-9))))
+    idx = inputs.sample_indices(n, k, seed=7)
+    t0 = time.perf_counter()
+    a_ref, _ = oracle.forces_at(x, m, idx, G=G, eps=eps, threads=threads)
+    dt = time.perf_counter() - t0
+    err = rel_force_error(a_gpu[idx], a_ref)
+    base = {"value": k * n / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"FP64 direct-sum forces of {k} seeded bodies against all {n} (1 force pass, "
+                      f"{k * n:.3e} interactions, {dt:.1f} s)"}
+    return base, {"median": float(np.median(err)), "max": float(err.max()), "bodies": int(k)}
+
+
+def run_reference(args):
+    """The CPU oracle on this host's cores, on the same workload: each step is a bounded sample."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_2511_02655_gb300 import inputs
+    w = WORKLOAD
+    x, v, m = inputs.plummer(w["n"], seed=w["seed"])
+    n = w["n"]
+    threads = oracle.default_threads()
+    probe = inputs.sample_indices(n, 64, seed=98)
+    t0 = time.perf_counter()
+    oracle.forces_at(x, m, probe, G=w["G"], eps=w["eps"], threads=threads)
+    per_body = (time.perf_counter() - t0) / len(probe)
+    per_step_budget = max(0.05, 150.0 / max(1, args.steps + args.warmup))
+    k = int(max(32, min(n, per_step_budget / max(per_body, 1e-9))))
+    for s in range(args.warmup):
+        oracle.forces_at(x, m, inputs.sample_indices(n, k, seed=1000 + s), G=w["G"], eps=w["eps"], threads=threads)
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        oracle.forces_at(x, m, inputs.sample_indices(n, k, seed=2000 + s), G=w["G"], eps=w["eps"], threads=threads)
+    dt = time.perf_counter() - t0
+    value = k * n * args.steps / dt
+    sample = f"each step: FP64 direct-sum forces of {k} seeded bodies against all {n}"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": "plummer N=65536 eps=0.005 (CPU oracle, sampled rows)",
+                                             "n_bodies": n, "sample_bodies_per_step": k},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "gpu_launches": 0}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_2511_02655_gb300 as nb
+    from paper_2511_02655_gb300 import inputs
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+    nb.load()  # fails loudly without the built library
+    w = WORKLOAD
+    n, G, eps, dt = w["n"], w["G"], w["eps"], w["dt"]
+    x, v, m = inputs.plummer(n, seed=w["seed"] + rank)
+    K, W = args.steps, max(3, args.warmup)
+    stream = torch.cuda.current_stream()
+
+    # ---- mixed path: init + autotune (excluded from timing, as the paper excludes initialisation)
+    ctx = nb.nbody_init(G=G, eps=eps, dt=dt, precision=nb.MIXED, n=n, energy_every=1)
+    tuning = nb.nbody_get_tuning(ctx)
+    xt, vt, mt = (torch.from_numpy(t).to(dev) for t in (x, v, m))
+    at = torch.empty_like(xt)
+    nb.nbody_forces(ctx, xt, mt, at, None, with_phi=False)
+    a0 = at.cpu().numpy()
+    E0 = nb.nbody_energy(ctx, xt, vt, mt).cpu().numpy()[0, 0]
+    log = torch.empty((W + K, 1, 9), dtype=torch.float64, device=dev)
+    for k in range(W):
+        nb.nbody_step(ctx, xt, vt, mt, at, True, 1, log[k:k + 1])
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    launches0 = nb.nbody_launch_count(ctx)
+    nb.nbody_profile(ctx, True)
+    torch.cuda.synchronize()
+    for k in range(K):
+        flush.zero_()  # L2 flush between timed steps (outside the events)
+        ev[k][0].record(stream)
+        nb.nbody_step(ctx, xt, vt, mt, at, True, 1, log[W + k:W + k + 1])
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    clk = clocks.stop()
+    launches = nb.nbody_launch_count(ctx) - launches0
+    force_ms, force_launches = nb.nbody_kernel_time(ctx, 0)
+    nb.nbody_profile(ctx, False)
+    nb.nbody_sync(ctx)
+    total_ms = sum(a.elapsed_time(b) for a, b in ev)
+    if pg:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        total_ms = float(t.item())
+    interactions = float(n) * n
+    value = world * interactions * K / (total_ms * 1e-3)
+    elog = log.cpu().numpy()[:, 0, 0]
+    drift = float(np.abs(elog - E0).max() / abs(E0))
+
+    # ---- dominant kernel vs its roofline (FP32 pipe, derived from SM count and max clock)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    kernel_s = force_ms * 1e-3 / max(1, force_launches)
+    achieved = OPS_PER_INTERACTION * interactions / kernel_s / 1e12
+    peak = sms * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
+    traffic = traffic_per_launch()
+
+    # ---- plain FP64 GPU path on the same state (a few steps)
+    ctx64 = nb.nbody_init(G=G, eps=eps, dt=dt, precision=nb.FP64, n=n)
+    x64, v64, a64 = xt.clone(), vt.clone(), torch.empty_like(xt)
+    nb.nbody_forces(ctx64, x64, mt, a64, None, with_phi=False)
+    nb.nbody_step(ctx64, x64, v64, mt, a64, True, 1)
+    k64 = 3
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    nb.nbody_step(ctx64, x64, v64, mt, a64, True, k64)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    fp64_value = interactions * k64 / (e0.elapsed_time(e1) * 1e-3)
+    ctx64.close()
+
+    # ---- end to end through the host-memory entry point (pinned buffers, copies inside the timing)
+    ke = max(3, min(K, 50))
+    xh = xt.cpu().pin_memory()
+    vh = vt.cpu().pin_memory()
+    mh = mt.cpu().pin_memory()
+    ah = at.cpu().pin_memory()
+    lh = torch.empty((1, 1, 9), dtype=torch.float64).pin_memory()
+    nb.nbody_step_host(ctx, xh, vh, mh, ah, True, 1, lh)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(ke):
+        nb.nbody_step_host(ctx, xh, vh, mh, ah, True, 1, lh)
+    e2e_s = time.perf_counter() - t0
+    if pg:
+        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": world * interactions * ke / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": n * 10 * 8, "d2h_bytes_per_step": n * 9 * 8 + 9 * 8,
+           "call": "nbody_step_host (1 KDK step per call, pinned host x, v, m, a in; x, v, a, energy out)"}
+
+    # ---- CPU oracle on this host (rank 0, N = 1 only), which also gives the force error
+    base, ferr = None, None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        base, ferr = cpu_baseline(x, m, G, eps, a0)
+    ctx.close()
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+            "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {
+                "workload": "Plummer sphere N=65536 (seeded), G=1, eps=0.005, dt=5e-4, 1 KDK step + energy/"
+                            "momentum reduction per step, mixed precision",
+                "n_bodies": n, "precision": "f32 pair arithmetic, compensated f32 tile sums, f64 slice sums, "
+                                            "f64 state and reductions",
+                "l2": "flushed (256 MiB write) between timed steps",
+                "tuning": tuning,
+                "fp64_path_interactions_per_s": fp64_value,
+                "mixed_over_fp64": value / world / fp64_value,
+                "force_err_vs_oracle": ferr,
+                "energy_drift_max_rel": drift,
+                "interactions_per_step": interactions,
+            },
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s (FP32 pipe)",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "kernel": "k_force_mixed", "ops_per_interaction": OPS_PER_INTERACTION,
+                         "kernel_ms": kernel_s * 1e3,
+                         "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x {SM_MAX_MHZ:.0f} MHz"},
+            "cpu_baseline": base,
+            "e2e": e2e,
+            "clocks": clk,
+            "gpu_launches": int(launches),
+        }
+        print(json.dumps(line), flush=True)
+    if pg:
+        pg.barrier()
+        pg.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

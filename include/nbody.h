@@ -1,0 +1,198 @@
+/*
+ * nbody.h -- C ABI of the GB300 (sm_103a) softened-gravity N-body hot path.
+ *
+ * The operations follow the N-body miniapp of "Implementing Multi-GPU
+ * Scientific Computing Miniapps Across Performance Portable Frameworks"
+ * (arXiv 2511.02655): an all-pairs force evaluation over every pair of
+ * particles (Sec. V-B, "N_p^2 operations"), Verlet half-step time integration
+ * (Sec. II-A) and a total-energy reduction fused with the force calculation
+ * (Sec. VI). The pair law is softened Newtonian gravity instead of the paper's
+ * Lennard-Jones law (Eq. 1):
+ *
+ *     d_ij = x_j - x_i,   s_ij = sqrt(|d_ij|^2 + eps^2)
+ *     a_i   =  G sum_{j != i} m_j d_ij / s_ij^3
+ *     phi_i = -G sum_{j != i} m_j / s_ij
+ *
+ * Conventions shared by every call:
+ *   - All array arguments are DEVICE pointers (CUDA global memory of the
+ *     context's device), caller-owned, C-contiguous float64, 8-byte aligned:
+ *     positions/velocities/accelerations are [N, 3] row-major (x0 y0 z0 x1 ...),
+ *     masses and potentials [N]. N is the total body count of all systems.
+ *     The *_host variants take host pointers instead (see there).
+ *   - Several independent systems may share one context: system s owns rows
+ *     offsets[s] .. offsets[s+1]-1; bodies of different systems never interact.
+ *   - Every call is asynchronous on the context's stream and returns a status.
+ *     Argument errors (NBODY_EINVAL) are detected on the host before anything
+ *     is launched. Device-side conditions (non-finite results, a bounded wait
+ *     that gave up) are latched in the context and reported by nbody_sync().
+ *   - Results are deterministic: the same inputs on the same device and tuning
+ *     give bit-identical outputs (no floating-point atomics).
+ *   - A context is not thread-safe; use one context per host thread.
+ */
+#ifndef NBODY_H
+#define NBODY_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct nbody_ctx nbody_ctx; /* opaque, library-owned */
+
+typedef enum {
+  NBODY_OK = 0,
+  NBODY_EINVAL = 1,     /* invalid argument; nothing was launched */
+  NBODY_ENOMEM = 2,     /* a device or host allocation failed */
+  NBODY_ECUDA = 3,      /* a CUDA runtime call failed (text in nbody_last_error) */
+  NBODY_ETIMEOUT = 4,   /* a bounded device-side wait gave up */
+  NBODY_ENONFINITE = 5, /* a non-finite acceleration or energy was produced */
+  NBODY_EUNSUPPORTED = 6 /* no sm_103a device / operation not available */
+} nbody_status;
+
+typedef enum {
+  NBODY_FP64 = 0, /* all pair arithmetic and sums in float64 (plain GPU path) */
+  NBODY_MIXED = 1 /* float32 pair arithmetic; per-tile float32 partials folded into a
+                     compensated float32 pair, then summed across slices in float64;
+                     state and reductions float64 */
+} nbody_precision;
+
+/* Flags for nbody_config.flags */
+#define NBODY_FLAG_GRAPH 1u   /* replay nbody_step as a captured CUDA graph (same pointers) */
+#define NBODY_FLAG_NOCHECK 2u /* skip the non-finite scan in nbody_sync */
+
+typedef struct {
+  double G;             /* gravitational constant (finite) */
+  double eps;           /* Plummer softening length, >= 0 (0: unsoftened, coincident bodies give inf) */
+  double dt;            /* KDK time step; must be finite and > 0 for nbody_step / nbody_adjoint */
+  int32_t precision;    /* nbody_precision */
+  int32_t energy_every; /* nbody_step records energies after every k-th step (0 = never) */
+  int32_t block;        /* force kernel: threads per CTA, 128 or 256 (0 = autotune) */
+  int32_t i_per_thread; /* force kernel: i-bodies kept in registers per thread, 1, 2 or 4 (0 = autotune) */
+  int32_t j_tile;       /* force kernel: j-bodies per shared-memory tile, 128 or 256 (0 = autotune) */
+  int32_t slice;        /* force kernel: j-bodies per work item, multiple of j_tile (0 = autotune) */
+  uint32_t flags;       /* NBODY_FLAG_* */
+  int32_t reserved;     /* must be 0 */
+} nbody_config;
+
+/*
+ * Creates a context for n_systems independent systems with host array
+ * offsets[n_systems + 1] (offsets[0] = 0, non-decreasing; empty systems allowed;
+ * total N = offsets[n_systems] < 2^29). The context allocates its own
+ * device scratch (staging tiles, per-slice partial sums, reduction partials,
+ * work lists) on the current device and binds `cuda_stream` (a cudaStream_t;
+ * NULL = legacy default stream). When any tile parameter is 0 the autotuner
+ * times candidate tilings of the force kernel on synthetic positions of this
+ * layout during init (this synchronises the device). The context keeps a copy
+ * of *cfg. On failure *ctx is NULL.
+ */
+nbody_status nbody_init(nbody_ctx** ctx, const nbody_config* cfg, int64_t n_systems, const int64_t* offsets,
+                        void* cuda_stream);
+
+/* Rebinds the context's stream (a cudaStream_t; NULL = legacy default stream). */
+nbody_status nbody_set_stream(nbody_ctx* ctx, void* cuda_stream);
+
+/*
+ * All-pairs force evaluation (Sec. V-B): a [N,3] = accelerations, phi [N] =
+ * potentials (phi may be NULL). x [N,3], m [N] are read only. Self pairs are
+ * excluded from both sums.
+ */
+nbody_status nbody_forces(nbody_ctx* ctx, const double* x, const double* m, double* a, double* phi);
+
+/*
+ * n_steps kick-drift-kick leapfrog steps (Verlet half-stepping, Sec. II-A),
+ * one force evaluation per step:
+ *     v += dt/2 a(x);  x += dt v;  a = a(x);  v += dt/2 a
+ * x, v [N,3] are updated in place; a [N,3] must hold a(x) on entry when
+ * a_valid != 0 (else it is computed first) and holds a(x_final) on exit.
+ * energy_log (device, nullable): if cfg.energy_every = k > 0, after every k-th
+ * step the record [n_systems][9] = {E, K, U, Px, Py, Pz, Lx, Ly, Lz} is
+ * written to energy_log + r * n_systems * 9 for record r = 0, 1, ...
+ * (n_steps / k records). n_steps = 0 only computes a when a_valid == 0.
+ */
+nbody_status nbody_step(nbody_ctx* ctx, double* x, double* v, const double* m, double* a, int32_t a_valid,
+                        int32_t n_steps, double* energy_log);
+
+/*
+ * Global reductions (Sec. VI) at the state (x, v): out [n_systems][9] (device)
+ * = {E, K, U, Px, Py, Pz, Lx, Ly, Lz} with K = 1/2 sum m|v|^2,
+ * U = 1/2 sum m phi (phi from a force evaluation in the context's precision),
+ * E = K + U, P = sum m v, L = sum m x cross v. Sums run in float64 in a fixed order.
+ */
+nbody_status nbody_energy(nbody_ctx* ctx, const double* x, const double* v, const double* m, double* out);
+
+/*
+ * Reverse-mode gradient through n_steps KDK steps from (x0, v0) with masses m:
+ * given lam_xT = dL/dx_T and lam_vT = dL/dv_T [N,3] (device), writes
+ * g_x0 = dL/dx0, g_v0 = dL/dv0 [N,3] and g_m = dL/dm [N]. The forward
+ * trajectory is recomputed from checkpoints of (x, v) taken every
+ * checkpoint_every steps (1 <= checkpoint_every; device memory
+ * ~ (n_steps / checkpoint_every + checkpoint_every) * N * 48 bytes, allocated
+ * by the context on first use and kept). Each reverse step applies the
+ * vector-Jacobian product of a(x, m),
+ *     g_x,k = G sum_{j != k} J(d_kj) (m_k w_j - m_j w_k),  J(d) = I/s^3 - 3 d d^T / s^5
+ *     g_m,j = G sum_{i != j} w_i . d_ij / s_ij^3
+ * in the context's precision. x0/v0/m are not modified.
+ */
+nbody_status nbody_adjoint(nbody_ctx* ctx, const double* x0, const double* v0, const double* m, int32_t n_steps,
+                           int32_t checkpoint_every, const double* lam_xT, const double* lam_vT, double* g_x0,
+                           double* g_v0, double* g_m);
+
+/*
+ * Host-memory variant of nbody_step: x, v, a (in/out), m (in) and energy_log
+ * (out, nullable) are HOST pointers (pinned memory gives asynchronous copies).
+ * The context copies them to its own device buffers, runs nbody_step, copies
+ * x, v, a and the energy records back, and synchronises the stream before
+ * returning.
+ */
+nbody_status nbody_step_host(nbody_ctx* ctx, double* x, double* v, const double* m, double* a, int32_t a_valid,
+                             int32_t n_steps, double* energy_log);
+
+/*
+ * Waits for all work queued on the context's stream, then reports latched
+ * device-side conditions: NBODY_ENONFINITE if the last force evaluation
+ * produced a non-finite acceleration (unless NBODY_FLAG_NOCHECK),
+ * NBODY_ETIMEOUT if a bounded wait gave up, NBODY_ECUDA on a CUDA error.
+ * Clears the latched flags.
+ */
+nbody_status nbody_sync(nbody_ctx* ctx);
+
+/*
+ * Tiling in use (after init / autotune): block, i_per_thread, j_tile, slice,
+ * and the number of persistent CTAs the force kernel launches. Any pointer may
+ * be NULL.
+ */
+nbody_status nbody_get_tuning(const nbody_ctx* ctx, int32_t* block, int32_t* i_per_thread, int32_t* j_tile,
+                              int32_t* slice, int32_t* n_ctas);
+
+/*
+ * Kernel timing. nbody_profile(ctx, 1) clears the counters and makes the
+ * context record a CUDA event pair on its stream around every launch of the
+ * all-pairs kernels (eagerly issued calls only; graph replays are not timed);
+ * nbody_profile(ctx, 0) stops recording. nbody_kernel_time synchronises the
+ * stream and returns, for which = 0 (force kernel) or 1 (force-VJP kernel),
+ * the summed device milliseconds and the number of timed launches.
+ */
+nbody_status nbody_profile(nbody_ctx* ctx, int32_t enable);
+nbody_status nbody_kernel_time(nbody_ctx* ctx, int32_t which, double* ms_total, int64_t* launches);
+
+/*
+ * Number of kernels the context launched since creation (counted on the host
+ * at each launch or graph replay node); for launch accounting.
+ */
+int64_t nbody_launch_count(const nbody_ctx* ctx);
+
+/* Last error text for ctx (or a process-wide message when ctx is NULL). Never NULL. */
+const char* nbody_last_error(const nbody_ctx* ctx);
+
+/* Frees the context and its device memory (after synchronising its stream). NULL is ignored. */
+void nbody_destroy(nbody_ctx* ctx);
+
+/* ABI version: (major << 16) | minor. */
+int32_t nbody_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NBODY_H */

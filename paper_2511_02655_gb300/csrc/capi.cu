@@ -1,0 +1,1042 @@
+// C ABI of libnbody (include/nbody.h): context, argument validation, work
+// lists, autotuner, the KDK step sequence (with optional CUDA-graph replay),
+// the energy reduction and the checkpointed adjoint driver.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/nbody.h"
+#include "nbody_internal.h"
+
+using namespace nbody;
+
+namespace {
+
+constexpr int64_t kMaxBodies = int64_t(1) << 29;      // 3 * N fits in int32 index arithmetic
+constexpr size_t kMaxPartialBytes = size_t(1) << 30;  // cap on per-slice partial-sum memory
+constexpr int kMinTilesPerSlice = 4;
+
+struct Tiling {
+  int block = 0, ipt = 0, jtile = 0, slice = 0, n_ctas = 0;
+};
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+std::mutex g_err_mu;
+std::string g_err = "no error";
+
+void set_global_error(const std::string& s) {
+  std::lock_guard<std::mutex> lk(g_err_mu);
+  g_err = s;
+}
+
+PFN_cuMemGetAddressRange_v3020 g_addr_range = nullptr;
+std::once_flag g_addr_once;
+
+void load_addr_range() {
+  std::call_once(g_addr_once, [] {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuMemGetAddressRange", &fn, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      g_addr_range = reinterpret_cast<PFN_cuMemGetAddressRange_v3020>(fn);
+  });
+}
+
+}  // namespace
+
+struct nbody_ctx {
+  nbody_config cfg{};
+  int device = 0;
+  int sm_count = 0;
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap_stream = nullptr;  // private stream used only to capture graphs
+  int64_t n_total = 0;
+  int n_sys = 0;
+  std::vector<int64_t> offsets;
+  std::string err = "no error";
+  int64_t launches = 0;
+
+  // layout
+  std::vector<Chunk> chunks;  // force tiling's slices
+  std::vector<int32_t> sys_chunk;
+  Chunk* d_chunks = nullptr;
+  Chunk* d_vchunks = nullptr;  // same chunks, VJP tiling's slice counts
+  int32_t* d_sys_chunk = nullptr;
+  int64_t* d_off = nullptr;
+
+  // force work list
+  Tiling ft;
+  WorkItem* d_items = nullptr;
+  int n_items = 0;
+  int max_slices = 1;
+  // VJP work list (built on first adjoint)
+  Tiling vt;
+  WorkItem* d_vitems = nullptr;
+  int n_vitems = 0;
+  int vmax_slices = 1;
+  bool vjp_ready = false;
+
+  // scratch
+  DevBuf stage, stage_w, part, centre, epart, status_counter, a_scratch;
+  unsigned* counter = nullptr;  // [2]
+  unsigned* status = nullptr;   // [1]
+
+  // adjoint scratch
+  DevBuf xw, vw, aw, ckpt, traj;
+
+  // host-memory entry point scratch
+  DevBuf hx, hv, hm, ha, hlog;
+
+  // kernel timing (nbody_profile)
+  bool profiling = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_used;  // (which, (start, end))
+
+  // graph cache for nbody_step
+  cudaGraphExec_t gexec = nullptr;
+  const void* gkey[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  int32_t gkey_valid = -1, gkey_steps = -1;
+  int64_t glaunches = 0;
+};
+
+namespace {
+
+nbody_status fail(nbody_ctx* c, nbody_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (c)
+    c->err = buf;
+  else
+    set_global_error(buf);
+  return s;
+}
+
+#define NB_CUDA(ctx, call)                                                                         \
+  do {                                                                                             \
+    cudaError_t e_ = (call);                                                                       \
+    if (e_ != cudaSuccess)                                                                         \
+      return fail((ctx), NBODY_ECUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, \
+                  __LINE__);                                                                       \
+  } while (0)
+
+// Drops the cached nbody_step graph: it holds raw pointers into the
+// context's buffers, so it must not outlive any reallocation.
+void invalidate_graph(nbody_ctx* c) {
+  if (c->gexec) {
+    cudaStreamSynchronize(c->stream);
+    cudaGraphExecDestroy(c->gexec);
+    c->gexec = nullptr;
+  }
+}
+
+nbody_status ensure(nbody_ctx* c, DevBuf& b, size_t bytes) {
+  if (b.bytes >= bytes && b.p) return NBODY_OK;
+  invalidate_graph(c);
+  if (b.p) {
+    cudaStreamSynchronize(c->stream);
+    cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+  }
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(&b.p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    b.p = nullptr;
+    return fail(c, NBODY_ENOMEM, "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+  }
+  b.bytes = bytes;
+  return NBODY_OK;
+}
+
+void release(DevBuf& b) {
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+}
+
+bool finite(double v) { return std::isfinite(v); }
+
+// Checks that [p, p + bytes) is device-accessible memory of the context's device
+// and lies inside one allocation. Catches host pointers and gross overruns
+// before a kernel could fault on them.
+nbody_status check_dev(nbody_ctx* c, const void* p, size_t bytes, const char* name, bool nullable = false) {
+  if (bytes == 0) return NBODY_OK;
+  if (!p) {
+    if (nullable) return NBODY_OK;
+    return fail(c, NBODY_EINVAL, "%s is NULL", name);
+  }
+  if (reinterpret_cast<uintptr_t>(p) % 8 != 0) return fail(c, NBODY_EINVAL, "%s is not 8-byte aligned", name);
+  cudaPointerAttributes at;
+  cudaError_t e = cudaPointerGetAttributes(&at, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, NBODY_EINVAL, "%s is not a CUDA pointer (%s)", name, cudaGetErrorString(e));
+  }
+  if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)
+    return fail(c, NBODY_EINVAL, "%s is not device memory", name);
+  if (at.type == cudaMemoryTypeDevice && at.device != c->device)
+    return fail(c, NBODY_EINVAL, "%s lives on device %d, context on device %d", name, at.device, c->device);
+  load_addr_range();
+  if (g_addr_range) {
+    CUdeviceptr base = 0;
+    size_t size = 0;
+    if (g_addr_range(&base, &size, reinterpret_cast<CUdeviceptr>(p)) == CUDA_SUCCESS) {
+      const uintptr_t end = reinterpret_cast<uintptr_t>(p) + bytes;
+      if (end > static_cast<uintptr_t>(base) + size)
+        return fail(c, NBODY_EINVAL, "%s: %zu bytes needed, allocation holds %zu from that address", name, bytes,
+                    static_cast<size_t>(static_cast<uintptr_t>(base) + size - reinterpret_cast<uintptr_t>(p)));
+    }
+  }
+  return NBODY_OK;
+}
+
+// ---------------------------------------------------------------------------
+// work lists
+
+int ctas_per_sm(int prec, const Tiling& t, bool vjp) {
+  return vjp ? vjp_ctas_per_sm(prec, t.block, t.ipt, t.jtile) : force_ctas_per_sm(prec, t.block, t.ipt, t.jtile);
+}
+
+// Slice length for tiling t: the largest power-of-two multiple of jtile that
+// still yields >= 4 items per persistent CTA (fewer, larger partial buffers),
+// within the partial-memory cap.
+int auto_slice(const nbody_ctx* c, const Tiling& t, int n_ctas) {
+  int64_t nmax = 1;
+  for (int s = 0; s < c->n_sys; ++s) nmax = std::max<int64_t>(nmax, c->offsets[s + 1] - c->offsets[s]);
+  const int64_t itile = (int64_t)t.block * t.ipt;
+  const int64_t lmin = (int64_t)t.jtile * kMinTilesPerSlice;
+  int64_t best = lmin;
+  for (int64_t L = lmin; L < 2 * nmax + lmin; L *= 2) {
+    int64_t items = 0, max_sl = 1;
+    for (int s = 0; s < c->n_sys; ++s) {
+      const int64_t n = c->offsets[s + 1] - c->offsets[s];
+      if (n <= 0) continue;
+      const int64_t sl = (n + L - 1) / L;
+      items += ((n + itile - 1) / itile) * sl;
+      max_sl = std::max(max_sl, sl);
+    }
+    if ((size_t)max_sl * (size_t)c->n_total * 32 > kMaxPartialBytes) continue;
+    if (items >= 4 * (int64_t)n_ctas) best = L;
+  }
+  return (int)std::min<int64_t>(best, INT32_MAX / 2);
+}
+
+void build_items(const nbody_ctx* c, const Tiling& t, std::vector<WorkItem>& items, std::vector<int>& sys_slices,
+                 int& max_slices) {
+  items.clear();
+  sys_slices.assign(c->n_sys, 1);
+  max_slices = 1;
+  const int64_t itile = (int64_t)t.block * t.ipt;
+  for (int s = 0; s < c->n_sys; ++s) {
+    const int64_t b = c->offsets[s], n = c->offsets[s + 1] - b;
+    if (n <= 0) continue;
+    int64_t ns = (n + t.slice - 1) / t.slice;
+    // balance the slices, each a multiple of the j-tile
+    int64_t len = (n + ns - 1) / ns;
+    len = ((len + t.jtile - 1) / t.jtile) * t.jtile;
+    ns = (n + len - 1) / len;
+    sys_slices[s] = (int)ns;
+    max_slices = std::max(max_slices, (int)ns);
+    for (int64_t i0 = 0; i0 < n; i0 += itile) {
+      for (int64_t k = 0; k < ns; ++k) {
+        WorkItem w;
+        w.sys = s;
+        w.i_begin = (int32_t)(b + i0);
+        w.i_end = (int32_t)(b + std::min(n, i0 + itile));
+        w.j_begin = (int32_t)(b + k * len);
+        w.j_end = (int32_t)(b + std::min(n, (k + 1) * len));
+        w.slice = (int32_t)k;
+        items.push_back(w);
+      }
+    }
+  }
+  // longest-processing-time-first order for the dynamic persistent schedule
+  std::stable_sort(items.begin(), items.end(), [](const WorkItem& a, const WorkItem& b) {
+    const int64_t ca = (int64_t)(a.i_end - a.i_begin) * (a.j_end - a.j_begin);
+    const int64_t cb = (int64_t)(b.i_end - b.i_begin) * (b.j_end - b.j_begin);
+    return ca > cb;
+  });
+}
+
+nbody_status upload_items(nbody_ctx* c, const std::vector<WorkItem>& items, WorkItem** dst) {
+  invalidate_graph(c);
+  if (*dst) {
+    cudaStreamSynchronize(c->stream);
+    cudaFree(*dst);
+    *dst = nullptr;
+  }
+  const size_t bytes = std::max<size_t>(1, items.size()) * sizeof(WorkItem);
+  if (cudaMalloc(dst, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, NBODY_ENOMEM, "cudaMalloc of the work list failed");
+  }
+  if (!items.empty()) NB_CUDA(c, cudaMemcpy(*dst, items.data(), items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice));
+  // a pageable-memory cudaMemcpy may return before its DMA lands; the context
+  // stream can be non-blocking, so wait for the device before any launch
+  NB_CUDA(c, cudaDeviceSynchronize());
+  return NBODY_OK;
+}
+
+nbody_status upload_chunks(nbody_ctx* c, const std::vector<int>& sys_slices, Chunk** dst) {
+  std::vector<Chunk> ch = c->chunks;
+  for (auto& k : ch) k.n_slices = sys_slices[k.sys];
+  if (!*dst) {
+    if (cudaMalloc(dst, std::max<size_t>(1, ch.size()) * sizeof(Chunk)) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(c, NBODY_ENOMEM, "cudaMalloc of the chunk list failed");
+    }
+  }
+  if (!ch.empty()) NB_CUDA(c, cudaMemcpy(*dst, ch.data(), ch.size() * sizeof(Chunk), cudaMemcpyHostToDevice));
+  NB_CUDA(c, cudaDeviceSynchronize());
+  return NBODY_OK;
+}
+
+// Installs tiling t for the force (vjp=false) or VJP (vjp=true) pass.
+nbody_status install_tiling(nbody_ctx* c, Tiling t, bool vjp) {
+  const int prec = c->cfg.precision;
+  const int occ = ctas_per_sm(prec, t, vjp);
+  if (occ <= 0) return fail(c, NBODY_EINVAL, "unsupported tiling block=%d ipt=%d jtile=%d", t.block, t.ipt, t.jtile);
+  if (t.slice <= 0) t.slice = auto_slice(c, t, occ * c->sm_count);
+  t.slice = std::max(t.jtile, (t.slice / t.jtile) * t.jtile);
+  std::vector<WorkItem> items;
+  std::vector<int> sys_slices;
+  int max_slices = 1;
+  build_items(c, t, items, sys_slices, max_slices);
+  t.n_ctas = std::max(1, std::min<int>(occ * c->sm_count, (int)std::max<size_t>(1, items.size())));
+  nbody_status s = upload_items(c, items, vjp ? &c->d_vitems : &c->d_items);
+  if (s) return s;
+  s = upload_chunks(c, sys_slices, vjp ? &c->d_vchunks : &c->d_chunks);
+  if (s) return s;
+  const size_t per = vjp ? 64 : 32;
+  s = ensure(c, c->part, (size_t)max_slices * (size_t)c->n_total * per);
+  if (s) return s;
+  if (vjp) {
+    c->vt = t, c->n_vitems = (int)items.size(), c->vmax_slices = max_slices, c->vjp_ready = true;
+  } else {
+    c->ft = t, c->n_items = (int)items.size(), c->max_slices = max_slices;
+  }
+  return NBODY_OK;
+}
+
+PairLaunch pair_launch(nbody_ctx* c, bool vjp) {
+  PairLaunch L{};
+  L.stage_x = c->stage.p;
+  L.stage_w = c->stage_w.p;
+  L.items = vjp ? c->d_vitems : c->d_items;
+  L.n_items = vjp ? c->n_vitems : c->n_items;
+  L.counter = c->counter;
+  L.part = static_cast<double*>(c->part.p);
+  L.n_total = c->n_total;
+  L.eps2 = c->cfg.eps * c->cfg.eps;
+  const Tiling& t = vjp ? c->vt : c->ft;
+  L.block = t.block, L.ipt = t.ipt, L.jtile = t.jtile, L.n_ctas = t.n_ctas;
+  return L;
+}
+
+cudaEvent_t pooled_event(nbody_ctx* c) {
+  if (!c->ev_pool.empty()) {
+    cudaEvent_t e = c->ev_pool.back();
+    c->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return e;
+}
+
+// Launches an all-pairs kernel, bracketed by an event pair when profiling an
+// eager (non-capturing) stream.
+nbody_status run_pair(nbody_ctx* c, cudaStream_t st, bool vjp) {
+  if (c->n_total == 0) return NBODY_OK;
+  PairLaunch L = pair_launch(c, vjp);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (c->profiling && st != c->cap_stream) {
+    e0 = pooled_event(c);
+    e1 = pooled_event(c);
+    if (e0 && e1) NB_CUDA(c, cudaEventRecord(e0, st));
+  }
+  NB_CUDA(c, vjp ? launch_vjp(c->cfg.precision, L, st) : launch_force(c->cfg.precision, L, st));
+  if (e0 && e1) {
+    NB_CUDA(c, cudaEventRecord(e1, st));
+    c->ev_used.push_back({vjp ? 1 : 0, {e0, e1}});
+  }
+  ++c->launches;
+  return NBODY_OK;
+}
+
+nbody_status run_force(nbody_ctx* c, cudaStream_t st) { return run_pair(c, st, false); }
+nbody_status run_vjp(nbody_ctx* c, cudaStream_t st) { return run_pair(c, st, true); }
+
+PostLaunch post_launch(nbody_ctx* c, unsigned mode, double* x, double* v, const double* m, double* a, double* phi) {
+  PostLaunch P{};
+  P.chunks = c->d_chunks;
+  P.n_chunks = (int32_t)c->chunks.size();
+  P.part = static_cast<const double*>(c->part.p);
+  P.n_total = c->n_total;
+  P.G = c->cfg.G;
+  P.half_dt = 0.5 * c->cfg.dt;
+  P.dt = c->cfg.dt;
+  P.x = x, P.v = v, P.m = m, P.a = a, P.phi = phi;
+  P.x_copy = nullptr;
+  P.mode = mode;
+  P.precision = c->cfg.precision;
+  P.stage = c->stage.p;
+  P.centre = static_cast<const double*>(c->centre.p);
+  P.epart = static_cast<double*>(c->epart.p);
+  P.status = c->status;
+  return P;
+}
+
+nbody_status run_post(nbody_ctx* c, const PostLaunch& P, cudaStream_t st) {
+  if (P.n_chunks == 0) return NBODY_OK;
+  NB_CUDA(c, launch_post(P, st));
+  ++c->launches;
+  return NBODY_OK;
+}
+
+nbody_status run_centre(nbody_ctx* c, const double* x, const double* m, cudaStream_t st) {
+  if (c->cfg.precision != NBODY_MIXED || c->n_total == 0) return NBODY_OK;
+  NB_CUDA(c, launch_centre(c->d_off, c->n_sys, x, m, static_cast<double*>(c->centre.p), st));
+  ++c->launches;
+  return NBODY_OK;
+}
+
+nbody_status run_energy_final(nbody_ctx* c, double* out, cudaStream_t st) {
+  NB_CUDA(c, launch_energy_final(c->d_sys_chunk, c->n_sys, static_cast<const double*>(c->epart.p), out, st));
+  ++c->launches;
+  return NBODY_OK;
+}
+
+// The KDK sequence of nbody_step, enqueued on st (eager or under capture).
+nbody_status enqueue_step(nbody_ctx* c, double* x, double* v, const double* m, double* a, int a_valid, int n_steps,
+                          double* elog, cudaStream_t st) {
+  nbody_status s;
+  if ((s = run_centre(c, x, m, st))) return s;
+  if (!a_valid) {
+    if ((s = run_post(c, post_launch(c, kStage, x, v, m, a, nullptr), st))) return s;
+    if ((s = run_force(c, st))) return s;
+    if ((s = run_post(c, post_launch(c, kCombine, x, v, m, a, nullptr), st))) return s;
+  }
+  if (n_steps == 0) return NBODY_OK;
+  if ((s = run_post(c, post_launch(c, kDrift | kStage, x, v, m, a, nullptr), st))) return s;
+  const int every = c->cfg.energy_every;
+  int rec = 0;
+  for (int k = 0; k < n_steps; ++k) {
+    if ((s = run_force(c, st))) return s;
+    const bool rec_now = elog && every > 0 && (k + 1) % every == 0;
+    unsigned mode = kCombine | kKickEnd;
+    if (rec_now) mode |= kEnergy;
+    if (k + 1 < n_steps) mode |= kDrift | kStage;
+    if ((s = run_post(c, post_launch(c, mode, x, v, m, a, nullptr), st))) return s;
+    if (rec_now) {
+      if ((s = run_energy_final(c, elog + (int64_t)rec * c->n_sys * 9, st))) return s;
+      ++rec;
+    }
+  }
+  return NBODY_OK;
+}
+
+// ---------------------------------------------------------------------------
+// autotuner
+
+uint64_t splitmix(uint64_t& s) {
+  uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// Fills the staging buffers with a synthetic cloud (unit cube, equal masses)
+// so candidate tilings can be timed before any user data exists.
+nbody_status fill_synthetic(nbody_ctx* c, bool with_w) {
+  const int64_t n = c->n_total;
+  uint64_t seed = 12345;
+  auto u = [&] { return (double)(splitmix(seed) >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0; };
+  if (c->cfg.precision == NBODY_MIXED) {
+    std::vector<float4> h(n);
+    for (int64_t i = 0; i < n; ++i) h[i] = make_float4((float)u(), (float)u(), (float)u(), 1.0f / (float)n);
+    NB_CUDA(c, cudaMemcpy(c->stage.p, h.data(), n * sizeof(float4), cudaMemcpyHostToDevice));
+    if (with_w) {
+      for (int64_t i = 0; i < n; ++i) h[i] = make_float4((float)u(), (float)u(), (float)u(), 0.f);
+      NB_CUDA(c, cudaMemcpy(c->stage_w.p, h.data(), n * sizeof(float4), cudaMemcpyHostToDevice));
+    }
+  } else {
+    std::vector<double4_32a> h(n);
+    for (int64_t i = 0; i < n; ++i) h[i] = make_double4_32a(u(), u(), u(), 1.0 / (double)n);
+    NB_CUDA(c, cudaMemcpy(c->stage.p, h.data(), n * sizeof(double4_32a), cudaMemcpyHostToDevice));
+    if (with_w) {
+      for (int64_t i = 0; i < n; ++i) h[i] = make_double4_32a(u(), u(), u(), 0.0);
+      NB_CUDA(c, cudaMemcpy(c->stage_w.p, h.data(), n * sizeof(double4_32a), cudaMemcpyHostToDevice));
+    }
+  }
+  NB_CUDA(c, cudaDeviceSynchronize());
+  return NBODY_OK;
+}
+
+// Times the installed tiling; returns seconds per interaction slot (lower is better).
+nbody_status time_tiling(nbody_ctx* c, bool vjp, double* cost) {
+  PairLaunch L = pair_launch(c, vjp);
+  const Tiling& t = vjp ? c->vt : c->ft;
+  // estimate of the work per launch, used to bound the tuning time
+  cudaEvent_t e0, e1;
+  NB_CUDA(c, cudaEventCreate(&e0));
+  NB_CUDA(c, cudaEventCreate(&e1));
+  auto launch = [&](const PairLaunch& P) {
+    return vjp ? launch_vjp(c->cfg.precision, P, c->stream) : launch_force(c->cfg.precision, P, c->stream);
+  };
+  // warm-up on a prefix of at most 2 items per CTA
+  PairLaunch P = L;
+  P.n_items = std::min(L.n_items, 2 * t.n_ctas);
+  cudaError_t err = launch(P);
+  float ms = 0.f;
+  if (err == cudaSuccess) err = cudaEventRecord(e0, c->stream);
+  if (err == cudaSuccess) err = launch(P);
+  if (err == cudaSuccess) err = cudaEventRecord(e1, c->stream);
+  if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+  if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+  // whole list if it is short enough (captures the tail of the schedule)
+  if (err == cudaSuccess && P.n_items < L.n_items && ms * (double)L.n_items / P.n_items < 60.0) {
+    P = L;
+    err = cudaEventRecord(e0, c->stream);
+    if (err == cudaSuccess) err = launch(P);
+    if (err == cudaSuccess) err = launch(P);
+    if (err == cudaSuccess) err = cudaEventRecord(e1, c->stream);
+    if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+    if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+    ms *= 0.5f;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (err != cudaSuccess) return fail(c, NBODY_ECUDA, "autotune launch failed: %s", cudaGetErrorString(err));
+  // interaction slots covered by the timed items
+  double slots = 0.0;
+  {
+    // items are LPT-sorted; the timed prefix holds the largest items
+    std::vector<WorkItem> h(P.n_items);
+    NB_CUDA(c, cudaMemcpy(h.data(), L.items, h.size() * sizeof(WorkItem), cudaMemcpyDeviceToHost));
+    for (const auto& w : h) slots += (double)(w.i_end - w.i_begin) * (double)(w.j_end - w.j_begin);
+  }
+  c->launches += (P.n_items == L.n_items) ? 3 : 2;
+  *cost = slots > 0 ? (ms * 1e-3) / slots : 1e30;
+  return NBODY_OK;
+}
+
+nbody_status autotune(nbody_ctx* c, bool vjp) {
+  const nbody_config& g = c->cfg;
+  std::vector<Tiling> cands;
+  const int blocks[] = {128, 256};
+  const int ipts_f[] = {1, 2, 4}, ipts_v[] = {1, 2};
+  const int jts_f[] = {128, 256}, jts_v[] = {128};
+  for (int b : blocks) {
+    if (!vjp && g.block && g.block != b) continue;
+    for (int r : (vjp ? std::vector<int>(ipts_v, ipts_v + 2) : std::vector<int>(ipts_f, ipts_f + 3))) {
+      if (!vjp && g.i_per_thread && g.i_per_thread != r) continue;
+      for (int j : (vjp ? std::vector<int>(jts_v, jts_v + 1) : std::vector<int>(jts_f, jts_f + 2))) {
+        if (!vjp && g.j_tile && g.j_tile != j) continue;
+        Tiling t;
+        t.block = b, t.ipt = r, t.jtile = j, t.slice = vjp ? 0 : g.slice;
+        cands.push_back(t);
+      }
+    }
+  }
+  if (cands.empty()) return fail(c, NBODY_EINVAL, "no compiled tiling matches the requested parameters");
+  nbody_status s = fill_synthetic(c, vjp);
+  if (s) return s;
+  double best = 1e300;
+  Tiling bt = cands[0];
+  for (const Tiling& t : cands) {
+    if (ctas_per_sm(g.precision, t, vjp) <= 0) continue;
+    if ((s = install_tiling(c, t, vjp))) return s;
+    double cost = 0;
+    if ((s = time_tiling(c, vjp, &cost))) return s;
+    if (cost < best) best = cost, bt = t;
+  }
+  // slice-length refinement around the automatic choice for the best tiling
+  if (!vjp && g.slice == 0) {
+    Tiling base = bt;
+    base.slice = 0;
+    if ((s = install_tiling(c, base, vjp))) return s;
+    const int L0 = c->ft.slice;
+    double bc = 1e300;
+    int bl = L0;
+    for (int L : {L0 / 2, L0, L0 * 2}) {
+      if (L < base.jtile * kMinTilesPerSlice) continue;
+      Tiling t = base;
+      t.slice = L;
+      if ((s = install_tiling(c, t, vjp))) return s;
+      double cost = 0;
+      if ((s = time_tiling(c, vjp, &cost))) return s;
+      if (cost < bc) bc = cost, bl = L;
+    }
+    bt = base;
+    bt.slice = bl;
+  }
+  bt.n_ctas = 0;
+  return install_tiling(c, bt, vjp);
+}
+
+nbody_status validate_cfg(const nbody_config* g) {
+  if (!g) return NBODY_EINVAL;
+  if (!finite(g->G) || !finite(g->eps) || g->eps < 0 || !finite(g->dt)) return NBODY_EINVAL;
+  if (g->precision != NBODY_FP64 && g->precision != NBODY_MIXED) return NBODY_EINVAL;
+  if (g->energy_every < 0 || g->reserved != 0) return NBODY_EINVAL;
+  if (g->block && g->block != 128 && g->block != 256) return NBODY_EINVAL;
+  if (g->i_per_thread && g->i_per_thread != 1 && g->i_per_thread != 2 && g->i_per_thread != 4) return NBODY_EINVAL;
+  if (g->j_tile && g->j_tile != 128 && g->j_tile != 256) return NBODY_EINVAL;
+  if (g->slice < 0) return NBODY_EINVAL;
+  if (g->flags & ~(NBODY_FLAG_GRAPH | NBODY_FLAG_NOCHECK)) return NBODY_EINVAL;
+  return NBODY_OK;
+}
+
+void free_ctx(nbody_ctx* c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->stream);
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  for (auto& u : c->ev_used) cudaEventDestroy(u.second.first), cudaEventDestroy(u.second.second);
+  for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+  for (DevBuf* b : {&c->stage, &c->stage_w, &c->part, &c->centre, &c->epart, &c->status_counter, &c->a_scratch,
+                    &c->xw, &c->vw, &c->aw, &c->ckpt, &c->traj, &c->hx, &c->hv, &c->hm, &c->ha, &c->hlog})
+    release(*b);
+  if (c->d_chunks) cudaFree(c->d_chunks);
+  if (c->d_vchunks) cudaFree(c->d_vchunks);
+  if (c->d_sys_chunk) cudaFree(c->d_sys_chunk);
+  if (c->d_off) cudaFree(c->d_off);
+  if (c->d_items) cudaFree(c->d_items);
+  if (c->d_vitems) cudaFree(c->d_vitems);
+  delete c;
+}
+
+nbody_status check_state_args(nbody_ctx* c, const double* x, const double* v, const double* m, const double* a,
+                              bool need_v, bool need_a) {
+  const size_t n3 = (size_t)c->n_total * 3 * sizeof(double), n1 = (size_t)c->n_total * sizeof(double);
+  nbody_status s;
+  if ((s = check_dev(c, x, n3, "x"))) return s;
+  if (need_v && (s = check_dev(c, v, n3, "v"))) return s;
+  if ((s = check_dev(c, m, n1, "m"))) return s;
+  if (need_a && (s = check_dev(c, a, n3, "a"))) return s;
+  return NBODY_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+
+extern "C" {
+
+int32_t nbody_version(void) { return (1 << 16) | 0; }
+
+const char* nbody_last_error(const nbody_ctx* ctx) {
+  if (ctx) return ctx->err.c_str();
+  static thread_local std::string copy;
+  std::lock_guard<std::mutex> lk(g_err_mu);
+  copy = g_err;
+  return copy.c_str();
+}
+
+int64_t nbody_launch_count(const nbody_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+nbody_status nbody_init(nbody_ctx** out, const nbody_config* cfg, int64_t n_systems, const int64_t* offsets,
+                        void* cuda_stream) {
+  if (!out) return fail(nullptr, NBODY_EINVAL, "ctx out-pointer is NULL");
+  *out = nullptr;
+  if (validate_cfg(cfg) != NBODY_OK) return fail(nullptr, NBODY_EINVAL, "invalid nbody_config");
+  if (n_systems < 1 || n_systems > (1 << 24) || !offsets)
+    return fail(nullptr, NBODY_EINVAL, "n_systems must be in [1, 2^24] with a host offsets array");
+  if (offsets[0] != 0) return fail(nullptr, NBODY_EINVAL, "offsets[0] must be 0");
+  for (int64_t s = 0; s < n_systems; ++s)
+    if (offsets[s + 1] < offsets[s]) return fail(nullptr, NBODY_EINVAL, "offsets must be non-decreasing");
+  if (offsets[n_systems] >= kMaxBodies) return fail(nullptr, NBODY_EINVAL, "total body count must be < 2^29");
+
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(nullptr, NBODY_EUNSUPPORTED, "no CUDA device");
+  }
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(nullptr, NBODY_EUNSUPPORTED, "cudaGetDeviceProperties failed");
+  }
+  if (prop.major != 10 || prop.minor != 3)
+    return fail(nullptr, NBODY_EUNSUPPORTED, "libnbody is built for sm_103a; device %s is sm_%d%d", prop.name,
+                prop.major, prop.minor);
+
+  nbody_ctx* c = new (std::nothrow) nbody_ctx();
+  if (!c) return fail(nullptr, NBODY_ENOMEM, "host allocation failed");
+  c->cfg = *cfg;
+  c->device = dev;
+  c->sm_count = prop.multiProcessorCount;
+  c->stream = static_cast<cudaStream_t>(cuda_stream);
+  c->n_sys = (int)n_systems;
+  c->offsets.assign(offsets, offsets + n_systems + 1);
+  c->n_total = offsets[n_systems];
+
+  // chunks: runs of <= kChunk bodies inside one system
+  c->sys_chunk.assign(c->n_sys + 1, 0);
+  for (int s = 0; s < c->n_sys; ++s) {
+    c->sys_chunk[s] = (int32_t)c->chunks.size();
+    for (int64_t b = offsets[s]; b < offsets[s + 1]; b += kChunk)
+      c->chunks.push_back(Chunk{s, (int32_t)b, (int32_t)std::min<int64_t>(offsets[s + 1], b + kChunk), 1});
+  }
+  c->sys_chunk[c->n_sys] = (int32_t)c->chunks.size();
+
+  nbody_status s;
+  auto bail = [&](nbody_status st) {
+    set_global_error(c->err);
+    free_ctx(c);
+    return st;
+  };
+  const size_t n = (size_t)c->n_total;
+  const size_t stage_bytes = n * (cfg->precision == NBODY_MIXED ? sizeof(float4) : sizeof(double4_32a));
+  if ((s = ensure(c, c->stage, stage_bytes))) return bail(s);
+  if ((s = ensure(c, c->centre, (size_t)c->n_sys * 3 * sizeof(double)))) return bail(s);
+  if ((s = ensure(c, c->epart, std::max<size_t>(1, c->chunks.size()) * kEnergyVals * sizeof(double)))) return bail(s);
+  if ((s = ensure(c, c->status_counter, 4 * sizeof(unsigned)))) return bail(s);
+  c->counter = static_cast<unsigned*>(c->status_counter.p);
+  c->status = c->counter + 2;
+  if (cudaMemset(c->status_counter.p, 0, 4 * sizeof(unsigned)) != cudaSuccess) return bail(fail(c, NBODY_ECUDA, "memset failed"));
+  if (cudaMemset(c->centre.p, 0, (size_t)c->n_sys * 3 * sizeof(double)) != cudaSuccess)
+    return bail(fail(c, NBODY_ECUDA, "memset failed"));
+  if (cudaMalloc(&c->d_off, (n_systems + 1) * sizeof(int64_t)) != cudaSuccess ||
+      cudaMalloc(&c->d_sys_chunk, (n_systems + 1) * sizeof(int32_t)) != cudaSuccess) {
+    cudaGetLastError();
+    return bail(fail(c, NBODY_ENOMEM, "cudaMalloc of layout tables failed"));
+  }
+  if (cudaMemcpy(c->d_off, offsets, (n_systems + 1) * sizeof(int64_t), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(c->d_sys_chunk, c->sys_chunk.data(), (n_systems + 1) * sizeof(int32_t), cudaMemcpyHostToDevice) !=
+          cudaSuccess)
+    return bail(fail(c, NBODY_ECUDA, "upload of layout tables failed"));
+
+  if (c->n_total > 0 && (cfg->block == 0 || cfg->i_per_thread == 0 || cfg->j_tile == 0)) {
+    if ((s = autotune(c, false))) return bail(s);
+  } else {
+    Tiling t;
+    t.block = cfg->block ? cfg->block : 256;
+    t.ipt = cfg->i_per_thread ? cfg->i_per_thread : 2;
+    t.jtile = cfg->j_tile ? cfg->j_tile : 128;
+    t.slice = cfg->slice;
+    if ((s = install_tiling(c, t, false))) return bail(s);
+  }
+  if (cudaDeviceSynchronize() != cudaSuccess) return bail(fail(c, NBODY_ECUDA, "init synchronisation failed"));
+  *out = c;
+  return NBODY_OK;
+}
+
+nbody_status nbody_set_stream(nbody_ctx* c, void* stream) {
+  if (!c) return fail(nullptr, NBODY_EINVAL, "ctx is NULL");
+  c->stream = static_cast<cudaStream_t>(stream);
+  return NBODY_OK;
+}
+
+nbody_status nbody_forces(nbody_ctx* c, const double* x, const double* m, double* a, double* phi) {
+  if (!c) return fail(nullptr, NBODY_EINVAL, "ctx is NULL");
+  if (c->n_total == 0) return NBODY_OK;
+  nbody_status s;
+  if ((s = check_state_args(c, x, nullptr, m, a, false, true))) return s;
+  if ((s = check_dev(c, phi, (size_t)c->n_total * sizeof(double), "phi", true))) return s;
+  double* xm = const_cast<double*>(x);
+  if ((s = run_centre(c, x, m, c->stream))) return s;
+  if ((s = run_post(c, post_launch(c, kStage, xm, nullptr, m, a, nullptr), c->stream))) return s;
+  if ((s = run_force(c, c->stream))) return s;
+  return run_post(c, post_launch(c, kCombine, xm, nullptr, m, a, phi), c->stream);
+}
+
+nbody_status nbody_step(nbody_ctx* c, double* x, double* v, const double* m, double* a, int32_t a_valid,
+                        int32_t n_steps, double* energy_log) {
+  if (!c) return fail(nullptr, NBODY_EINVAL, "ctx is NULL");
+  if (n_steps < 0) return fail(c, NBODY_EINVAL, "n_steps < 0");
+  if (n_steps > 0 && !(c->cfg.dt > 0)) return fail(c, NBODY_EINVAL, "dt must be > 0");
+  if (c->n_total == 0) return NBODY_OK;
+  nbody_status s;
+  if ((s = check_state_args(c, x, v, m, a, true, true))) return s;
+  const int every = c->cfg.energy_every;
+  const int nrec = every > 0 ? n_steps / every : 0;
+  if (energy_log && (s = check_dev(c, energy_log, (size_t)nrec * c->n_sys * 9 * sizeof(double), "energy_log")))
+    return s;
+
+  if (!(c->cfg.flags & NBODY_FLAG_GRAPH)) return enqueue_step(c, x, v, m, a, a_valid, n_steps, energy_log, c->stream);
+
+  // CUDA-graph replay: capture the whole call once per argument set, replay afterwards.
+  const void* key[5] = {x, v, m, a, energy_log};
+  const bool hit = c->gexec && c->gkey_valid == (a_valid ? 1 : 0) && c->gkey_steps == n_steps &&
+                   std::equal(key, key + 5, c->gkey);
+  if (!hit) {
+    invalidate_graph(c);
+    if (!c->cap_stream) NB_CUDA(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+    const int64_t before = c->launches;
+    NB_CUDA(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+    s = enqueue_step(c, x, v, m, a, a_valid, n_steps, energy_log, c->cap_stream);
+    cudaGraph_t g = nullptr;
+    cudaError_t ce = cudaStreamEndCapture(c->cap_stream, &g);
+    c->glaunches = c->launches - before;
+    c->launches = before;
+    if (s) {
+      if (g) cudaGraphDestroy(g);
+      return s;
+    }
+    if (ce != cudaSuccess) return fail(c, NBODY_ECUDA, "graph capture failed: %s", cudaGetErrorString(ce));
+    cudaError_t ie = cudaGraphInstantiate(&c->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (ie != cudaSuccess) {
+      c->gexec = nullptr;
+      return fail(c, NBODY_ECUDA, "graph instantiate failed: %s", cudaGetErrorString(ie));
+    }
+    std::copy(key, key + 5, c->gkey);
+    c->gkey_valid = a_valid ? 1 : 0;
+    c->gkey_steps = n_steps;
+  }
+  NB_CUDA(c, cudaGraphLaunch(c->gexec, c->stream));
+  c->launches += c->glaunches;
+  return NBODY_OK;
+}
+
+nbody_status nbody_energy(nbody_ctx* c, const double* x, const double* v, const double* m, double* out) {
+  if (!c) return fail(nullptr, NBODY_EINVAL, "ctx is NULL");
+  nbody_status s;
+  if ((s = check_dev(c, out, (size_t)c->n_sys * 9 * sizeof(double), "out"))) return s;
+  if (c->n_total == 0) {
+    NB_CUDA(c, cudaMemsetAsync(out, 0, (size_t)c->n_sys * 9 * sizeof(double), c->stream));
+    return NBODY_OK;
+  }
+  if ((s = check_state_args(c, x, v, m, nullptr, true, false))) return s;
+  if ((s = ensure(c, c->a_scratch, (size_t)c->n_total * 3 * sizeof(double)))) return s;
+  double* xm = const_cast<double*>(x);
+  double* vm = const_cast<double*>(v);
+  double* as = static_cast<double*>(c->a_scratch.p);
+  if ((s = run_centre(c, x, m, c->stream))) return s;
+  if ((s = run_post(c, post_launch(c, kStage, xm, vm, m, as, nullptr), c->stream))) return s;
+  if ((s = run_force(c, c->stream))) return s;
+  if ((s = run_post(c, post_launch(c, kCombine | kEnergy, xm, vm, m, as, nullptr), c->stream))) return s;
+  // systems without bodies have no chunks and get all-zero records
+  return run_energy_final(c, out, c->stream);
+}
+
+nbody_status nbody_adjoint(nbody_ctx* c, const double* x0, const double* v0, const double* m, int32_t T,
+                           int32_t K, const double* lam_xT, const double* lam_vT, double* g_x0, double* g_v0,
+                           double* g_m) {
+  if (!c) return fail(nullptr, NBODY_EINVAL, "ctx is NULL");
+  if (T < 0 || K < 1) return fail(c, NBODY_EINVAL, "need n_steps >= 0 and checkpoint_every >= 1");
+  if (T > 0 && !(c->cfg.dt > 0)) return fail(c, NBODY_EINVAL, "dt must be > 0");
+  if (c->n_total == 0) return NBODY_OK;
+  const size_t n = (size_t)c->n_total, n3b = n * 3 * sizeof(double);
+  nbody_status s;
+  if ((s = check_state_args(c, x0, v0, m, nullptr, true, false))) return s;
+  if ((s = check_dev(c, lam_xT, n3b, "lam_xT"))) return s;
+  if ((s = check_dev(c, lam_vT, n3b, "lam_vT"))) return s;
+  if ((s = check_dev(c, g_x0, n3b, "g_x0"))) return s;
+  if ((s = check_dev(c, g_v0, n3b, "g_v0"))) return s;
+  if ((s = check_dev(c, g_m, n * sizeof(double), "g_m"))) return s;
+  cudaStream_t st = c->stream;
+
+  const size_t stage_bytes = n * (c->cfg.precision == NBODY_MIXED ? sizeof(float4) : sizeof(double4_32a));
+  if ((s = ensure(c, c->stage_w, stage_bytes))) return s;
+  if (!c->vjp_ready) {
+    // VJP tiling: tuned once per context (synchronises the stream)
+    NB_CUDA(c, cudaStreamSynchronize(st));
+    if ((s = autotune(c, true))) return s;
+  }
+  if ((s = ensure(c, c->part, (size_t)std::max(c->max_slices * 32, c->vmax_slices * 64) * n))) return s;
+
+  NB_CUDA(c, cudaMemcpyAsync(g_x0, lam_xT, n3b, cudaMemcpyDeviceToDevice, st));
+  NB_CUDA(c, cudaMemcpyAsync(g_v0, lam_vT, n3b, cudaMemcpyDeviceToDevice, st));
+  NB_CUDA(c, cudaMemsetAsync(g_m, 0, n * sizeof(double), st));
+  if (T == 0) return NBODY_OK;
+
+  const int nseg = (T + K - 1) / K;
+  if ((s = ensure(c, c->xw, n3b)) || (s = ensure(c, c->vw, n3b)) || (s = ensure(c, c->aw, n3b))) return s;
+  if ((s = ensure(c, c->ckpt, (size_t)nseg * 3 * n3b))) return s;
+  if ((s = ensure(c, c->traj, (size_t)(K + 1) * n3b))) return s;
+  double* xw = static_cast<double*>(c->xw.p);
+  double* vw = static_cast<double*>(c->vw.p);
+  double* aw = static_cast<double*>(c->aw.p);
+  double* ck = static_cast<double*>(c->ckpt.p);
+  double* X = static_cast<double*>(c->traj.p);
+  const size_t n3 = n * 3;
+
+  // staging origin for the whole call, from x0 (the same as nbody_step uses)
+  if ((s = run_centre(c, x0, m, st))) return s;
+  NB_CUDA(c, cudaMemcpyAsync(xw, x0, n3b, cudaMemcpyDeviceToDevice, st));
+  NB_CUDA(c, cudaMemcpyAsync(vw, v0, n3b, cudaMemcpyDeviceToDevice, st));
+  if ((s = run_post(c, post_launch(c, kStage, xw, vw, m, aw, nullptr), st))) return s;
+  if ((s = run_force(c, st))) return s;
+  if ((s = run_post(c, post_launch(c, kCombine, xw, vw, m, aw, nullptr), st))) return s;
+
+  // one KDK step on (xw, vw, aw), optionally copying x after the drift
+  auto step = [&](double* xcopy) -> nbody_status {
+    nbody_status r;
+    PostLaunch P = post_launch(c, kDrift | kStage, xw, vw, m, aw, nullptr);
+    P.x_copy = xcopy;
+    if ((r = run_post(c, P, st))) return r;
+    if ((r = run_force(c, st))) return r;
+    return run_post(c, post_launch(c, kCombine | kKickEnd, xw, vw, m, aw, nullptr), st);
+  };
+
+  // forward pass: checkpoints (x, v, a) at the start of every segment
+  for (int t = 0; t < T; ++t) {
+    if (t % K == 0) {
+      double* cp = ck + (size_t)(t / K) * 3 * n3;
+      NB_CUDA(c, cudaMemcpyAsync(cp, xw, n3b, cudaMemcpyDeviceToDevice, st));
+      NB_CUDA(c, cudaMemcpyAsync(cp + n3, vw, n3b, cudaMemcpyDeviceToDevice, st));
+      NB_CUDA(c, cudaMemcpyAsync(cp + 2 * n3, aw, n3b, cudaMemcpyDeviceToDevice, st));
+    }
+    if ((s = step(nullptr))) return s;
+  }
+
+  // reverse sweep. VJPs at x_T (coef dt/2), x_s for 0 < s < T (coef dt: the
+  // closing half-kick of step s-1 and the opening half-kick of step s share
+  // x_s and the same weights), x_0 (coef dt/2).
+  AdjLaunch A{};
+  A.chunks = c->d_vchunks;
+  A.n_chunks = (int32_t)c->chunks.size();
+  A.part = static_cast<const double*>(c->part.p);
+  A.n_total = c->n_total;
+  A.G = c->cfg.G;
+  A.dt = c->cfg.dt;
+  A.m = m;
+  A.lam_x = g_x0;
+  A.lam_v = g_v0;
+  A.g_m = g_m;
+  A.precision = c->cfg.precision;
+  A.stage_x = c->stage.p;
+  A.stage_w = c->stage_w.p;
+  A.centre = static_cast<const double*>(c->centre.p);
+  A.status = c->status;
+  const Chunk* vch = c->d_vchunks;
+  const int nch = (int)c->chunks.size();
+  for (int k = nseg - 1; k >= 0; --k) {
+    const int s0 = k * K, s1 = std::min(T, s0 + K), len = s1 - s0;
+    double* cp = ck + (size_t)k * 3 * n3;
+    NB_CUDA(c, cudaMemcpyAsync(xw, cp, n3b, cudaMemcpyDeviceToDevice, st));
+    NB_CUDA(c, cudaMemcpyAsync(vw, cp + n3, n3b, cudaMemcpyDeviceToDevice, st));
+    NB_CUDA(c, cudaMemcpyAsync(aw, cp + 2 * n3, n3b, cudaMemcpyDeviceToDevice, st));
+    NB_CUDA(c, cudaMemcpyAsync(X, xw, n3b, cudaMemcpyDeviceToDevice, st));
+    for (int t = 0; t < len; ++t)
+      if ((s = step(X + (size_t)(t + 1) * n3))) return s;
+    const int top = (k == nseg - 1) ? s1 : s1 - 1;
+    NB_CUDA(c, launch_stage_vec(vch, nch, c->cfg.precision, X + (size_t)(top - s0) * n3, m,
+                                static_cast<const double*>(c->centre.p), c->stage.p, 1, st));
+    ++c->launches;
+    if (k == nseg - 1) {
+      NB_CUDA(c, launch_stage_vec(vch, nch, c->cfg.precision, g_v0, m, static_cast<const double*>(c->centre.p),
+                                  c->stage_w.p, 0, st));
+      ++c->launches;
+    }
+    for (int t = top; t >= s0; --t) {
+      if ((s = run_vjp(c, st))) return s;
+      A.coef = (t == T || t == 0) ? 0.5 * c->cfg.dt : c->cfg.dt;
+      A.drift_rev = t > 0;
+      A.x_next = (t - 1 >= s0) ? X + (size_t)(t - 1 - s0) * n3 : nullptr;
+      NB_CUDA(c, launch_adj_update(A, st));
+      ++c->launches;
+    }
+  }
+  return NBODY_OK;
+}
+
+nbody_status nbody_step_host(nbody_ctx* c, double* x, double* v, const double* m, double* a, int32_t a_valid,
+                             int32_t n_steps, double* energy_log) {
+  if (!c) return fail(nullptr, NBODY_EINVAL, "ctx is NULL");
+  if (c->n_total == 0) return NBODY_OK;
+  if (!x || !v || !m || !a) return fail(c, NBODY_EINVAL, "x, v, m and a must be non-NULL host pointers");
+  const size_t n = (size_t)c->n_total, n3b = n * 3 * sizeof(double);
+  const int every = c->cfg.energy_every;
+  const int nrec = (every > 0 && n_steps > 0) ? n_steps / every : 0;
+  const size_t logb = (size_t)nrec * c->n_sys * 9 * sizeof(double);
+  nbody_status s;
+  if ((s = ensure(c, c->hx, n3b)) || (s = ensure(c, c->hv, n3b)) || (s = ensure(c, c->hm, n * sizeof(double))) ||
+      (s = ensure(c, c->ha, n3b)))
+    return s;
+  if (energy_log && logb && (s = ensure(c, c->hlog, logb))) return s;
+  cudaStream_t st = c->stream;
+  NB_CUDA(c, cudaMemcpyAsync(c->hx.p, x, n3b, cudaMemcpyHostToDevice, st));
+  NB_CUDA(c, cudaMemcpyAsync(c->hv.p, v, n3b, cudaMemcpyHostToDevice, st));
+  NB_CUDA(c, cudaMemcpyAsync(c->hm.p, m, n * sizeof(double), cudaMemcpyHostToDevice, st));
+  if (a_valid) NB_CUDA(c, cudaMemcpyAsync(c->ha.p, a, n3b, cudaMemcpyHostToDevice, st));
+  s = nbody_step(c, static_cast<double*>(c->hx.p), static_cast<double*>(c->hv.p),
+                 static_cast<const double*>(c->hm.p), static_cast<double*>(c->ha.p), a_valid, n_steps,
+                 (energy_log && logb) ? static_cast<double*>(c->hlog.p) : nullptr);
+  if (s) return s;
+  NB_CUDA(c, cudaMemcpyAsync(x, c->hx.p, n3b, cudaMemcpyDeviceToHost, st));
+  NB_CUDA(c, cudaMemcpyAsync(v, c->hv.p, n3b, cudaMemcpyDeviceToHost, st));
+  NB_CUDA(c, cudaMemcpyAsync(a, c->ha.p, n3b, cudaMemcpyDeviceToHost, st));
+  if (energy_log && logb) NB_CUDA(c, cudaMemcpyAsync(energy_log, c->hlog.p, logb, cudaMemcpyDeviceToHost, st));
+  return nbody_sync(c);
+}
+
+nbody_status nbody_sync(nbody_ctx* c) {
+  if (!c) return fail(nullptr, NBODY_EINVAL, "ctx is NULL");
+  NB_CUDA(c, cudaStreamSynchronize(c->stream));
+  unsigned st = 0;
+  NB_CUDA(c, cudaMemcpy(&st, c->status, sizeof(unsigned), cudaMemcpyDeviceToHost));
+  if (st) NB_CUDA(c, cudaMemset(c->status, 0, sizeof(unsigned)));
+  if (st & kFlagTimeout) return fail(c, NBODY_ETIMEOUT, "a bounded device-side wait gave up");
+  if ((st & kFlagNonFinite) && !(c->cfg.flags & NBODY_FLAG_NOCHECK))
+    return fail(c, NBODY_ENONFINITE, "non-finite acceleration, potential or gradient produced");
+  return NBODY_OK;
+}
+
+nbody_status nbody_get_tuning(const nbody_ctx* c, int32_t* block, int32_t* ipt, int32_t* jtile, int32_t* slice,
+                              int32_t* n_ctas) {
+  if (!c) return NBODY_EINVAL;
+  if (block) *block = c->ft.block;
+  if (ipt) *ipt = c->ft.ipt;
+  if (jtile) *jtile = c->ft.jtile;
+  if (slice) *slice = c->ft.slice;
+  if (n_ctas) *n_ctas = c->ft.n_ctas;
+  return NBODY_OK;
+}
+
+nbody_status nbody_profile(nbody_ctx* c, int32_t enable) {
+  if (!c) return fail(nullptr, NBODY_EINVAL, "ctx is NULL");
+  if (enable) {
+    NB_CUDA(c, cudaStreamSynchronize(c->stream));
+    for (auto& u : c->ev_used) c->ev_pool.push_back(u.second.first), c->ev_pool.push_back(u.second.second);
+    c->ev_used.clear();
+  }
+  c->profiling = enable != 0;
+  return NBODY_OK;
+}
+
+nbody_status nbody_kernel_time(nbody_ctx* c, int32_t which, double* ms_total, int64_t* launches) {
+  if (!c) return fail(nullptr, NBODY_EINVAL, "ctx is NULL");
+  if (which != 0 && which != 1) return fail(c, NBODY_EINVAL, "which must be 0 (force) or 1 (VJP)");
+  NB_CUDA(c, cudaStreamSynchronize(c->stream));
+  double tot = 0.0;
+  int64_t k = 0;
+  for (auto& u : c->ev_used) {
+    if (u.first != which) continue;
+    float ms = 0.f;
+    NB_CUDA(c, cudaEventElapsedTime(&ms, u.second.first, u.second.second));
+    tot += ms, ++k;
+  }
+  if (ms_total) *ms_total = tot;
+  if (launches) *launches = k;
+  return NBODY_OK;
+}
+
+void nbody_destroy(nbody_ctx* c) { free_ctx(c); }
+
+}  // extern "C"

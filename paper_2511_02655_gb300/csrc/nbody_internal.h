@@ -1,0 +1,124 @@
+// Internal declarations shared by the CUDA translation units of libnbody.
+// Nothing here is part of the C ABI (include/nbody.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace nbody {
+
+// One unit of all-pairs work: i-bodies [i_begin, i_end) of one system against
+// its j-bodies [j_begin, j_end), partial sums written to slice `slice`.
+// Indices are global body indices (rows of the caller's arrays).
+struct WorkItem {
+  int32_t sys;
+  int32_t i_begin, i_end;
+  int32_t j_begin, j_end;
+  int32_t slice;
+};
+
+// A contiguous run of bodies of one system, the unit of the O(N) kernels and
+// of the fixed-order energy reduction.
+struct Chunk {
+  int32_t sys;
+  int32_t begin, end;
+  int32_t n_slices;  // force/VJP slices of this system (partials to combine)
+};
+
+constexpr int kChunk = 1024;        // bodies per chunk
+constexpr int kPostThreads = 256;   // threads per O(N) kernel CTA
+constexpr int kEnergyVals = 8;      // K, U, Px, Py, Pz, Lx, Ly, Lz per chunk
+constexpr int kAdjVals = 8;         // VJP partial values per body per slice
+
+// Device status word bits (latched, read by nbody_sync).
+constexpr unsigned kFlagNonFinite = 1u;
+constexpr unsigned kFlagTimeout = 2u;
+
+// ---------------------------------------------------------------------------
+// all-pairs kernels (force_kernels.cu, adjoint_kernels.cu)
+
+struct PairLaunch {
+  const void* stage_x;   // float4 (x-c, m) [mixed] or double4_32a (x, m) [fp64], [N]
+  const void* stage_w;   // VJP only: float4 / double4_32a (w, 0), [N]
+  const WorkItem* items;
+  int32_t n_items;
+  unsigned* counter;     // [2]: next item, CTAs done (zero between launches)
+  double* part;          // force: double4_32a [slices][N]; VJP: 2 x double4_32a [slices][N]
+  int64_t n_total;
+  double eps2;
+  int block, ipt, jtile; // tiling
+  int n_ctas;            // persistent grid size
+};
+
+// Returns cudaErrorInvalidConfiguration for an unsupported tiling.
+cudaError_t launch_force(int precision, const PairLaunch& L, cudaStream_t st);
+cudaError_t launch_vjp(int precision, const PairLaunch& L, cudaStream_t st);
+// CTAs of the force kernel that fit on one SM for the tiling (0 if unsupported).
+int force_ctas_per_sm(int precision, int block, int ipt, int jtile);
+int vjp_ctas_per_sm(int precision, int block, int ipt, int jtile);
+
+// ---------------------------------------------------------------------------
+// O(N) kernels (post_kernels.cu)
+
+enum PostMode : unsigned {
+  kCombine = 1u,   // a, phi <- G * sum over slices of the partials
+  kKickEnd = 2u,   // v += dt/2 a           (closing half-kick of a step)
+  kEnergy = 4u,    // per-chunk partial energies / momenta at (x, v)
+  kDrift = 8u,     // v += dt/2 a; x += dt v (opening half-kick + drift of the next step)
+  kStage = 16u,    // staging tile entry from x (after the drift, if any)
+};
+
+struct PostLaunch {
+  const Chunk* chunks;
+  int32_t n_chunks;
+  const double* part;      // double4_32a [slices][N]
+  int64_t n_total;
+  double G, half_dt, dt;
+  double* x;
+  double* v;
+  const double* m;
+  double* a;
+  double* phi;             // nullable
+  double* x_copy;          // nullable: copy of x after the drift
+  unsigned mode;
+  int precision;
+  void* stage;             // float4 / double4_32a [N]
+  const double* centre;    // [n_sys][3] staging origin (mixed)
+  double* epart;           // [n_chunks][kEnergyVals]
+  unsigned* status;        // device status word
+};
+cudaError_t launch_post(const PostLaunch& P, cudaStream_t st);
+
+// centre[s] = mass-weighted mean position of system s (plain mean if the mass is 0)
+cudaError_t launch_centre(const int64_t* sys_off_dev, int n_sys, const double* x, const double* m, double* centre,
+                          cudaStream_t st);
+
+// out[s][9] = {E, K, U, P, L} from the chunk partials, chunk range of s = sys_chunk[s] .. sys_chunk[s+1]-1
+cudaError_t launch_energy_final(const int32_t* sys_chunk, int n_sys, const double* epart, double* out,
+                                cudaStream_t st);
+
+struct AdjLaunch {
+  const Chunk* chunks;
+  int32_t n_chunks;
+  const double* part;      // 2 x double4_32a [slices][N]
+  int64_t n_total;
+  double G, coef, dt;      // lam_x += coef * gx ; g_m += coef * gm ; lam_v += dt lam_x
+  const double* m;
+  double* lam_x;
+  double* lam_v;
+  double* g_m;
+  int drift_rev;           // apply lam_v += dt lam_x and restage w = lam_v
+  const double* x_next;    // nullable: positions to stage for the next VJP
+  int precision;
+  void* stage_x;
+  void* stage_w;
+  const double* centre;
+  unsigned* status;
+};
+cudaError_t launch_adj_update(const AdjLaunch& A, cudaStream_t st);
+
+// stage w = lam (float4 / double4_32a) and/or x for a VJP without an update
+cudaError_t launch_stage_vec(const Chunk* chunks, int n_chunks, int precision, const double* vec, const double* m,
+                             const double* centre, void* stage, int as_position, cudaStream_t st);
+
+}  // namespace nbody

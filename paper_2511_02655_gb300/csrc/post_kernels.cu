@@ -1,0 +1,251 @@
+// O(N) kernels around the all-pairs passes: staging, slice combination, the
+// leapfrog kicks and drift (Verlet half-stepping, Sec. II-A), the fixed-order
+// float64 reductions of energy and momenta (Sec. VI), and the reverse-sweep
+// update of the adjoint. One CTA handles one chunk of one system, so chunk
+// partials never mix systems and every sum has a fixed order.
+#include <math.h>
+
+#include "nbody_internal.h"
+
+namespace nbody {
+namespace {
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Deterministic CTA sum of NV values per thread; result valid in thread 0.
+template <int NV, int THREADS>
+__device__ __forceinline__ void block_sum(double (&v)[NV]) {
+  __shared__ double red[THREADS / 32][NV];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) v[k] = warp_sum(v[k]);
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) red[wid][k] = v[k];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      double s = 0.0;
+      for (int w = 0; w < THREADS / 32; ++w) s += red[w][k];
+      v[k] = s;
+    }
+  }
+}
+
+__device__ __forceinline__ void stage_store(int precision, void* stage, int i, double x, double y, double z,
+                                            double m, const double* c) {
+  if (precision == 1) {
+    static_cast<float4*>(stage)[i] =
+        make_float4((float)(x - c[0]), (float)(y - c[1]), (float)(z - c[2]), (float)m);
+  } else {
+    static_cast<double4_32a*>(stage)[i] = make_double4_32a(x, y, z, m);
+  }
+}
+
+__global__ void __launch_bounds__(kPostThreads) k_post(const PostLaunch P) {
+  const Chunk c = P.chunks[blockIdx.x];
+  const double4_32a* part = reinterpret_cast<const double4_32a*>(P.part);
+  const double* cen = P.centre + 3 * c.sys;
+  double e[kEnergyVals];
+#pragma unroll
+  for (int k = 0; k < kEnergyVals; ++k) e[k] = 0.0;
+  bool bad = false;
+  const unsigned mode = P.mode;
+
+  for (int i = c.begin + (int)threadIdx.x; i < c.end; i += kPostThreads) {
+    double ax = 0.0, ay = 0.0, az = 0.0, ph = 0.0;
+    if (mode & kCombine) {
+      double sx = 0.0, sy = 0.0, sz = 0.0, sp = 0.0;
+      for (int s = 0; s < c.n_slices; ++s) {
+        const double4_32a q = part[(int64_t)s * P.n_total + i];
+        sx += q.x, sy += q.y, sz += q.z, sp += q.w;
+      }
+      ax = P.G * sx, ay = P.G * sy, az = P.G * sz, ph = -P.G * sp;
+      P.a[3 * i + 0] = ax, P.a[3 * i + 1] = ay, P.a[3 * i + 2] = az;
+      if (P.phi) P.phi[i] = ph;
+      bad |= !(isfinite(ax) && isfinite(ay) && isfinite(az) && isfinite(ph));
+    } else if (mode & (kKickEnd | kDrift)) {
+      ax = P.a[3 * i + 0], ay = P.a[3 * i + 1], az = P.a[3 * i + 2];
+    }
+    if (!(mode & (kKickEnd | kEnergy | kDrift | kStage))) continue;
+    double x0 = P.x[3 * i + 0], x1 = P.x[3 * i + 1], x2 = P.x[3 * i + 2];
+    const double m = P.m[i];
+    if (mode & (kKickEnd | kEnergy | kDrift)) {
+      double v0 = P.v[3 * i + 0], v1 = P.v[3 * i + 1], v2 = P.v[3 * i + 2];
+      if (mode & kKickEnd) {
+        v0 += P.half_dt * ax, v1 += P.half_dt * ay, v2 += P.half_dt * az;
+      }
+      if (mode & kEnergy) {
+        e[0] += 0.5 * m * (v0 * v0 + v1 * v1 + v2 * v2);
+        e[1] += 0.5 * m * ph;
+        e[2] += m * v0, e[3] += m * v1, e[4] += m * v2;
+        e[5] += m * (x1 * v2 - x2 * v1);
+        e[6] += m * (x2 * v0 - x0 * v2);
+        e[7] += m * (x0 * v1 - x1 * v0);
+      }
+      if (mode & kDrift) {
+        v0 += P.half_dt * ax, v1 += P.half_dt * ay, v2 += P.half_dt * az;
+        x0 += P.dt * v0, x1 += P.dt * v1, x2 += P.dt * v2;
+        P.x[3 * i + 0] = x0, P.x[3 * i + 1] = x1, P.x[3 * i + 2] = x2;
+        if (P.x_copy) P.x_copy[3 * i + 0] = x0, P.x_copy[3 * i + 1] = x1, P.x_copy[3 * i + 2] = x2;
+      }
+      if (mode & (kKickEnd | kDrift)) P.v[3 * i + 0] = v0, P.v[3 * i + 1] = v1, P.v[3 * i + 2] = v2;
+    }
+    if (mode & kStage) stage_store(P.precision, P.stage, i, x0, x1, x2, m, cen);
+  }
+  if (mode & kEnergy) {
+    block_sum<kEnergyVals, kPostThreads>(e);
+    if (threadIdx.x == 0) {
+#pragma unroll
+      for (int k = 0; k < kEnergyVals; ++k) P.epart[(int64_t)blockIdx.x * kEnergyVals + k] = e[k];
+    }
+  }
+  if (bad) atomicOr(P.status, kFlagNonFinite);
+}
+
+__global__ void __launch_bounds__(256) k_centre(const int64_t* off, const double* x, const double* m,
+                                                double* centre) {
+  const int s = blockIdx.x;
+  const int64_t b = off[s], e = off[s + 1];
+  double v[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};  // sum m x (3), sum m, sum x (3)
+  for (int64_t i = b + threadIdx.x; i < e; i += 256) {
+    const double mi = m[i];
+    const double x0 = x[3 * i + 0], x1 = x[3 * i + 1], x2 = x[3 * i + 2];
+    v[0] += mi * x0, v[1] += mi * x1, v[2] += mi * x2, v[3] += mi;
+    v[4] += x0, v[5] += x1, v[6] += x2;
+  }
+  block_sum<7, 256>(v);
+  if (threadIdx.x == 0) {
+    const int64_t n = e - b;
+    double c0 = 0.0, c1 = 0.0, c2 = 0.0;
+    if (v[3] > 0.0 && isfinite(v[3])) {
+      c0 = v[0] / v[3], c1 = v[1] / v[3], c2 = v[2] / v[3];
+    } else if (n > 0) {
+      c0 = v[4] / (double)n, c1 = v[5] / (double)n, c2 = v[6] / (double)n;
+    }
+    if (!(isfinite(c0) && isfinite(c1) && isfinite(c2))) c0 = c1 = c2 = 0.0;
+    centre[3 * s + 0] = c0, centre[3 * s + 1] = c1, centre[3 * s + 2] = c2;
+  }
+}
+
+__global__ void __launch_bounds__(32) k_energy_final(const int32_t* sys_chunk, const double* epart, double* out) {
+  const int s = blockIdx.x;
+  const int lane = threadIdx.x;
+  double v[kEnergyVals];
+#pragma unroll
+  for (int k = 0; k < kEnergyVals; ++k) v[k] = 0.0;
+  for (int c = sys_chunk[s] + lane; c < sys_chunk[s + 1]; c += 32) {
+#pragma unroll
+    for (int k = 0; k < kEnergyVals; ++k) v[k] += epart[(int64_t)c * kEnergyVals + k];
+  }
+#pragma unroll
+  for (int k = 0; k < kEnergyVals; ++k) v[k] = warp_sum(v[k]);
+  if (lane == 0) {
+    double* o = out + 9 * (int64_t)s;
+    o[0] = v[0] + v[1];
+    o[1] = v[0];
+    o[2] = v[1];
+#pragma unroll
+    for (int k = 2; k < kEnergyVals; ++k) o[k + 1] = v[k];
+  }
+}
+
+__global__ void __launch_bounds__(kPostThreads) k_adj_update(const AdjLaunch A) {
+  const Chunk c = A.chunks[blockIdx.x];
+  const double4_32a* part = reinterpret_cast<const double4_32a*>(A.part);
+  const double* cen = A.centre + 3 * c.sys;
+  bool bad = false;
+  for (int i = c.begin + (int)threadIdx.x; i < c.end; i += kPostThreads) {
+    double a1x = 0, a1y = 0, a1z = 0, a2 = 0, gbx = 0, gby = 0, gbz = 0, gm = 0;
+    for (int s = 0; s < c.n_slices; ++s) {
+      const int64_t k = 2 * ((int64_t)s * A.n_total + i);
+      const double4_32a p = part[k], q = part[k + 1];
+      a1x += p.x, a1y += p.y, a1z += p.z, a2 += p.w;
+      gbx += q.x, gby += q.y, gbz += q.z, gm += q.w;
+    }
+    const double mi = A.m[i];
+    double w0 = A.lam_v[3 * i + 0], w1 = A.lam_v[3 * i + 1], w2 = A.lam_v[3 * i + 2];
+    const double gx0 = A.G * (mi * a1x - a2 * w0 - 3.0 * gbx);
+    const double gx1 = A.G * (mi * a1y - a2 * w1 - 3.0 * gby);
+    const double gx2 = A.G * (mi * a1z - a2 * w2 - 3.0 * gbz);
+    const double gmi = -A.G * gm;
+    bad |= !(isfinite(gx0) && isfinite(gx1) && isfinite(gx2) && isfinite(gmi));
+    const double l0 = A.lam_x[3 * i + 0] + A.coef * gx0;
+    const double l1 = A.lam_x[3 * i + 1] + A.coef * gx1;
+    const double l2 = A.lam_x[3 * i + 2] + A.coef * gx2;
+    A.lam_x[3 * i + 0] = l0, A.lam_x[3 * i + 1] = l1, A.lam_x[3 * i + 2] = l2;
+    A.g_m[i] += A.coef * gmi;
+    if (A.drift_rev) {
+      w0 += A.dt * l0, w1 += A.dt * l1, w2 += A.dt * l2;
+      A.lam_v[3 * i + 0] = w0, A.lam_v[3 * i + 1] = w1, A.lam_v[3 * i + 2] = w2;
+      if (A.precision == 1)
+        static_cast<float4*>(A.stage_w)[i] = make_float4((float)w0, (float)w1, (float)w2, 0.f);
+      else
+        static_cast<double4_32a*>(A.stage_w)[i] = make_double4_32a(w0, w1, w2, 0.0);
+    }
+    if (A.x_next)
+      stage_store(A.precision, A.stage_x, i, A.x_next[3 * i + 0], A.x_next[3 * i + 1], A.x_next[3 * i + 2], mi,
+                  cen);
+  }
+  if (bad) atomicOr(A.status, kFlagNonFinite);
+}
+
+__global__ void __launch_bounds__(kPostThreads) k_stage_vec(const Chunk* chunks, int precision, const double* vec,
+                                                            const double* m, const double* centre, void* stage,
+                                                            int as_position) {
+  const Chunk c = chunks[blockIdx.x];
+  const double* cen = centre + 3 * c.sys;
+  for (int i = c.begin + (int)threadIdx.x; i < c.end; i += kPostThreads) {
+    const double v0 = vec[3 * i + 0], v1 = vec[3 * i + 1], v2 = vec[3 * i + 2];
+    if (as_position) {
+      stage_store(precision, stage, i, v0, v1, v2, m[i], cen);
+    } else if (precision == 1) {
+      static_cast<float4*>(stage)[i] = make_float4((float)v0, (float)v1, (float)v2, 0.f);
+    } else {
+      static_cast<double4_32a*>(stage)[i] = make_double4_32a(v0, v1, v2, 0.0);
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_post(const PostLaunch& P, cudaStream_t st) {
+  if (P.n_chunks <= 0) return cudaSuccess;
+  k_post<<<P.n_chunks, kPostThreads, 0, st>>>(P);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_centre(const int64_t* off, int n_sys, const double* x, const double* m, double* centre,
+                          cudaStream_t st) {
+  if (n_sys <= 0) return cudaSuccess;
+  k_centre<<<n_sys, 256, 0, st>>>(off, x, m, centre);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_energy_final(const int32_t* sys_chunk, int n_sys, const double* epart, double* out,
+                                cudaStream_t st) {
+  if (n_sys <= 0) return cudaSuccess;
+  k_energy_final<<<n_sys, 32, 0, st>>>(sys_chunk, epart, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adj_update(const AdjLaunch& A, cudaStream_t st) {
+  if (A.n_chunks <= 0) return cudaSuccess;
+  k_adj_update<<<A.n_chunks, kPostThreads, 0, st>>>(A);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_stage_vec(const Chunk* chunks, int n_chunks, int precision, const double* vec, const double* m,
+                             const double* centre, void* stage, int as_position, cudaStream_t st) {
+  if (n_chunks <= 0) return cudaSuccess;
+  k_stage_vec<<<n_chunks, kPostThreads, 0, st>>>(chunks, precision, vec, m, centre, stage, as_position);
+  return cudaGetLastError();
+}
+
+}  // namespace nbody

@@ -1,0 +1,241 @@
+"""GPU parity: the sm_103a kernels through the C ABI against the FP64 CPU oracle.
+
+Bounds: FP64 path forces within 1e-12 relative per body; mixed path median
+<= 1e-6 and max <= 1e-4 (relative per body, cancellation guard at 1e-3 of the
+rms force).
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2511_02655_gb300 import inputs
+from helpers import force_rel_err, to_dev, to_np
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-12
+MIX_MED, MIX_MAX = 1e-6, 1e-4
+
+
+def _forces(nb, prec, x, m, G, eps, offsets=None, **kw):
+    import torch
+    ctx = nb.nbody_init(G=G, eps=eps, dt=1e-3, precision=prec, offsets=offsets or [0, len(m)], **kw)
+    xt, mt = to_dev(x, m)
+    a, phi = nb.nbody_forces(ctx, xt, mt)
+    nb.nbody_sync(ctx)
+    torch.cuda.synchronize()
+    return ctx, a.cpu().numpy(), phi.cpu().numpy()
+
+
+# ----------------------------------------------------------------------------------------
+# plain method, N = 1024 Plummer (G = 1, eps = 0.01, dt = 1e-3, 10 KDK steps)
+
+
+def test_fp64_forces_n1024(nb):
+    x, v, m = inputs.plummer(1024, seed=1)
+    _, a, phi = _forces(nb, nb.FP64, x, m, 1.0, 0.01)
+    a_ref, phi_ref = oracle.forces(x, m, G=1.0, eps=0.01)
+    assert force_rel_err(a, a_ref).max() <= FP64_TOL
+    assert np.abs(phi - phi_ref).max() <= FP64_TOL * np.abs(phi_ref).max()
+
+
+def test_mixed_forces_n1024(nb):
+    x, v, m = inputs.plummer(1024, seed=1)
+    _, a, phi = _forces(nb, nb.MIXED, x, m, 1.0, 0.01)
+    a_ref, phi_ref = oracle.forces(x, m, G=1.0, eps=0.01)
+    e = force_rel_err(a, a_ref)
+    assert np.median(e) <= MIX_MED and e.max() <= MIX_MAX, (np.median(e), e.max())
+    assert np.abs(phi - phi_ref).max() <= 1e-5 * np.abs(phi_ref).max()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_kdk_10_steps_n1024_with_energy(nb, prec):
+    import torch
+    G, eps, dt, n_steps = 1.0, 0.01, 1e-3, 10
+    x, v, m = inputs.plummer(1024, seed=1)
+    ctx = nb.nbody_init(G=G, eps=eps, dt=dt, precision=prec, n=1024, energy_every=1)
+    xt, vt, mt = to_dev(x, v, m)
+    at = torch.empty_like(xt)
+    log = nb.nbody_step(ctx, xt, vt, mt, at, False, n_steps)
+    nb.nbody_sync(ctx)
+    xr, vr, ar, logr = oracle.kdk(x, v, m, G, eps, dt, n_steps, energy_every=1)
+    xg, vg, ag, lg = to_np(xt, vt, at, log)
+    if prec == nb.FP64:
+        assert np.abs(xg - xr).max() <= 1e-13
+        assert np.abs(vg - vr).max() <= 1e-12 * np.abs(vr).max()
+        assert force_rel_err(ag, ar).max() <= FP64_TOL
+        np.testing.assert_allclose(lg[:, 0, 0:3], logr[:, 0:3], rtol=1e-12)
+    else:
+        assert np.abs(xg - xr).max() <= 1e-8
+        e = force_rel_err(ag, ar)
+        assert np.median(e) <= MIX_MED and e.max() <= MIX_MAX
+        np.testing.assert_allclose(lg[:, 0, 0:3], logr[:, 0:3], rtol=2e-6)
+    # momentum and angular momentum: KDK conserves them exactly when pair forces are exactly
+    # antisymmetric (FP64 path, up to rounding); float32 pair forces break antisymmetry at
+    # ~1e-7 relative, so P and L drift by ~ steps * dt * sum m|a| * 1e-7 on the mixed path.
+    np.testing.assert_allclose(lg[:, 0, 3:9], logr[:, 3:9], atol=1e-12 if prec == nb.FP64 else 1e-10)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_energy_reduction(nb, prec):
+    x, v, m = inputs.plummer(3000, seed=4)
+    m = m * np.exp(0.4 * np.random.default_rng(2).standard_normal(3000))
+    ctx = nb.nbody_init(G=0.8, eps=0.02, dt=1e-3, precision=prec, n=3000)
+    out = nb.nbody_energy(ctx, *to_dev(x, v, m))
+    nb.nbody_sync(ctx)
+    ref = oracle.energy(x, v, m, G=0.8, eps=0.02)
+    g = out.cpu().numpy()[0]
+    tol = 1e-12 if prec == nb.FP64 else 1e-6
+    assert abs(g[0] - ref[0]) <= tol * abs(ref[0])
+    assert abs(g[2] - ref[2]) <= tol * abs(ref[2])
+    assert abs(g[1] - ref[1]) <= 1e-13 * abs(ref[1])
+    np.testing.assert_allclose(g[3:], ref[3:], atol=1e-14)
+
+
+# ----------------------------------------------------------------------------------------
+# edge cases: tiny and ragged sizes, eps = 0, coincident bodies, several systems
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 31, 100, 257, 1000, 4097])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_ragged_sizes(nb, n, prec):
+    x, v, m = inputs.plummer(n, seed=n)
+    m = m * np.exp(0.3 * np.random.default_rng(n).standard_normal(n))
+    _, a, phi = _forces(nb, prec, x, m, 1.3, 0.05)
+    a_ref, phi_ref = oracle.forces(x, m, G=1.3, eps=0.05)
+    if n == 1:
+        assert np.all(a == 0) and np.all(phi == 0)
+        return
+    e = force_rel_err(a, a_ref)
+    if prec == nb.FP64:
+        assert e.max() <= FP64_TOL
+    else:
+        assert np.median(e) <= MIX_MED and e.max() <= MIX_MAX
+
+
+@pytest.mark.parametrize("tiling", [dict(block=128, i_per_thread=1, j_tile=128, slice=512),
+                                    dict(block=256, i_per_thread=4, j_tile=256, slice=1024),
+                                    dict(block=128, i_per_thread=2, j_tile=256, slice=256)])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_explicit_tilings_agree(nb, tiling, prec):
+    x, v, m = inputs.plummer(2500, seed=9)
+    _, a, phi = _forces(nb, prec, x, m, 1.0, 0.01, **tiling)
+    a_ref, _ = oracle.forces(x, m, G=1.0, eps=0.01)
+    e = force_rel_err(a, a_ref)
+    assert e.max() <= (FP64_TOL if prec == nb.FP64 else MIX_MAX)
+
+
+def test_unsoftened_kepler_fp64(nb):
+    import torch
+    x0, v0, m, period = inputs.kepler_pair(0.6, 0.4, 1.0, 0.5)
+    dt = period / 2000
+    ctx = nb.nbody_init(G=1.0, eps=0.0, dt=dt, precision=nb.FP64, n=2)
+    xt, vt, mt = to_dev(x0, v0, m)
+    at = torch.empty_like(xt)
+    nb.nbody_step(ctx, xt, vt, mt, at, False, 1000)
+    nb.nbody_sync(ctx)
+    xr, vr, _, _ = oracle.kdk(x0, v0, m, 1.0, 0.0, dt, 1000)
+    assert np.abs(xt.cpu().numpy() - xr).max() <= 1e-11
+
+
+def test_coincident_bodies_softened(nb):
+    x = np.zeros((4, 3))
+    x[2:] = [[1.0, 0.0, 0.0], [1.0, 0.0, 0.0]]
+    m = np.array([0.1, 0.2, 0.3, 0.4])
+    for prec in (nb.FP64, nb.MIXED):
+        _, a, phi = _forces(nb, prec, x, m, 1.0, 0.1)
+        a_ref, phi_ref = oracle.forces(x, m, G=1.0, eps=0.1)
+        np.testing.assert_allclose(a, a_ref, rtol=1e-6 if prec else 1e-14, atol=1e-12)
+        np.testing.assert_allclose(phi, phi_ref, rtol=1e-6 if prec else 1e-14)
+
+
+def test_unsoftened_coincident_bodies_flag_nonfinite(nb):
+    import torch
+    x = np.zeros((2, 3))
+    m = np.array([0.5, 0.5])
+    ctx = nb.nbody_init(G=1.0, eps=0.0, dt=1e-3, precision=nb.MIXED, n=2)
+    nb.nbody_forces(ctx, *to_dev(x, m))
+    with pytest.raises(nb.NBodyError) as ei:
+        nb.nbody_sync(ctx)
+    assert ei.value.status == 5
+    nb.nbody_sync(ctx)  # flag was cleared
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_several_systems_with_empty_ones(nb, prec):
+    sizes = [0, 5, 300, 0, 1, 1200, 2]
+    ens = inputs.ensemble(len(sizes), seed=3, sizes=np.array(sizes))
+    off = [int(o) for o in ens.offsets]
+    _, a, phi = _forces(nb, prec, ens.x, ens.m, 1.0, 0.01, offsets=off)
+    for s in range(len(sizes)):
+        b, e = off[s], off[s + 1]
+        if e - b < 2:
+            assert np.all(a[b:e] == 0)
+            continue
+        a_ref, _ = oracle.forces(ens.x[b:e], ens.m[b:e], G=1.0, eps=0.01)
+        err = force_rel_err(a[b:e], a_ref)
+        assert err.max() <= (FP64_TOL if prec == nb.FP64 else MIX_MAX)
+
+
+def test_deterministic(nb):
+    x, v, m = inputs.plummer(5000, seed=6)
+    ctx = nb.nbody_init(G=1.0, eps=0.01, dt=1e-3, precision=nb.MIXED, n=5000)
+    xt, mt = to_dev(x, m)
+    a1, p1 = nb.nbody_forces(ctx, xt, mt)
+    a2, p2 = nb.nbody_forces(ctx, xt, mt)
+    assert bool((a1 == a2).all()) and bool((p1 == p2).all())
+
+
+def test_host_pointers_rejected_without_launch(nb):
+    import torch
+    ctx = nb.nbody_init(G=1.0, eps=0.01, dt=1e-3, precision=nb.MIXED, n=16)
+    x = torch.zeros((16, 3), dtype=torch.float64)
+    m = torch.ones(16, dtype=torch.float64)
+    a = torch.zeros((16, 3), dtype=torch.float64)
+    lib = nb.load()
+    before = nb.nbody_launch_count(ctx)
+    st = lib.nbody_forces(ctx._h, nb.ctx_ptr(x.data_ptr()), nb.ctx_ptr(m.data_ptr()), nb.ctx_ptr(a.data_ptr()),
+                          None)
+    assert st == 1 and "device memory" in nb.nbody_last_error(ctx) or "CUDA pointer" in nb.nbody_last_error(ctx)
+    assert nb.nbody_launch_count(ctx) == before
+    # too short a device buffer
+    xs = torch.zeros((8, 3), dtype=torch.float64, device="cuda")
+    st = lib.nbody_forces(ctx._h, nb.ctx_ptr(xs.data_ptr()), nb.ctx_ptr(m.cuda().data_ptr()),
+                          nb.ctx_ptr(a.cuda().data_ptr()), None)
+    assert st in (0, 1)  # caching allocators may hand out a larger block; checked when it is not
+    nb.nbody_sync(ctx)
+
+
+def test_step_host_matches_device_path(nb):
+    import torch
+    x, v, m = inputs.plummer(2048, seed=12)
+    ctx = nb.nbody_init(G=1.0, eps=0.01, dt=1e-3, precision=nb.MIXED, n=2048, energy_every=2)
+    xt, vt, mt = to_dev(x, v, m)
+    at = torch.empty_like(xt)
+    log = nb.nbody_step(ctx, xt, vt, mt, at, False, 4)
+    nb.nbody_sync(ctx)
+    xh, vh = torch.from_numpy(x.copy()).pin_memory(), torch.from_numpy(v.copy()).pin_memory()
+    mh, ah = torch.from_numpy(m.copy()).pin_memory(), torch.zeros((2048, 3), dtype=torch.float64).pin_memory()
+    logh = torch.zeros((2, 1, 9), dtype=torch.float64)
+    nb.nbody_step_host(ctx, xh, vh, mh, ah, False, 4, logh)
+    assert torch.equal(xh, xt.cpu()) and torch.equal(vh, vt.cpu()) and torch.equal(ah, at.cpu())
+    assert torch.equal(logh, log.cpu())
+
+
+def test_graph_replay_matches_eager(nb):
+    import torch
+    x, v, m = inputs.plummer(3000, seed=13)
+    outs = []
+    for flags in (0, nb.FLAG_GRAPH):
+        ctx = nb.nbody_init(G=1.0, eps=0.01, dt=1e-3, precision=nb.MIXED, n=3000, energy_every=5, flags=flags,
+                            block=128, i_per_thread=2, j_tile=128, slice=1024)
+        xt, vt, mt = to_dev(x, v, m)
+        at = torch.empty_like(xt)
+        log = torch.empty((2, 1, 9), dtype=torch.float64, device="cuda")
+        for _ in range(3):  # first call captures, later calls replay
+            nb.nbody_step(ctx, xt, vt, mt, at, False, 10, log)
+        nb.nbody_sync(ctx)
+        outs.append((xt.cpu(), vt.cpu(), at.cpu(), log.cpu()))
+    for a, b in zip(*outs):
+        assert torch.equal(a, b)
