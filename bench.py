@@ -236,11 +236,13 @@ def run_ours(args):
     launches0 = nb.nbody_launch_count(ctx)
     nb.nbody_profile(ctx, True)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("bench_timed")  # lets ncu select the timed launches (--nvtx-include)
     for k in range(K):
         flush.zero_()  # L2 flush between timed steps (outside the events)
         ev[k][0].record(stream)
         nb.nbody_step(ctx, xt, vt, mt, at, True, 1, log[W + k:W + k + 1])
         ev[k][1].record(stream)
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     if pg:
         pg.barrier()

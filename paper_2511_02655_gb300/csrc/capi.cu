@@ -103,6 +103,7 @@ struct nbody_ctx {
 
   // kernel timing (nbody_profile)
   bool profiling = false;
+  bool capturing = false;  // enqueueing into a graph capture (no timing events then)
   std::vector<cudaEvent_t> ev_pool;
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_used;  // (which, (start, end))
 
@@ -371,7 +372,7 @@ nbody_status run_pair(nbody_ctx* c, cudaStream_t st, bool vjp) {
   if (c->n_total == 0) return NBODY_OK;
   PairLaunch L = pair_launch(c, vjp);
   cudaEvent_t e0 = nullptr, e1 = nullptr;
-  if (c->profiling && st != c->cap_stream) {
+  if (c->profiling && !c->capturing) {
     e0 = pooled_event(c);
     e1 = pooled_event(c);
     if (e0 && e1) NB_CUDA(c, cudaEventRecord(e0, st));
@@ -788,7 +789,9 @@ nbody_status nbody_step(nbody_ctx* c, double* x, double* v, const double* m, dou
     if (!c->cap_stream) NB_CUDA(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
     const int64_t before = c->launches;
     NB_CUDA(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+    c->capturing = true;
     s = enqueue_step(c, x, v, m, a, a_valid, n_steps, energy_log, c->cap_stream);
+    c->capturing = false;
     cudaGraph_t g = nullptr;
     cudaError_t ce = cudaStreamEndCapture(c->cap_stream, &g);
     c->glaunches = c->launches - before;

@@ -239,3 +239,18 @@ def test_graph_replay_matches_eager(nb):
         outs.append((xt.cpu(), vt.cpu(), at.cpu(), log.cpu()))
     for a, b in zip(*outs):
         assert torch.equal(a, b)
+
+
+def test_kernel_profiling_counts_force_launches(nb):
+    import torch
+    x, v, m = inputs.plummer(4096, seed=14)
+    ctx = nb.nbody_init(G=1.0, eps=0.01, dt=1e-3, precision=nb.MIXED, n=4096)
+    xt, vt, mt = to_dev(x, v, m)
+    at = torch.empty_like(xt)
+    nb.nbody_profile(ctx, True)
+    nb.nbody_step(ctx, xt, vt, mt, at, False, 5)
+    ms, k = nb.nbody_kernel_time(ctx, 0)
+    assert k == 6 and ms > 0
+    nb.nbody_profile(ctx, False)
+    nb.nbody_step(ctx, xt, vt, mt, at, True, 2)
+    assert nb.nbody_kernel_time(ctx, 0)[1] == 6
