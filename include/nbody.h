@@ -182,6 +182,40 @@ nbody_status nbody_kernel_time(nbody_ctx* ctx, int32_t which, double* ms_total, 
  */
 int64_t nbody_launch_count(const nbody_ctx* ctx);
 
+/*
+ * Largest body count nbody_forces_noalloc accepts. Its scratch is a fixed
+ * 16 MiB + 256 B __device__ array (16 bytes per body), reserved on every GPU
+ * that loads the library for the life of the process.
+ */
+#define NBODY_NOALLOC_MAX_BODIES 1048576
+
+/*
+ * Mixed-precision forces of ONE system without allocating anything: no
+ * context, no cudaMalloc/cudaFree, no allocating library call. For callers
+ * that cannot allocate device memory where they need forces (a fixed memory
+ * budget owned by a host framework, a plugin handed only ready-made buffers,
+ * code that must not hit the allocator or its implicit synchronisation).
+ * The paper has no counterpart; this is a deployment convenience.
+ *
+ * x [n,3], m [n] (read), a [n,3] (written), phi [n] (written, nullable) are
+ * device pointers on the current device; the work is queued on cuda_stream
+ * (NULL = legacy default stream) and is asynchronous. Same pair arithmetic as
+ * nbody_forces with NBODY_MIXED (float32 pairs, compensated float32 tile sums,
+ * float64 result), but one CTA per i-tile and no j-slices, so results agree
+ * with nbody_forces to rounding, not bit for bit.
+ *
+ * Scratch is a static __device__ array shared by every call in the process:
+ * calls that overlap on the GPU (different streams, or different host threads)
+ * race on it and must be serialised by the caller. Each call overwrites
+ * everything it reads, so no state carries over from an earlier call. The
+ * first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before
+ * any stream capture. Returns NBODY_EINVAL for n > NBODY_NOALLOC_MAX_BODIES,
+ * n < 0, bad pointers or parameters (message in nbody_last_error(NULL)).
+ */
+nbody_status nbody_forces_noalloc(const double* x, const double* m, int64_t n, double G, double eps, double* a,
+                                  double* phi, void* cuda_stream);
+
 /* Last error text for ctx (or a process-wide message when ctx is NULL). Never NULL. */
 const char* nbody_last_error(const nbody_ctx* ctx);
 

@@ -84,6 +84,7 @@ def load():
             "nbody_profile": (i32, [p, i32]),
             "nbody_kernel_time": (i32, [p, i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)]),
             "nbody_last_error": (ctypes.c_char_p, [p]),
+            "nbody_forces_noalloc": (i32, [p, p, i64, ctypes.c_double, ctypes.c_double, p, p, p]),
             "nbody_destroy": (None, [p]),
             "nbody_version": (i32, []),
         }
@@ -303,6 +304,33 @@ def nbody_kernel_time(ctx: Context, which: int = 0):
     ms, k = ctypes.c_double(), ctypes.c_int64()
     _check(load().nbody_kernel_time(ctx._h, int(which), ctypes.byref(ms), ctypes.byref(k)), ctx)
     return ms.value, k.value
+
+
+NOALLOC_MAX_BODIES = 1048576
+
+
+def nbody_forces_noalloc(x, m, G, eps, a=None, phi=None):
+    """Forces of one system through the allocation-free entry point (no context).
+
+    For callers that cannot allocate device memory at this point: the library
+    uses a fixed static device array as scratch. Output tensors are allocated
+    here by torch only when not supplied. Calls overlapping on the GPU race on
+    the shared scratch.
+    """
+    torch = _torch()
+    n = int(m.shape[0])
+    for t, name, shape in ((x, "x", (n, 3)), (m, "m", (n,))):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()
+                and tuple(t.shape) == shape):
+            raise ValueError(f"{name} must be a contiguous CUDA float64 tensor of shape {shape}")
+    if a is None:
+        a = torch.empty((n, 3), dtype=torch.float64, device=x.device)
+    stream = torch.cuda.current_stream().cuda_stream
+    st = load().nbody_forces_noalloc(ctx_ptr(x.data_ptr()), ctx_ptr(m.data_ptr()), n, float(G), float(eps),
+                                     ctx_ptr(a.data_ptr()), ctx_ptr(phi.data_ptr()) if phi is not None else None,
+                                     ctx_ptr(stream))
+    _check(st)
+    return a, phi
 
 
 def nbody_destroy(ctx: Context):

@@ -16,7 +16,7 @@ INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libnbody.so")
 BUILD_DIR = os.path.join(HERE, "_build")
 
-SOURCES = ["force_kernels.cu", "adjoint_kernels.cu", "post_kernels.cu", "capi.cu"]
+SOURCES = ["force_kernels.cu", "adjoint_kernels.cu", "post_kernels.cu", "capi.cu", "noalloc.cu"]
 HEADERS = ["nbody_internal.h", "pair_common.cuh"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -58,6 +58,11 @@ void load_addr_range() {
 
 }  // namespace
 
+namespace nbody {
+// Error text reported by nbody_last_error(NULL), for entry points without a context.
+void set_global_error_text(const char* msg) { set_global_error(msg); }
+}  // namespace nbody
+
 struct nbody_ctx {
   nbody_config cfg{};
   int device = 0;
