@@ -72,7 +72,8 @@ typedef struct {
   int32_t j_tile;       /* force kernel: j-bodies per shared-memory tile, 128 or 256 (0 = autotune) */
   int32_t slice;        /* force kernel: j-bodies per work item, multiple of j_tile (0 = autotune) */
   uint32_t flags;       /* NBODY_FLAG_* */
-  int32_t reserved;     /* must be 0 */
+  int32_t variant;      /* mixed force kernel: 1 = scalar float32, 2 = packed float32x2 (bit-identical
+                           results), 0 = autotune; must be 0 or 1 for NBODY_FP64 */
 } nbody_config;
 
 /*
@@ -95,7 +96,10 @@ nbody_status nbody_set_stream(nbody_ctx* ctx, void* cuda_stream);
 /*
  * All-pairs force evaluation (Sec. V-B): a [N,3] = accelerations, phi [N] =
  * potentials (phi may be NULL). x [N,3], m [N] are read only. Self pairs are
- * excluded from both sums.
+ * excluded from both sums. In NBODY_MIXED, pairs closer than 4 eps take their
+ * separation from x in float64 (rounded once to float32) instead of from the
+ * float32 staging copy, so that the staging rounding of |x - c| 2^-24 does not
+ * dominate close-pair forces.
  */
 nbody_status nbody_forces(nbody_ctx* ctx, const double* x, const double* m, double* a, double* phi);
 
@@ -159,11 +163,12 @@ nbody_status nbody_sync(nbody_ctx* ctx);
 
 /*
  * Tiling in use (after init / autotune): block, i_per_thread, j_tile, slice,
- * and the number of persistent CTAs the force kernel launches. Any pointer may
- * be NULL.
+ * the number of persistent CTAs the force kernel launches, and the force
+ * kernel variant (as in nbody_config.variant: 1 scalar, 2 packed). Any pointer
+ * may be NULL.
  */
 nbody_status nbody_get_tuning(const nbody_ctx* ctx, int32_t* block, int32_t* i_per_thread, int32_t* j_tile,
-                              int32_t* slice, int32_t* n_ctas);
+                              int32_t* slice, int32_t* n_ctas, int32_t* variant);
 
 /*
  * Kernel timing. nbody_profile(ctx, 1) clears the counters and makes the

@@ -52,7 +52,7 @@ class _Config(ctypes.Structure):
         ("G", ctypes.c_double), ("eps", ctypes.c_double), ("dt", ctypes.c_double),
         ("precision", ctypes.c_int32), ("energy_every", ctypes.c_int32), ("block", ctypes.c_int32),
         ("i_per_thread", ctypes.c_int32), ("j_tile", ctypes.c_int32), ("slice", ctypes.c_int32),
-        ("flags", ctypes.c_uint32), ("reserved", ctypes.c_int32),
+        ("flags", ctypes.c_uint32), ("variant", ctypes.c_int32),
     ]
 
 
@@ -79,7 +79,7 @@ def load():
             "nbody_adjoint": (i32, [p, p, p, p, i32, i32, p, p, p, p, p]),
             "nbody_step_host": (i32, [p, p, p, p, p, i32, i32, p]),
             "nbody_sync": (i32, [p]),
-            "nbody_get_tuning": (i32, [p] + [ctypes.POINTER(i32)] * 5),
+            "nbody_get_tuning": (i32, [p] + [ctypes.POINTER(i32)] * 6),
             "nbody_launch_count": (i64, [p]),
             "nbody_profile": (i32, [p, i32]),
             "nbody_kernel_time": (i32, [p, i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)]),
@@ -173,10 +173,11 @@ def _dev(t, name, shape, ctx: Context, allow_none=False):
 
 
 def nbody_init(*, G=1.0, eps=0.0, dt=0.0, precision=MIXED, offsets=None, n=None, energy_every=0, block=0,
-               i_per_thread=0, j_tile=0, slice=0, flags=0, stream=None) -> Context:
+               i_per_thread=0, j_tile=0, slice=0, flags=0, variant=0, stream=None) -> Context:
     """Creates a context for systems with row ranges ``offsets`` (or one system of ``n`` bodies).
 
-    Tile parameters left at 0 are chosen by the autotuner during init.
+    Tile parameters (and the mixed kernel ``variant``: 1 scalar, 2 packed) left at 0
+    are chosen by the autotuner during init.
     ``stream``: a torch.cuda.Stream (default: the current stream).
     """
     torch = _torch()
@@ -187,7 +188,7 @@ def nbody_init(*, G=1.0, eps=0.0, dt=0.0, precision=MIXED, offsets=None, n=None,
         offsets = [0, int(n)]
     offs = (ctypes.c_int64 * len(offsets))(*[int(o) for o in offsets])
     cfg = _Config(float(G), float(eps), float(dt), int(precision), int(energy_every), int(block),
-                  int(i_per_thread), int(j_tile), int(slice), int(flags), 0)
+                  int(i_per_thread), int(j_tile), int(slice), int(flags), int(variant))
     s = (stream or torch.cuda.current_stream()).cuda_stream
     h = ctypes.c_void_p()
     _check(lib.nbody_init(ctypes.byref(h), ctypes.byref(cfg), len(offsets) - 1, offs, ctx_ptr(s)))
@@ -285,9 +286,9 @@ def nbody_sync(ctx: Context):
 
 
 def nbody_get_tuning(ctx: Context) -> dict:
-    vals = [ctypes.c_int32() for _ in range(5)]
+    vals = [ctypes.c_int32() for _ in range(6)]
     _check(load().nbody_get_tuning(ctx._h, *[ctypes.byref(v) for v in vals]), ctx)
-    return dict(zip(("block", "i_per_thread", "j_tile", "slice", "n_ctas"), (v.value for v in vals)))
+    return dict(zip(("block", "i_per_thread", "j_tile", "slice", "n_ctas", "variant"), (v.value for v in vals)))
 
 
 def nbody_launch_count(ctx: Context) -> int:

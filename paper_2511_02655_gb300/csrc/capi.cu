@@ -27,7 +27,11 @@ constexpr int kMinTilesPerSlice = 4;
 
 struct Tiling {
   int block = 0, ipt = 0, jtile = 0, slice = 0, n_ctas = 0;
+  int variant = 0;  // force (mixed): 0 scalar, 1 packed float32x2
 };
+
+// Near-pair refinement radius of the mixed force kernel, in softening lengths.
+constexpr double kNearRadiusEps = 4.0;
 
 struct DevBuf {
   void* p = nullptr;
@@ -218,7 +222,8 @@ nbody_status check_dev(nbody_ctx* c, const void* p, size_t bytes, const char* na
 // work lists
 
 int ctas_per_sm(int prec, const Tiling& t, bool vjp) {
-  return vjp ? vjp_ctas_per_sm(prec, t.block, t.ipt, t.jtile) : force_ctas_per_sm(prec, t.block, t.ipt, t.jtile);
+  return vjp ? vjp_ctas_per_sm(prec, t.block, t.ipt, t.jtile)
+             : force_ctas_per_sm(prec, t.variant, t.block, t.ipt, t.jtile);
 }
 
 // Slice length for tiling t: the largest power-of-two multiple of jtile that
@@ -319,7 +324,9 @@ nbody_status upload_chunks(nbody_ctx* c, const std::vector<int>& sys_slices, Chu
 nbody_status install_tiling(nbody_ctx* c, Tiling t, bool vjp) {
   const int prec = c->cfg.precision;
   const int occ = ctas_per_sm(prec, t, vjp);
-  if (occ <= 0) return fail(c, NBODY_EINVAL, "unsupported tiling block=%d ipt=%d jtile=%d", t.block, t.ipt, t.jtile);
+  if (occ <= 0)
+    return fail(c, NBODY_EINVAL, "unsupported tiling block=%d ipt=%d jtile=%d variant=%d", t.block, t.ipt, t.jtile,
+                t.variant);
   if (t.slice <= 0) t.slice = auto_slice(c, t, occ * c->sm_count);
   t.slice = std::max(t.jtile, (t.slice / t.jtile) * t.jtile);
   std::vector<WorkItem> items;
@@ -342,8 +349,12 @@ nbody_status install_tiling(nbody_ctx* c, Tiling t, bool vjp) {
   return NBODY_OK;
 }
 
-PairLaunch pair_launch(nbody_ctx* c, bool vjp) {
+PairLaunch pair_launch(nbody_ctx* c, bool vjp, const double* x64 = nullptr) {
   PairLaunch L{};
+  L.x64 = x64;
+  L.r2_near = (!vjp && x64 && c->cfg.precision == NBODY_MIXED)
+                  ? (float)(kNearRadiusEps * kNearRadiusEps * c->cfg.eps * c->cfg.eps)
+                  : 0.f;
   L.stage_x = c->stage.p;
   L.stage_w = c->stage_w.p;
   L.items = vjp ? c->d_vitems : c->d_items;
@@ -354,6 +365,7 @@ PairLaunch pair_launch(nbody_ctx* c, bool vjp) {
   L.eps2 = c->cfg.eps * c->cfg.eps;
   const Tiling& t = vjp ? c->vt : c->ft;
   L.block = t.block, L.ipt = t.ipt, L.jtile = t.jtile, L.n_ctas = t.n_ctas;
+  L.variant = vjp ? 0 : t.variant;
   return L;
 }
 
@@ -373,9 +385,9 @@ cudaEvent_t pooled_event(nbody_ctx* c) {
 
 // Launches an all-pairs kernel, bracketed by an event pair when profiling an
 // eager (non-capturing) stream.
-nbody_status run_pair(nbody_ctx* c, cudaStream_t st, bool vjp) {
+nbody_status run_pair(nbody_ctx* c, cudaStream_t st, bool vjp, const double* x64) {
   if (c->n_total == 0) return NBODY_OK;
-  PairLaunch L = pair_launch(c, vjp);
+  PairLaunch L = pair_launch(c, vjp, x64);
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (c->profiling && !c->capturing) {
     e0 = pooled_event(c);
@@ -391,8 +403,9 @@ nbody_status run_pair(nbody_ctx* c, cudaStream_t st, bool vjp) {
   return NBODY_OK;
 }
 
-nbody_status run_force(nbody_ctx* c, cudaStream_t st) { return run_pair(c, st, false); }
-nbody_status run_vjp(nbody_ctx* c, cudaStream_t st) { return run_pair(c, st, true); }
+// x64: the float64 positions the staging was taken from (near-pair refinement).
+nbody_status run_force(nbody_ctx* c, cudaStream_t st, const double* x64) { return run_pair(c, st, false, x64); }
+nbody_status run_vjp(nbody_ctx* c, cudaStream_t st) { return run_pair(c, st, true, nullptr); }
 
 PostLaunch post_launch(nbody_ctx* c, unsigned mode, double* x, double* v, const double* m, double* a, double* phi) {
   PostLaunch P{};
@@ -423,8 +436,9 @@ nbody_status run_post(nbody_ctx* c, const PostLaunch& P, cudaStream_t st) {
 
 nbody_status run_centre(nbody_ctx* c, const double* x, const double* m, cudaStream_t st) {
   if (c->cfg.precision != NBODY_MIXED || c->n_total == 0) return NBODY_OK;
-  NB_CUDA(c, launch_centre(c->d_off, c->n_sys, x, m, static_cast<double*>(c->centre.p), st));
-  ++c->launches;
+  NB_CUDA(c, launch_centre(c->d_chunks, (int)c->chunks.size(), c->d_sys_chunk, c->d_off, c->n_sys, x, m,
+                           static_cast<double*>(c->epart.p), static_cast<double*>(c->centre.p), st));
+  c->launches += c->chunks.empty() ? 1 : 2;
   return NBODY_OK;
 }
 
@@ -441,7 +455,7 @@ nbody_status enqueue_step(nbody_ctx* c, double* x, double* v, const double* m, d
   if ((s = run_centre(c, x, m, st))) return s;
   if (!a_valid) {
     if ((s = run_post(c, post_launch(c, kStage, x, v, m, a, nullptr), st))) return s;
-    if ((s = run_force(c, st))) return s;
+    if ((s = run_force(c, st, x))) return s;
     if ((s = run_post(c, post_launch(c, kCombine, x, v, m, a, nullptr), st))) return s;
   }
   if (n_steps == 0) return NBODY_OK;
@@ -449,7 +463,7 @@ nbody_status enqueue_step(nbody_ctx* c, double* x, double* v, const double* m, d
   const int every = c->cfg.energy_every;
   int rec = 0;
   for (int k = 0; k < n_steps; ++k) {
-    if ((s = run_force(c, st))) return s;
+    if ((s = run_force(c, st, x))) return s;
     const bool rec_now = elog && every > 0 && (k + 1) % every == 0;
     unsigned mode = kCombine | kKickEnd;
     if (rec_now) mode |= kEnergy;
@@ -500,17 +514,28 @@ nbody_status fill_synthetic(nbody_ctx* c, bool with_w) {
   return NBODY_OK;
 }
 
-// Times the installed tiling; returns seconds per interaction slot (lower is better).
+// Times the installed tiling; returns seconds per interaction slot (lower is
+// better). When the whole work list is timed, the O(N) pass that adds the
+// slices is timed with it, so that longer lists of shorter slices pay for
+// their partial-sum traffic.
 nbody_status time_tiling(nbody_ctx* c, bool vjp, double* cost) {
   PairLaunch L = pair_launch(c, vjp);
   const Tiling& t = vjp ? c->vt : c->ft;
-  // estimate of the work per launch, used to bound the tuning time
   cudaEvent_t e0, e1;
   NB_CUDA(c, cudaEventCreate(&e0));
   NB_CUDA(c, cudaEventCreate(&e1));
   auto launch = [&](const PairLaunch& P) {
     return vjp ? launch_vjp(c->cfg.precision, P, c->stream) : launch_force(c->cfg.precision, P, c->stream);
   };
+  PostLaunch C{};
+  C.chunks = vjp ? c->d_vchunks : c->d_chunks;
+  C.n_chunks = (int32_t)c->chunks.size();
+  C.part = static_cast<const double*>(c->part.p);
+  C.n_total = c->n_total;
+  C.G = 1.0;
+  C.a = static_cast<double*>(c->a_scratch.p);
+  C.mode = kCombine;
+  C.status = c->status;
   // warm-up on a prefix of at most 2 items per CTA
   PairLaunch P = L;
   P.n_items = std::min(L.n_items, 2 * t.n_ctas);
@@ -521,29 +546,34 @@ nbody_status time_tiling(nbody_ctx* c, bool vjp, double* cost) {
   if (err == cudaSuccess) err = cudaEventRecord(e1, c->stream);
   if (err == cudaSuccess) err = cudaEventSynchronize(e1);
   if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
-  // whole list if it is short enough (captures the tail of the schedule)
-  if (err == cudaSuccess && P.n_items < L.n_items && ms * (double)L.n_items / P.n_items < 60.0) {
+  // whole list if it is short enough (captures the tail of the schedule and the slice combine)
+  int timed_launches = 2;
+  if (err == cudaSuccess && ms * (double)L.n_items / std::max(1, P.n_items) < 60.0) {
     P = L;
-    err = cudaEventRecord(e0, c->stream);
-    if (err == cudaSuccess) err = launch(P);
-    if (err == cudaSuccess) err = launch(P);
+    err = launch(P);  // every (slice, body) partial is written before it is combined
+    if (err == cudaSuccess && !vjp) err = launch_post(C, c->stream);
+    if (err == cudaSuccess) err = cudaEventRecord(e0, c->stream);
+    for (int rep = 0; rep < 2 && err == cudaSuccess; ++rep) {
+      err = launch(P);
+      if (err == cudaSuccess && !vjp) err = launch_post(C, c->stream);
+    }
     if (err == cudaSuccess) err = cudaEventRecord(e1, c->stream);
     if (err == cudaSuccess) err = cudaEventSynchronize(e1);
     if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
     ms *= 0.5f;
+    timed_launches += vjp ? 3 : 6;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (err != cudaSuccess) return fail(c, NBODY_ECUDA, "autotune launch failed: %s", cudaGetErrorString(err));
-  // interaction slots covered by the timed items
+  // interaction slots covered by the timed items (the list is longest-first)
   double slots = 0.0;
   {
-    // items are LPT-sorted; the timed prefix holds the largest items
     std::vector<WorkItem> h(P.n_items);
     NB_CUDA(c, cudaMemcpy(h.data(), L.items, h.size() * sizeof(WorkItem), cudaMemcpyDeviceToHost));
     for (const auto& w : h) slots += (double)(w.i_end - w.i_begin) * (double)(w.j_end - w.j_begin);
   }
-  c->launches += (P.n_items == L.n_items) ? 3 : 2;
+  c->launches += timed_launches;
   *cost = slots > 0 ? (ms * 1e-3) / slots : 1e30;
   return NBODY_OK;
 }
@@ -554,21 +584,25 @@ nbody_status autotune(nbody_ctx* c, bool vjp) {
   const int blocks[] = {128, 256};
   const int ipts_f[] = {1, 2, 4}, ipts_v[] = {1, 2};
   const int jts_f[] = {128, 256}, jts_v[] = {128};
-  for (int b : blocks) {
-    if (!vjp && g.block && g.block != b) continue;
-    for (int r : (vjp ? std::vector<int>(ipts_v, ipts_v + 2) : std::vector<int>(ipts_f, ipts_f + 3))) {
-      if (!vjp && g.i_per_thread && g.i_per_thread != r) continue;
-      for (int j : (vjp ? std::vector<int>(jts_v, jts_v + 1) : std::vector<int>(jts_f, jts_f + 2))) {
-        if (!vjp && g.j_tile && g.j_tile != j) continue;
-        Tiling t;
-        t.block = b, t.ipt = r, t.jtile = j, t.slice = vjp ? 0 : g.slice;
-        cands.push_back(t);
+  std::vector<int> variants = {0};
+  if (!vjp && g.precision == NBODY_MIXED) variants = g.variant ? std::vector<int>{g.variant - 1} : std::vector<int>{0, 1};
+  for (int var : variants)
+    for (int b : blocks) {
+      if (!vjp && g.block && g.block != b) continue;
+      for (int r : (vjp ? std::vector<int>(ipts_v, ipts_v + 2) : std::vector<int>(ipts_f, ipts_f + 3))) {
+        if (!vjp && g.i_per_thread && g.i_per_thread != r) continue;
+        for (int j : (vjp ? std::vector<int>(jts_v, jts_v + 1) : std::vector<int>(jts_f, jts_f + 2))) {
+          if (!vjp && g.j_tile && g.j_tile != j) continue;
+          Tiling t;
+          t.block = b, t.ipt = r, t.jtile = j, t.slice = vjp ? 0 : g.slice, t.variant = var;
+          cands.push_back(t);
+        }
       }
     }
-  }
   if (cands.empty()) return fail(c, NBODY_EINVAL, "no compiled tiling matches the requested parameters");
   nbody_status s = fill_synthetic(c, vjp);
   if (s) return s;
+  if ((s = ensure(c, c->a_scratch, (size_t)c->n_total * 3 * sizeof(double)))) return s;
   double best = 1e300;
   Tiling bt = cands[0];
   for (const Tiling& t : cands) {
@@ -599,14 +633,19 @@ nbody_status autotune(nbody_ctx* c, bool vjp) {
     bt.slice = bl;
   }
   bt.n_ctas = 0;
-  return install_tiling(c, bt, vjp);
+  if ((s = install_tiling(c, bt, vjp))) return s;
+  // synthetic data must not leave a latched device condition behind
+  NB_CUDA(c, cudaStreamSynchronize(c->stream));
+  NB_CUDA(c, cudaMemset(c->status, 0, sizeof(unsigned)));
+  return NBODY_OK;
 }
 
 nbody_status validate_cfg(const nbody_config* g) {
   if (!g) return NBODY_EINVAL;
   if (!finite(g->G) || !finite(g->eps) || g->eps < 0 || !finite(g->dt)) return NBODY_EINVAL;
   if (g->precision != NBODY_FP64 && g->precision != NBODY_MIXED) return NBODY_EINVAL;
-  if (g->energy_every < 0 || g->reserved != 0) return NBODY_EINVAL;
+  if (g->energy_every < 0 || g->variant < 0 || g->variant > 2) return NBODY_EINVAL;
+  if (g->precision == NBODY_FP64 && g->variant > 1) return NBODY_EINVAL;
   if (g->block && g->block != 128 && g->block != 256) return NBODY_EINVAL;
   if (g->i_per_thread && g->i_per_thread != 1 && g->i_per_thread != 2 && g->i_per_thread != 4) return NBODY_EINVAL;
   if (g->j_tile && g->j_tile != 128 && g->j_tile != 256) return NBODY_EINVAL;
@@ -736,7 +775,8 @@ nbody_status nbody_init(nbody_ctx** out, const nbody_config* cfg, int64_t n_syst
           cudaSuccess)
     return bail(fail(c, NBODY_ECUDA, "upload of layout tables failed"));
 
-  if (c->n_total > 0 && (cfg->block == 0 || cfg->i_per_thread == 0 || cfg->j_tile == 0)) {
+  const bool fixed_variant = cfg->precision == NBODY_FP64 || cfg->variant != 0;
+  if (c->n_total > 0 && (cfg->block == 0 || cfg->i_per_thread == 0 || cfg->j_tile == 0 || !fixed_variant)) {
     if ((s = autotune(c, false))) return bail(s);
   } else {
     Tiling t;
@@ -744,6 +784,7 @@ nbody_status nbody_init(nbody_ctx** out, const nbody_config* cfg, int64_t n_syst
     t.ipt = cfg->i_per_thread ? cfg->i_per_thread : 2;
     t.jtile = cfg->j_tile ? cfg->j_tile : 128;
     t.slice = cfg->slice;
+    t.variant = (cfg->precision == NBODY_MIXED && cfg->variant == 2) ? 1 : 0;
     if ((s = install_tiling(c, t, false))) return bail(s);
   }
   if (cudaDeviceSynchronize() != cudaSuccess) return bail(fail(c, NBODY_ECUDA, "init synchronisation failed"));
@@ -766,7 +807,7 @@ nbody_status nbody_forces(nbody_ctx* c, const double* x, const double* m, double
   double* xm = const_cast<double*>(x);
   if ((s = run_centre(c, x, m, c->stream))) return s;
   if ((s = run_post(c, post_launch(c, kStage, xm, nullptr, m, a, nullptr), c->stream))) return s;
-  if ((s = run_force(c, c->stream))) return s;
+  if ((s = run_force(c, c->stream, x))) return s;
   return run_post(c, post_launch(c, kCombine, xm, nullptr, m, a, phi), c->stream);
 }
 
@@ -836,7 +877,7 @@ nbody_status nbody_energy(nbody_ctx* c, const double* x, const double* v, const 
   double* as = static_cast<double*>(c->a_scratch.p);
   if ((s = run_centre(c, x, m, c->stream))) return s;
   if ((s = run_post(c, post_launch(c, kStage, xm, vm, m, as, nullptr), c->stream))) return s;
-  if ((s = run_force(c, c->stream))) return s;
+  if ((s = run_force(c, c->stream, x))) return s;
   if ((s = run_post(c, post_launch(c, kCombine | kEnergy, xm, vm, m, as, nullptr), c->stream))) return s;
   // systems without bodies have no chunks and get all-zero records
   return run_energy_final(c, out, c->stream);
@@ -889,7 +930,7 @@ nbody_status nbody_adjoint(nbody_ctx* c, const double* x0, const double* v0, con
   NB_CUDA(c, cudaMemcpyAsync(xw, x0, n3b, cudaMemcpyDeviceToDevice, st));
   NB_CUDA(c, cudaMemcpyAsync(vw, v0, n3b, cudaMemcpyDeviceToDevice, st));
   if ((s = run_post(c, post_launch(c, kStage, xw, vw, m, aw, nullptr), st))) return s;
-  if ((s = run_force(c, st))) return s;
+  if ((s = run_force(c, st, xw))) return s;
   if ((s = run_post(c, post_launch(c, kCombine, xw, vw, m, aw, nullptr), st))) return s;
 
   // one KDK step on (xw, vw, aw), optionally copying x after the drift
@@ -898,7 +939,7 @@ nbody_status nbody_adjoint(nbody_ctx* c, const double* x0, const double* v0, con
     PostLaunch P = post_launch(c, kDrift | kStage, xw, vw, m, aw, nullptr);
     P.x_copy = xcopy;
     if ((r = run_post(c, P, st))) return r;
-    if ((r = run_force(c, st))) return r;
+    if ((r = run_force(c, st, xw))) return r;
     return run_post(c, post_launch(c, kCombine | kKickEnd, xw, vw, m, aw, nullptr), st);
   };
 
@@ -1007,13 +1048,14 @@ nbody_status nbody_sync(nbody_ctx* c) {
 }
 
 nbody_status nbody_get_tuning(const nbody_ctx* c, int32_t* block, int32_t* ipt, int32_t* jtile, int32_t* slice,
-                              int32_t* n_ctas) {
+                              int32_t* n_ctas, int32_t* variant) {
   if (!c) return NBODY_EINVAL;
   if (block) *block = c->ft.block;
   if (ipt) *ipt = c->ft.ipt;
   if (jtile) *jtile = c->ft.jtile;
   if (slice) *slice = c->ft.slice;
   if (n_ctas) *n_ctas = c->ft.n_ctas;
+  if (variant) *variant = c->ft.variant + 1;
   return NBODY_OK;
 }
 

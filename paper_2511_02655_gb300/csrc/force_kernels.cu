@@ -9,7 +9,9 @@
 //           pair per body (TwoSum), converted to float64 per work item.
 //   fp64  : staged double4_32a (x, y, z, m), every operation in float64.
 //
-// Both are persistent kernels over a work list of (i-tile, j-slice) items.
+// The mixed path has a scalar kernel and a packed one (two j-bodies per
+// float32x2 instruction); the autotuner picks.
+// Both precisions are persistent kernels over a work list of (i-tile, j-slice) items.
 // i-bodies live in registers (R per thread, strided by the CTA size so loads
 // and stores coalesce), j-bodies stream through a shared-memory tile that
 // every thread reads with broadcast loads; the next tile is prefetched into
@@ -23,40 +25,107 @@
 namespace nbody {
 namespace {
 
-template <bool MASK>
-__device__ __forceinline__ void pair_f32(const float4 q, const float xi, const float yi, const float zi,
-                                         const float eps2, float& ax, float& ay, float& az, float& pp,
-                                         const bool self) {
+// Near-pair refinement. The float32 staging coordinates carry an absolute
+// rounding error of about |x - c| 2^-24, harmless for distant pairs but
+// dominant for pairs closer than a few softening lengths. Pairs with s^2 below
+// the refinement radius get d recomputed from the caller's float64 positions,
+// rounded once. Such pairs are rare, so they are found without a branch per
+// pair: every pair folds its s^2 into a running minimum (one FMNMX), and after
+// each sub-block of kSub j-bodies a thread whose minimum fell below the radius
+// rescans that sub-block and, for each near pair, adds the refined
+// contribution minus the unrefined one it accumulated in the first pass.
+constexpr int kSub = 32;
+
+__device__ __forceinline__ void refine_pair(const double* __restrict__ x64, const int i, const int j, const float eps2,
+                                            float& dx, float& dy, float& dz, float& r2) {
+  dx = (float)(x64[3 * (int64_t)j + 0] - x64[3 * (int64_t)i + 0]);
+  dy = (float)(x64[3 * (int64_t)j + 1] - x64[3 * (int64_t)i + 1]);
+  dz = (float)(x64[3 * (int64_t)j + 2] - x64[3 * (int64_t)i + 2]);
+  r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
+}
+
+// Second look at one pair (j-body q at global index jg, i-body at ig) of a
+// flagged sub-block: if it is near and not the self pair, replace its
+// unrefined contribution in (ax, ay, az, pp) by the refined one. The
+// unrefined terms are recomputed with exactly the first pass's operations.
+__device__ __forceinline__ void correct_pair(const float4 q, const int jg, const int ig, const int i_end,
+                                             const float xi, const float yi, const float zi, const float eps2,
+                                             const float r2c, const double* __restrict__ x64, float& ax, float& ay,
+                                             float& az, float& pp) {
   const float dx = q.x - xi;
   const float dy = q.y - yi;
   const float dz = q.z - zi;
   const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
+  if (!(r2 < r2c) || ig >= i_end || jg < 0 || ig == jg) return;
+  const float iu = rsq_approx(r2);
+  const float msu = q.w * iu;
+  const float wu = msu * (iu * iu);
+  float rx, ry, rz, rr2;
+  refine_pair(x64, ig, jg, eps2, rx, ry, rz, rr2);
+  const float ir = rsq_approx(rr2);
+  const float msr = q.w * ir;
+  const float wr = msr * (ir * ir);
+  ax += fmaf(rx, wr, -(dx * wu));
+  ay += fmaf(ry, wr, -(dy * wu));
+  az += fmaf(rz, wr, -(dz * wu));
+  pp += msr - msu;
+}
+
+// ---- scalar kernel: one j-body against the thread's R i-bodies per step
+
+template <bool MASK>
+__device__ __forceinline__ void pair_f32(const float4 q, const int jg, const int ig, const float xi, const float yi,
+                                         const float zi, const float eps2, float& ax, float& ay, float& az, float& pp,
+                                         float& mn) {
+  const float dx = q.x - xi;
+  const float dy = q.y - yi;
+  const float dz = q.z - zi;
+  const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
+  mn = fminf(mn, r2);
   float inv = rsq_approx(r2);
-  if (MASK) inv = self ? 0.f : inv;
-  const float ms = q.w * inv;         // m_j / s
-  const float w = ms * (inv * inv);   // m_j / s^3
+  if (MASK) inv = (jg == ig) ? 0.f : inv;
+  const float ms = q.w * inv;        // m_j / s
+  const float w = ms * (inv * inv);  // m_j / s^3
   ax = fmaf(dx, w, ax);
   ay = fmaf(dy, w, ay);
   az = fmaf(dz, w, az);
   pp += ms;
 }
 
-template <bool MASK>
-__device__ __forceinline__ void pair_f64(const double4_32a q, const double xi, const double yi, const double zi,
-                                         const double eps2, double& ax, double& ay, double& az, double& pp,
-                                         const bool self) {
-  const double dx = q.x - xi;
-  const double dy = q.y - yi;
-  const double dz = q.z - zi;
-  const double r2 = fma(dx, dx, fma(dy, dy, fma(dz, dz, eps2)));
-  double inv = rsqrt(r2);
-  if (MASK) inv = self ? 0.0 : inv;
-  const double ms = q.w * inv;
-  const double w = ms * (inv * inv);
-  ax = fma(dx, w, ax);
-  ay = fma(dy, w, ay);
-  az = fma(dz, w, az);
-  pp += ms;
+template <int R, bool MASK>
+__device__ __forceinline__ void tile_pass_f32(const float4* tile, const int jt, const int nj, const float (&xi)[R],
+                                              const float (&yi)[R], const float (&zi)[R], const int (&ig)[R],
+                                              const int i_end, const float eps2, const float r2c,
+                                              const double* __restrict__ x64, float (&ax)[R], float (&ay)[R],
+                                              float (&az)[R], float (&pp)[R]) {
+  for (int jb = 0; jb < nj; jb += kSub) {
+    const int nb = min(kSub, nj - jb);
+    float mn = 3.0e38f;
+    if (nb == kSub) {
+#pragma unroll 8
+      for (int j = jb; j < jb + kSub; ++j) {
+        const float4 q = tile[j];
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+          pair_f32<MASK>(q, jt + j, ig[r], xi[r], yi[r], zi[r], eps2, ax[r], ay[r], az[r], pp[r], mn);
+      }
+    } else {
+      for (int j = jb; j < jb + nb; ++j) {
+        const float4 q = tile[j];
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+          pair_f32<MASK>(q, jt + j, ig[r], xi[r], yi[r], zi[r], eps2, ax[r], ay[r], az[r], pp[r], mn);
+      }
+    }
+    if (mn < r2c) {
+      for (int j = jb; j < jb + nb; ++j) {
+        const float4 q = tile[j];
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+          correct_pair(q, jt + j, ig[r], i_end, xi[r], yi[r], zi[r], eps2, r2c, x64, ax[r], ay[r], az[r], pp[r]);
+      }
+    }
+  }
 }
 
 template <int BLOCK, int R, int J>
@@ -67,6 +136,8 @@ __global__ void __launch_bounds__(BLOCK) k_force_mixed(const PairLaunch L) {
   const float4* __restrict__ st = static_cast<const float4*>(L.stage_x);
   double4_32a* __restrict__ part = reinterpret_cast<double4_32a*>(L.part);
   const float eps2 = (float)L.eps2;
+  const float r2c = L.r2_near;
+  const double* __restrict__ x64 = L.x64;
 
   for (;;) {
     const int it = next_item(L.counter, &s_item);
@@ -112,32 +183,11 @@ __global__ void __launch_bounds__(BLOCK) k_force_mixed(const PairLaunch L) {
       float ax[R], ay[R], az[R], pp[R];
 #pragma unroll
       for (int r = 0; r < R; ++r) ax[r] = ay[r] = az[r] = pp[r] = 0.f;
-
       const bool diag = (jt < w.i_end) && (w.i_begin < jt + nj);
-      if (diag) {
-        for (int j = 0; j < nj; ++j) {
-          const float4 q = tile[j];
-#pragma unroll
-          for (int r = 0; r < R; ++r)
-            pair_f32<true>(q, xi[r], yi[r], zi[r], eps2, ax[r], ay[r], az[r], pp[r], jt + j == ig[r]);
-        }
-      } else if (nj == J) {
-#pragma unroll 8
-        for (int j = 0; j < J; ++j) {
-          const float4 q = tile[j];
-#pragma unroll
-          for (int r = 0; r < R; ++r)
-            pair_f32<false>(q, xi[r], yi[r], zi[r], eps2, ax[r], ay[r], az[r], pp[r], false);
-        }
-      } else {
-#pragma unroll 4
-        for (int j = 0; j < nj; ++j) {
-          const float4 q = tile[j];
-#pragma unroll
-          for (int r = 0; r < R; ++r)
-            pair_f32<false>(q, xi[r], yi[r], zi[r], eps2, ax[r], ay[r], az[r], pp[r], false);
-        }
-      }
+      if (diag)
+        tile_pass_f32<R, true>(tile, jt, nj, xi, yi, zi, ig, w.i_end, eps2, r2c, x64, ax, ay, az, pp);
+      else
+        tile_pass_f32<R, false>(tile, jt, nj, xi, yi, zi, ig, w.i_end, eps2, r2c, x64, ax, ay, az, pp);
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         two_sum_acc(hx[r], lx[r], ax[r]);
@@ -152,10 +202,211 @@ __global__ void __launch_bounds__(BLOCK) k_force_mixed(const PairLaunch L) {
     for (int r = 0; r < R; ++r) {
       if (ig[r] < w.i_end)
         out[ig[r]] = make_double4_32a((double)hx[r] + (double)lx[r], (double)hy[r] + (double)ly[r],
-                                  (double)hz[r] + (double)lz[r], (double)hp[r] + (double)lp[r]);
+                                      (double)hz[r] + (double)lz[r], (double)hp[r] + (double)lp[r]);
     }
   }
   retire_cta(L.counter);
+}
+
+// ---- packed kernel: two j-bodies per float32x2 instruction
+//
+// The j-tile is kept as structure of arrays (x[], y[], z[], m[]), so one
+// 16-byte shared load yields the coordinates of four j-bodies, i.e. two
+// float32x2 operands, and each i-body is held once as a duplicated pair
+// (-x_i, -x_i). Lane 0 of every float32x2 accumulator sums the even j-bodies
+// of a tile, lane 1 the odd ones; the lanes are added when the tile is folded.
+// FADD2 / FFMA2 / FMUL2 halve the issue slots of the FMA-pipe work, which
+// leaves issue bandwidth for the MUFU, shared-load and minimum instructions.
+// Tail tiles are padded to a multiple of four with massless bodies far away.
+
+constexpr float kFarAway = 1.0e18f;
+
+template <bool MASK>
+__device__ __forceinline__ void pair2_f32x2(const float2 xj, const float2 yj, const float2 zj, const float2 mj,
+                                            const int jg0, const int ig, const float2 nx, const float2 ny,
+                                            const float2 nz, const float2 e2, float2& ax, float2& ay, float2& az,
+                                            float2& pp, float& mn0, float& mn1) {
+  const float2 dx = __fadd2_rn(xj, nx);
+  const float2 dy = __fadd2_rn(yj, ny);
+  const float2 dz = __fadd2_rn(zj, nz);
+  const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __ffma2_rn(dz, dz, e2)));
+  mn0 = fminf(mn0, r2.x);
+  mn1 = fminf(mn1, r2.y);
+  float2 inv = make_float2(rsq_approx(r2.x), rsq_approx(r2.y));
+  if (MASK) {
+    inv.x = (jg0 == ig) ? 0.f : inv.x;
+    inv.y = (jg0 + 1 == ig) ? 0.f : inv.y;
+  }
+  const float2 ms = __fmul2_rn(mj, inv);
+  const float2 w = __fmul2_rn(ms, __fmul2_rn(inv, inv));
+  ax = __ffma2_rn(dx, w, ax);
+  ay = __ffma2_rn(dy, w, ay);
+  az = __ffma2_rn(dz, w, az);
+  pp = __fadd2_rn(pp, ms);
+}
+
+// Four j-bodies (tile entries j..j+3) against the thread's R i-bodies.
+template <int R, bool MASK>
+__device__ __forceinline__ void quad_f32x2(const float* tx, const float* ty, const float* tz, const float* tm,
+                                           const int j, const int jg, const int (&ig)[R], const float2 (&nx)[R],
+                                           const float2 (&ny)[R], const float2 (&nz)[R], const float2 e2,
+                                           float2 (&ax)[R], float2 (&ay)[R], float2 (&az)[R], float2 (&pp)[R],
+                                           float& mn0, float& mn1) {
+  const float4 X = *reinterpret_cast<const float4*>(tx + j);
+  const float4 Y = *reinterpret_cast<const float4*>(ty + j);
+  const float4 Z = *reinterpret_cast<const float4*>(tz + j);
+  const float4 M = *reinterpret_cast<const float4*>(tm + j);
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    pair2_f32x2<MASK>(make_float2(X.x, X.y), make_float2(Y.x, Y.y), make_float2(Z.x, Z.y), make_float2(M.x, M.y),
+                      jg, ig[r], nx[r], ny[r], nz[r], e2, ax[r], ay[r], az[r], pp[r], mn0, mn1);
+    pair2_f32x2<MASK>(make_float2(X.z, X.w), make_float2(Y.z, Y.w), make_float2(Z.z, Z.w), make_float2(M.z, M.w),
+                      jg + 2, ig[r], nx[r], ny[r], nz[r], e2, ax[r], ay[r], az[r], pp[r], mn0, mn1);
+  }
+}
+
+template <int R, bool MASK>
+__device__ __forceinline__ void tile_pass_f32x2(const float* tx, const float* ty, const float* tz, const float* tm,
+                                                const int jt, const int nj, const int (&ig)[R], const float2 (&nx)[R],
+                                                const float2 (&ny)[R], const float2 (&nz)[R], const int i_end,
+                                                const float2 e2, const float r2c, const double* __restrict__ x64,
+                                                float2 (&ax)[R], float2 (&ay)[R], float2 (&az)[R], float2 (&pp)[R]) {
+  const int nj4 = (nj + 3) & ~3;  // the tile is padded to a multiple of four
+  for (int jb = 0; jb < nj4; jb += kSub) {
+    const int nb = min(kSub, nj4 - jb);
+    float mn0 = 3.0e38f, mn1 = 3.0e38f;
+    if (nb == kSub) {
+#pragma unroll 4
+      for (int j = jb; j < jb + kSub; j += 4)
+        quad_f32x2<R, MASK>(tx, ty, tz, tm, j, jt + j, ig, nx, ny, nz, e2, ax, ay, az, pp, mn0, mn1);
+    } else {
+      for (int j = jb; j < jb + nb; j += 4)
+        quad_f32x2<R, MASK>(tx, ty, tz, tm, j, jt + j, ig, nx, ny, nz, e2, ax, ay, az, pp, mn0, mn1);
+    }
+    if (fminf(mn0, mn1) < r2c) {
+      for (int j = jb; j < min(jb + nb, nj); ++j) {
+        const float4 q = make_float4(tx[j], ty[j], tz[j], tm[j]);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          float& cx = (j & 1) ? ax[r].y : ax[r].x;
+          float& cy = (j & 1) ? ay[r].y : ay[r].x;
+          float& cz = (j & 1) ? az[r].y : az[r].x;
+          float& cp = (j & 1) ? pp[r].y : pp[r].x;
+          correct_pair(q, jt + j, ig[r], i_end, -nx[r].x, -ny[r].x, -nz[r].x, e2.x, r2c, x64, cx, cy, cz, cp);
+        }
+      }
+    }
+  }
+}
+
+template <int BLOCK, int R, int J>
+__global__ void __launch_bounds__(BLOCK) k_force_mixed2(const PairLaunch L) {
+  static_assert(J % 4 == 0, "tiles hold whole quads of j-bodies");
+  constexpr int LPT = (J + BLOCK - 1) / BLOCK;
+  __shared__ __align__(16) float tx[J];
+  __shared__ __align__(16) float ty[J];
+  __shared__ __align__(16) float tz[J];
+  __shared__ __align__(16) float tm[J];
+  __shared__ int s_item;
+  const float4* __restrict__ st = static_cast<const float4*>(L.stage_x);
+  double4_32a* __restrict__ part = reinterpret_cast<double4_32a*>(L.part);
+  const float eps2 = (float)L.eps2;
+  const float2 e2 = make_float2(eps2, eps2);
+  const float r2c = L.r2_near;
+  const double* __restrict__ x64 = L.x64;
+
+  for (;;) {
+    const int it = next_item(L.counter, &s_item);
+    if (it >= L.n_items) break;
+    const WorkItem w = L.items[it];
+
+    float2 nx[R], ny[R], nz[R];
+    float hx[R], hy[R], hz[R], hp[R], lx[R], ly[R], lz[R], lp[R];
+    int ig[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      ig[r] = w.i_begin + (int)threadIdx.x + r * BLOCK;
+      const float4 q = ig[r] < w.i_end ? st[ig[r]] : make_float4(0.f, 0.f, 0.f, 0.f);
+      nx[r] = make_float2(-q.x, -q.x);
+      ny[r] = make_float2(-q.y, -q.y);
+      nz[r] = make_float2(-q.z, -q.z);
+      hx[r] = hy[r] = hz[r] = hp[r] = 0.f;
+      lx[r] = ly[r] = lz[r] = lp[r] = 0.f;
+    }
+
+    float4 pre[LPT];
+#pragma unroll
+    for (int k = 0; k < LPT; ++k) {
+      const int jj = w.j_begin + (int)threadIdx.x + k * BLOCK;
+      if ((int)threadIdx.x + k * BLOCK < J && jj < w.j_end) pre[k] = st[jj];
+    }
+
+    for (int jt = w.j_begin; jt < w.j_end; jt += J) {
+      const int nj = min(J, w.j_end - jt);
+      const int nj4 = (nj + 3) & ~3;
+      __syncthreads();
+#pragma unroll
+      for (int k = 0; k < LPT; ++k) {
+        const int t = (int)threadIdx.x + k * BLOCK;
+        if (t < nj) {
+          tx[t] = pre[k].x, ty[t] = pre[k].y, tz[t] = pre[k].z, tm[t] = pre[k].w;
+        } else if (t < nj4) {
+          tx[t] = kFarAway, ty[t] = kFarAway, tz[t] = kFarAway, tm[t] = 0.f;
+        }
+      }
+      __syncthreads();
+      if (jt + J < w.j_end) {
+#pragma unroll
+        for (int k = 0; k < LPT; ++k) {
+          const int jj = jt + J + (int)threadIdx.x + k * BLOCK;
+          if ((int)threadIdx.x + k * BLOCK < J && jj < w.j_end) pre[k] = st[jj];
+        }
+      }
+
+      float2 ax[R], ay[R], az[R], pp[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) ax[r] = ay[r] = az[r] = pp[r] = make_float2(0.f, 0.f);
+      const bool diag = (jt < w.i_end) && (w.i_begin < jt + nj);
+      if (diag)
+        tile_pass_f32x2<R, true>(tx, ty, tz, tm, jt, nj, ig, nx, ny, nz, w.i_end, e2, r2c, x64, ax, ay, az, pp);
+      else
+        tile_pass_f32x2<R, false>(tx, ty, tz, tm, jt, nj, ig, nx, ny, nz, w.i_end, e2, r2c, x64, ax, ay, az, pp);
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        two_sum_acc(hx[r], lx[r], ax[r].x + ax[r].y);
+        two_sum_acc(hy[r], ly[r], ay[r].x + ay[r].y);
+        two_sum_acc(hz[r], lz[r], az[r].x + az[r].y);
+        two_sum_acc(hp[r], lp[r], pp[r].x + pp[r].y);
+      }
+    }
+
+    double4_32a* out = part + (int64_t)w.slice * L.n_total;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      if (ig[r] < w.i_end)
+        out[ig[r]] = make_double4_32a((double)hx[r] + (double)lx[r], (double)hy[r] + (double)ly[r],
+                                      (double)hz[r] + (double)lz[r], (double)hp[r] + (double)lp[r]);
+    }
+  }
+  retire_cta(L.counter);
+}
+
+template <bool MASK>
+__device__ __forceinline__ void pair_f64(const double4_32a q, const double xi, const double yi, const double zi,
+                                         const double eps2, double& ax, double& ay, double& az, double& pp,
+                                         const bool self) {
+  const double dx = q.x - xi;
+  const double dy = q.y - yi;
+  const double dz = q.z - zi;
+  const double r2 = fma(dx, dx, fma(dy, dy, fma(dz, dz, eps2)));
+  double inv = rsqrt(r2);
+  if (MASK) inv = self ? 0.0 : inv;
+  const double ms = q.w * inv;
+  const double w = ms * (inv * inv);
+  ax = fma(dx, w, ax);
+  ay = fma(dy, w, ay);
+  az = fma(dz, w, az);
+  pp += ms;
 }
 
 template <int BLOCK, int R, int J>
@@ -239,29 +490,50 @@ int occupancy_of(K kern, int block) {
   return n;
 }
 
-// Tilings compiled: BLOCK in {128, 256}, R in {1, 2, 4}, J in {128, 256}.
+// Tilings compiled: BLOCK in {128, 256}, R in {1, 2, 4}, J in {128, 256}
+// (the packed mixed kernel, variant 1, for R in {1, 2, 4} too).
 #define NBODY_FORCE_TILINGS(X) \
   X(128, 1, 128) X(128, 2, 128) X(128, 4, 128) X(128, 1, 256) X(128, 2, 256) X(128, 4, 256) \
   X(256, 1, 128) X(256, 2, 128) X(256, 4, 128) X(256, 1, 256) X(256, 2, 256) X(256, 4, 256)
+#define NBODY_PACKED_TILINGS(X) NBODY_FORCE_TILINGS(X)
 
 }  // namespace
 
 cudaError_t launch_force(int precision, const PairLaunch& L, cudaStream_t st) {
   if (L.n_ctas <= 0) return cudaErrorInvalidConfiguration;
-#define NBODY_X(B, R, J)                                                                     \
-  if (L.block == B && L.ipt == R && L.jtile == J) {                                          \
-    if (precision == 1)                                                                      \
-      k_force_mixed<B, R, J><<<L.n_ctas, B, 0, st>>>(L);                                     \
-    else                                                                                     \
-      k_force_fp64<B, R, J><<<L.n_ctas, B, 0, st>>>(L);                                      \
-    return cudaGetLastError();                                                               \
+  if (precision == 1 && L.variant == 1) {
+#define NBODY_X(B, R, J)                                               \
+  if (L.block == B && L.ipt == R && L.jtile == J) {                    \
+    k_force_mixed2<B, R, J><<<L.n_ctas, B, 0, st>>>(L);                \
+    return cudaGetLastError();                                         \
+  }
+    NBODY_PACKED_TILINGS(NBODY_X)
+#undef NBODY_X
+    return cudaErrorInvalidConfiguration;
+  }
+  if (L.variant != 0) return cudaErrorInvalidConfiguration;
+#define NBODY_X(B, R, J)                                               \
+  if (L.block == B && L.ipt == R && L.jtile == J) {                    \
+    if (precision == 1)                                                \
+      k_force_mixed<B, R, J><<<L.n_ctas, B, 0, st>>>(L);               \
+    else                                                               \
+      k_force_fp64<B, R, J><<<L.n_ctas, B, 0, st>>>(L);                \
+    return cudaGetLastError();                                         \
   }
   NBODY_FORCE_TILINGS(NBODY_X)
 #undef NBODY_X
   return cudaErrorInvalidConfiguration;
 }
 
-int force_ctas_per_sm(int precision, int block, int ipt, int jtile) {
+int force_ctas_per_sm(int precision, int variant, int block, int ipt, int jtile) {
+  if (precision == 1 && variant == 1) {
+#define NBODY_X(B, R, J) \
+  if (block == B && ipt == R && jtile == J) return occupancy_of(k_force_mixed2<B, R, J>, B);
+    NBODY_PACKED_TILINGS(NBODY_X)
+#undef NBODY_X
+    return 0;
+  }
+  if (variant != 0) return 0;
 #define NBODY_X(B, R, J)                                                                     \
   if (block == B && ipt == R && jtile == J)                                                  \
     return precision == 1 ? occupancy_of(k_force_mixed<B, R, J>, B) : occupancy_of(k_force_fp64<B, R, J>, B);

@@ -25,7 +25,7 @@ struct Chunk {
   int32_t n_slices;  // force/VJP slices of this system (partials to combine)
 };
 
-constexpr int kChunk = 1024;        // bodies per chunk
+constexpr int kChunk = 256;         // bodies per chunk (one per thread of an O(N) CTA)
 constexpr int kPostThreads = 256;   // threads per O(N) kernel CTA
 constexpr int kEnergyVals = 8;      // K, U, Px, Py, Pz, Lx, Ly, Lz per chunk
 constexpr int kAdjVals = 8;         // VJP partial values per body per slice
@@ -46,6 +46,9 @@ struct PairLaunch {
   double* part;          // force: double4_32a [slices][N]; VJP: 2 x double4_32a [slices][N]
   int64_t n_total;
   double eps2;
+  const double* x64;     // force (mixed): caller's float64 positions [N,3] for near-pair refinement
+  float r2_near;         // force (mixed): refine pairs with s^2 below this (0 = never)
+  int variant;           // force (mixed): 0 scalar float32, 1 packed float32x2
   int block, ipt, jtile; // tiling
   int n_ctas;            // persistent grid size
 };
@@ -54,7 +57,7 @@ struct PairLaunch {
 cudaError_t launch_force(int precision, const PairLaunch& L, cudaStream_t st);
 cudaError_t launch_vjp(int precision, const PairLaunch& L, cudaStream_t st);
 // CTAs of the force kernel that fit on one SM for the tiling (0 if unsupported).
-int force_ctas_per_sm(int precision, int block, int ipt, int jtile);
+int force_ctas_per_sm(int precision, int variant, int block, int ipt, int jtile);
 int vjp_ctas_per_sm(int precision, int block, int ipt, int jtile);
 
 // ---------------------------------------------------------------------------
@@ -89,9 +92,10 @@ struct PostLaunch {
 };
 cudaError_t launch_post(const PostLaunch& P, cudaStream_t st);
 
-// centre[s] = mass-weighted mean position of system s (plain mean if the mass is 0)
-cudaError_t launch_centre(const int64_t* sys_off_dev, int n_sys, const double* x, const double* m, double* centre,
-                          cudaStream_t st);
+// centre[s] = mass-weighted mean position of system s (plain mean if the mass is 0);
+// two passes: per-chunk sums into cpart [n_chunks][kEnergyVals], then per system in order.
+cudaError_t launch_centre(const Chunk* chunks, int n_chunks, const int32_t* sys_chunk, const int64_t* off, int n_sys,
+                          const double* x, const double* m, double* cpart, double* centre, cudaStream_t st);
 
 // out[s][9] = {E, K, U, P, L} from the chunk partials, chunk range of s = sys_chunk[s] .. sys_chunk[s+1]-1
 cudaError_t launch_energy_final(const int32_t* sys_chunk, int n_sys, const double* epart, double* out,

@@ -62,6 +62,7 @@ __global__ void __launch_bounds__(kPostThreads) k_post(const PostLaunch P) {
     double ax = 0.0, ay = 0.0, az = 0.0, ph = 0.0;
     if (mode & kCombine) {
       double sx = 0.0, sy = 0.0, sz = 0.0, sp = 0.0;
+#pragma unroll 8
       for (int s = 0; s < c.n_slices; ++s) {
         const double4_32a q = part[(int64_t)s * P.n_total + i];
         sx += q.x, sy += q.y, sz += q.z, sp += q.w;
@@ -109,20 +110,38 @@ __global__ void __launch_bounds__(kPostThreads) k_post(const PostLaunch P) {
   if (bad) atomicOr(P.status, kFlagNonFinite);
 }
 
-__global__ void __launch_bounds__(256) k_centre(const int64_t* off, const double* x, const double* m,
-                                                double* centre) {
-  const int s = blockIdx.x;
-  const int64_t b = off[s], e = off[s + 1];
-  double v[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};  // sum m x (3), sum m, sum x (3)
-  for (int64_t i = b + threadIdx.x; i < e; i += 256) {
+// Staging origin, pass 1: per chunk, sum m x (3), sum m, sum x (3) into cpart[chunk][8].
+__global__ void __launch_bounds__(kPostThreads) k_centre_part(const Chunk* chunks, const double* x, const double* m,
+                                                              double* cpart) {
+  const Chunk c = chunks[blockIdx.x];
+  double v[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  for (int i = c.begin + (int)threadIdx.x; i < c.end; i += kPostThreads) {
     const double mi = m[i];
     const double x0 = x[3 * i + 0], x1 = x[3 * i + 1], x2 = x[3 * i + 2];
     v[0] += mi * x0, v[1] += mi * x1, v[2] += mi * x2, v[3] += mi;
     v[4] += x0, v[5] += x1, v[6] += x2;
   }
-  block_sum<7, 256>(v);
+  block_sum<7, kPostThreads>(v);
   if (threadIdx.x == 0) {
-    const int64_t n = e - b;
+#pragma unroll
+    for (int k = 0; k < 7; ++k) cpart[(int64_t)blockIdx.x * kEnergyVals + k] = v[k];
+  }
+}
+
+// Pass 2: per system, the chunk sums in a fixed order -> mass-weighted mean
+// position (plain mean if the mass is not positive; 0 for an empty system).
+__global__ void __launch_bounds__(32) k_centre_final(const int32_t* sys_chunk, const int64_t* off,
+                                                     const double* cpart, double* centre) {
+  const int s = blockIdx.x;
+  double v[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  for (int c = sys_chunk[s] + (int)threadIdx.x; c < sys_chunk[s + 1]; c += 32) {
+#pragma unroll
+    for (int k = 0; k < 7; ++k) v[k] += cpart[(int64_t)c * kEnergyVals + k];
+  }
+#pragma unroll
+  for (int k = 0; k < 7; ++k) v[k] = warp_sum(v[k]);
+  if (threadIdx.x == 0) {
+    const int64_t n = off[s + 1] - off[s];
     double c0 = 0.0, c1 = 0.0, c2 = 0.0;
     if (v[3] > 0.0 && isfinite(v[3])) {
       c0 = v[0] / v[3], c1 = v[1] / v[3], c2 = v[2] / v[3];
@@ -163,6 +182,7 @@ __global__ void __launch_bounds__(kPostThreads) k_adj_update(const AdjLaunch A) 
   bool bad = false;
   for (int i = c.begin + (int)threadIdx.x; i < c.end; i += kPostThreads) {
     double a1x = 0, a1y = 0, a1z = 0, a2 = 0, gbx = 0, gby = 0, gbz = 0, gm = 0;
+#pragma unroll 4
     for (int s = 0; s < c.n_slices; ++s) {
       const int64_t k = 2 * ((int64_t)s * A.n_total + i);
       const double4_32a p = part[k], q = part[k + 1];
@@ -221,10 +241,15 @@ cudaError_t launch_post(const PostLaunch& P, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_centre(const int64_t* off, int n_sys, const double* x, const double* m, double* centre,
-                          cudaStream_t st) {
+cudaError_t launch_centre(const Chunk* chunks, int n_chunks, const int32_t* sys_chunk, const int64_t* off, int n_sys,
+                          const double* x, const double* m, double* cpart, double* centre, cudaStream_t st) {
   if (n_sys <= 0) return cudaSuccess;
-  k_centre<<<n_sys, 256, 0, st>>>(off, x, m, centre);
+  if (n_chunks > 0) {
+    k_centre_part<<<n_chunks, kPostThreads, 0, st>>>(chunks, x, m, cpart);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  k_centre_final<<<n_sys, 32, 0, st>>>(sys_chunk, off, cpart, centre);
   return cudaGetLastError();
 }
 

@@ -59,7 +59,7 @@ def _cfg(**kw):
 
 @pytest.mark.parametrize("bad", [dict(eps=-1.0), dict(precision=7), dict(block=96), dict(i_per_thread=3),
                                  dict(j_tile=100), dict(energy_every=-1), dict(flags=64), dict(G=float("nan")),
-                                 dict(reserved=1)])
+                                 dict(variant=3), dict(variant=2, precision=0)])
 def test_init_rejects_bad_config_before_touching_a_device(lib, bad):
     h = ctypes.c_void_p(123)
     offs = (ctypes.c_int64 * 2)(0, 16)

@@ -1,0 +1,156 @@
+"""GPU adjoint (force-VJP kernel + checkpointed reverse leapfrog) against the
+oracle's reverse sweep, against central finite differences, and through the
+torch.autograd.Function wrapper."""
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2511_02655_gb300 import inputs
+from helpers import to_dev, to_np
+
+pytestmark = pytest.mark.gpu
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300))
+
+
+def _small_case(n=96, seed=21):
+    x, v, m = inputs.plummer(n, seed=seed)
+    m = m * np.exp(0.3 * np.random.default_rng(seed).standard_normal(n))
+    t = inputs.targets(n, seed=seed + 1)
+    return x, v, m, t
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-11), (1, 2e-5)])
+@pytest.mark.parametrize("T,K", [(20, 5), (17, 4), (9, 1), (12, 12), (5, 8), (1, 1)])
+def test_adjoint_matches_oracle_reverse_sweep(nb, prec, tol, T, K):
+    import torch
+    G, eps, dt = 1.0, 0.05, 5e-3
+    x, v, m, t = _small_case()
+    xT, vT, _, _ = oracle.kdk(x, v, m, G, eps, dt, T)
+    lx, lv = 2 * (xT - t), 0.1 * np.random.default_rng(3).standard_normal(xT.shape)
+    gx_o, gv_o, gm_o = oracle.adjoint(x, v, m, G, eps, dt, T, lx, lv)
+    ctx = nb.nbody_init(G=G, eps=eps, dt=dt, precision=prec, n=len(m))
+    xt, vt, mt, lxt, lvt = to_dev(x, v, m, lx, lv)
+    gx, gv, gm = nb.nbody_adjoint(ctx, xt, vt, mt, T, K, lxt, lvt)
+    nb.nbody_sync(ctx)
+    gx, gv, gm = to_np(gx, gv, gm)
+    assert rel(gx, gx_o) <= tol and rel(gv, gv_o) <= tol and rel(gm, gm_o) <= tol, \
+        (rel(gx, gx_o), rel(gv, gv_o), rel(gm, gm_o))
+    # inputs untouched
+    assert np.array_equal(xt.cpu().numpy(), x) and np.array_equal(vt.cpu().numpy(), v)
+
+
+def test_adjoint_zero_steps_is_identity(nb):
+    x, v, m, t = _small_case(16)
+    ctx = nb.nbody_init(G=1.0, eps=0.05, dt=1e-3, precision=nb.MIXED, n=16)
+    lx, lv = np.ones((16, 3)), 2 * np.ones((16, 3))
+    gx, gv, gm = nb.nbody_adjoint(ctx, *to_dev(x, v, m), 0, 3, *to_dev(lx, lv))
+    gx, gv, gm = to_np(gx, gv, gm)
+    assert np.array_equal(gx, lx) and np.array_equal(gv, lv) and np.all(gm == 0)
+
+
+def test_adjoint_several_systems(nb):
+    sizes = [7, 130, 0, 300]
+    ens = inputs.ensemble(len(sizes), seed=5, sizes=np.array(sizes))
+    off = [int(o) for o in ens.offsets]
+    G, eps, dt, T, K = 1.0, 0.05, 4e-3, 10, 3
+    t = inputs.targets(off[-1], seed=6)
+    ctx = nb.nbody_init(G=G, eps=eps, dt=dt, precision=nb.FP64, offsets=off)
+    lx_all = np.zeros((off[-1], 3))
+    for s in range(len(sizes)):
+        b, e = off[s], off[s + 1]
+        if e > b:
+            xT, _, _, _ = oracle.kdk(ens.x[b:e], ens.v[b:e], ens.m[b:e], G, eps, dt, T)
+            lx_all[b:e] = 2 * (xT - t[b:e])
+    gx, gv, gm = nb.nbody_adjoint(ctx, *to_dev(ens.x, ens.v, ens.m), T, K, *to_dev(lx_all, np.zeros_like(lx_all)))
+    gx, gv, gm = to_np(gx, gv, gm)
+    for s in range(len(sizes)):
+        b, e = off[s], off[s + 1]
+        if e == b:
+            continue
+        ox, ov, om = oracle.adjoint(ens.x[b:e], ens.v[b:e], ens.m[b:e], G, eps, dt, T, lx_all[b:e],
+                                    np.zeros((e - b, 3)))
+        assert rel(gx[b:e], ox) <= 1e-11 and rel(gv[b:e], ov) <= 1e-11 and rel(gm[b:e], om) <= 1e-11
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_autograd_function(nb, prec):
+    import torch
+    G, eps, dt, T, K = 1.0, 0.05, 5e-3, 12, 5
+    x, v, m, t = _small_case(64, seed=40)
+    ctx = nb.nbody_init(G=G, eps=eps, dt=dt, precision=prec, n=64)
+    xt, vt, mt, tt = to_dev(x, v, m, t)
+    x0 = xt.clone().requires_grad_(True)
+    v0 = vt.clone().requires_grad_(True)
+    m0 = mt.clone().requires_grad_(True)
+    xT, vT = nb.NBodyAdjoint.apply(ctx, x0, v0, m0, T, K)
+    loss = ((xT - tt) ** 2).sum() + 0.5 * (vT ** 2).sum()
+    loss.backward()
+    # the forward equals nbody_step, the backward equals nbody_adjoint
+    xs, vs, a = xt.clone(), vt.clone(), torch.empty_like(xt)
+    nb.nbody_step(ctx, xs, vs, mt, a, False, T)
+    assert torch.equal(xs, xT.detach()) and torch.equal(vs, vT.detach())
+    gx, gv, gm = nb.nbody_adjoint(ctx, xt, vt, mt, T, K, 2 * (xs - tt), vs.clone())
+    for g, ref in ((gx, x0.grad), (gv, v0.grad), (gm, m0.grad)):
+        assert torch.allclose(g, ref, rtol=1e-14, atol=0)
+    ox, ov, om = oracle.adjoint(x, v, m, G, eps, dt, T, 2 * (xs.cpu().numpy() - t), vs.cpu().numpy())
+    tol = 1e-11 if prec == 0 else 2e-5
+    assert rel(x0.grad.cpu().numpy(), ox) <= tol and rel(m0.grad.cpu().numpy(), om) <= tol
+
+
+@pytest.mark.slow
+def test_adjoint_n16384_200_steps_vs_finite_differences(nb):
+    """N = 16384 Plummer, 200 KDK steps, dt = 1e-3, checkpoints every 20 steps; loss = sum |x_T - t|^2.
+    FP64 and mixed adjoint gradients vs FP64 central differences (h = 1e-6) on 32 coordinates
+    (12 positions, 12 velocities, 8 masses), relative error <= 1e-4."""
+    import torch
+    n, G, eps, dt, T, K = 16384, 1.0, 0.01, 1e-3, 200, 20
+    x, v, m = inputs.plummer(n, seed=5)
+    t = inputs.targets(n, seed=6)
+    rng = np.random.default_rng(7)
+    pos = [(int(i), int(c)) for i, c in zip(rng.choice(n, 12, replace=False), rng.integers(0, 3, 12))]
+    vel = [(int(i), int(c)) for i, c in zip(rng.choice(n, 12, replace=False), rng.integers(0, 3, 12))]
+    mas = [int(i) for i in rng.choice(n, 8, replace=False)]
+    tt = to_dev(t)[0]
+    # FD systems: 64 perturbed copies advanced together as one batched FP64 ensemble
+    h = 1e-6
+    copies_x, copies_v, copies_m = [], [], []
+    for kind, items in (("x", pos), ("v", vel), ("m", [(i, None) for i in mas])):
+        for i, c in items:
+            for sgn in (1.0, -1.0):
+                xx, vv, mm = x.copy(), v.copy(), m.copy()
+                if kind == "x":
+                    xx[i, c] += sgn * h
+                elif kind == "v":
+                    vv[i, c] += sgn * h
+                else:
+                    mm[i] += sgn * h
+                copies_x.append(xx), copies_v.append(vv), copies_m.append(mm)
+    nc = len(copies_x)
+    off = [k * n for k in range(nc + 1)]
+    ctxb = nb.nbody_init(G=G, eps=eps, dt=dt, precision=nb.FP64, offsets=off)
+    xb, vb, mb = to_dev(np.concatenate(copies_x), np.concatenate(copies_v), np.concatenate(copies_m))
+    ab = torch.empty_like(xb)
+    nb.nbody_step(ctxb, xb, vb, mb, ab, False, T)
+    nb.nbody_sync(ctxb)
+    # L+ - L- = sum (x+ - x-) . (x+ + x- - 2t): differencing the trajectories first avoids the
+    # cancellation of two ~5e4-sized sums
+    xr = xb.view(nc, n, 3)
+    dL = ((xr[0::2] - xr[1::2]) * (xr[0::2] + xr[1::2] - 2 * tt)).sum(dim=(1, 2)).cpu().numpy()
+    fd = dL / (2 * h)
+    ctxb.close()
+    for prec in (nb.FP64, nb.MIXED):
+        ctx = nb.nbody_init(G=G, eps=eps, dt=dt, precision=prec, n=n)
+        xt, vt, mt = to_dev(x, v, m)
+        xs, vs, a = xt.clone(), vt.clone(), torch.empty_like(xt)
+        nb.nbody_step(ctx, xs, vs, mt, a, False, T)
+        gx, gv, gm = nb.nbody_adjoint(ctx, xt, vt, mt, T, K, 2 * (xs - tt), torch.zeros_like(vs))
+        nb.nbody_sync(ctx)
+        gx, gv, gm = to_np(gx, gv, gm)
+        ad = np.array([gx[i, c] for i, c in pos] + [gv[i, c] for i, c in vel] + [gm[i] for i in mas])
+        err = np.abs(ad - fd) / np.maximum(np.abs(fd), 1e-3 * np.abs(fd).max())
+        assert err.max() <= 1e-4, (prec, err.max(), np.argmax(err))
+        ctx.close()
