@@ -52,11 +52,27 @@ def parse():
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=("ours", "reference"), default="ours")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-aux", action="store_true", help="skip the other workloads' short measurements")
     return p.parse_args()
 
 
 def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def reduce_max(value, dist=None, device=None):
+    """Max of a float over all ranks (identity without a process group)."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world, max_seconds):
+    """Whole-job throughput: units all ranks processed / the slowest rank's time."""
+    return world * float(units_per_rank) / max_seconds
 
 
 class ClockSampler:
@@ -156,6 +172,100 @@ def cpu_baseline(x, m, G, eps, a_gpu, budget_s=12.0):
     return base, {"median": float(np.median(err)), "max": float(err.max()), "bodies": int(k)}
 
 
+def _event_time(fn, stream):
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) * 1e-3
+
+
+def aux_measurements(dev):
+    """The other workloads, each measured briefly (rank 0, one GPU): CUDA-event times around
+    nbody_step / nbody_adjoint calls, initialisation and autotuning excluded."""
+    import numpy as np
+    import torch
+
+    import paper_2511_02655_gb300 as nb
+    from paper_2511_02655_gb300 import inputs
+    stream = torch.cuda.current_stream()
+    out = {}
+    # two Plummer spheres, N = 1 048 576, eps = 0.002, dt = 5e-4, mixed
+    n = 1048576
+    x, v, m = inputs.two_spheres(n, seed=3)
+    ctx = nb.nbody_init(G=1.0, eps=0.002, dt=5e-4, precision=nb.MIXED, n=n)
+    xt, vt, mt = (torch.from_numpy(t).to(dev) for t in (x, v, m))
+    at = torch.empty_like(xt)
+    nb.nbody_forces(ctx, xt, mt, at, None, with_phi=False)
+    nb.nbody_profile(ctx, True)
+    k = 3
+    sec = _event_time(lambda: nb.nbody_step(ctx, xt, vt, mt, at, True, k), stream)
+    kms, kl = nb.nbody_kernel_time(ctx, 0)
+    nb.nbody_sync(ctx)
+    out["two_spheres_1m"] = {"interactions_per_s": float(n) * n * k / sec, "steps": k,
+                             "force_kernel_ms": kms / kl, "tuning": nb.nbody_get_tuning(ctx)}
+    ctx.close()
+    del xt, vt, mt, at
+    # ensemble: 512 Plummer systems, N log-uniform in [64, 16384], eps = 0.01, dt = 1e-3
+    ens = inputs.ensemble(512, seed=4)
+    off = [int(o) for o in ens.offsets]
+    pairs = float((np.diff(ens.offsets).astype(np.float64) ** 2).sum())
+    ctx = nb.nbody_init(G=1.0, eps=0.01, dt=1e-3, precision=nb.MIXED, offsets=off, energy_every=50,
+                        flags=nb.FLAG_GRAPH)
+    xt, vt, mt = (torch.from_numpy(t).to(dev) for t in (ens.x, ens.v, ens.m))
+    at = torch.empty_like(xt)
+    log = torch.empty((1, 512, 9), dtype=torch.float64, device=dev)
+    nb.nbody_forces(ctx, xt, mt, at, None, with_phi=False)
+    nb.nbody_step(ctx, xt, vt, mt, at, True, 50, log)  # captures the graph
+    l0 = nb.nbody_launch_count(ctx)
+    sec = _event_time(lambda: nb.nbody_step(ctx, xt, vt, mt, at, True, 50, log), stream)
+    nb.nbody_sync(ctx)
+    launches = nb.nbody_launch_count(ctx) - l0
+    ctx.close()
+    # the same systems as 512 separate FP64 contexts, one launch sequence per system, 1 step
+    ctxs, bufs = [], []
+    for s_ in range(512):
+        b, e = off[s_], off[s_ + 1]
+        c1 = nb.nbody_init(G=1.0, eps=0.01, dt=1e-3, precision=nb.FP64, n=e - b, block=128, i_per_thread=1,
+                           j_tile=128)
+        xs, vs, ms = (torch.from_numpy(np.ascontiguousarray(t[b:e])).to(dev) for t in (ens.x, ens.v, ens.m))
+        a1 = torch.empty_like(xs)
+        nb.nbody_forces(c1, xs, ms, a1, None, with_phi=False)
+        ctxs.append(c1), bufs.append((xs, vs, ms, a1))
+
+    def per_system():
+        for c1, (xs, vs, ms, a1) in zip(ctxs, bufs):
+            nb.nbody_step(c1, xs, vs, ms, a1, True, 1)
+
+    sec64 = _event_time(per_system, stream)
+    for c1 in ctxs:
+        c1.close()
+    out["ensemble_512"] = {"mixed_graph_interactions_per_s": pairs * 50 / sec, "steps": 50,
+                           "fp64_per_system_interactions_per_s": pairs / sec64,
+                           "graph_over_fp64_per_system": (pairs * 50 / sec) / (pairs / sec64),
+                           "pairs_per_step": pairs, "launches_per_50_steps": int(launches)}
+    # adjoint: N = 16384 Plummer, 200 KDK steps, dt = 1e-3, checkpoints every 20, loss sum |x_T - t|^2
+    n = 16384
+    x, v, m = inputs.plummer(n, seed=5)
+    t = torch.from_numpy(inputs.targets(n, seed=6)).to(dev)
+    for prec, name in ((nb.MIXED, "adjoint_16384_mixed"), (nb.FP64, "adjoint_16384_fp64")):
+        ctx = nb.nbody_init(G=1.0, eps=0.01, dt=1e-3, precision=prec, n=n)
+        xt, vt, mt = (torch.from_numpy(a).to(dev) for a in (x, v, m))
+        xs, vs, at = xt.clone(), vt.clone(), torch.empty_like(xt)
+        nb.nbody_step(ctx, xs, vs, mt, at, False, 200)
+        lam = 2 * (xs - t)
+        nb.nbody_adjoint(ctx, xt, vt, mt, 200, 20, lam, torch.zeros_like(vs))  # tunes the VJP tiling
+        sec = _event_time(lambda: nb.nbody_adjoint(ctx, xt, vt, mt, 200, 20, lam, torch.zeros_like(vs)), stream)
+        nb.nbody_sync(ctx)
+        out[name] = {"seconds": sec, "steps": 200, "checkpoint_every": 20,
+                     "force_equivalent_passes": "1 forward + 1 recompute force pass and 1 VJP pass per step"}
+        ctx.close()
+    return out
+
+
 def run_reference(args):
     """The CPU oracle on this host's cores, on the same workload: each step is a bounded sample."""
     rank, world, _ = dist_env()
@@ -251,13 +361,9 @@ def run_ours(args):
     force_ms, force_launches = nb.nbody_kernel_time(ctx, 0)
     nb.nbody_profile(ctx, False)
     nb.nbody_sync(ctx)
-    total_ms = sum(a.elapsed_time(b) for a, b in ev)
-    if pg:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = reduce_max(sum(a.elapsed_time(b) for a, b in ev), pg, dev)
     interactions = float(n) * n
-    value = world * interactions * K / (total_ms * 1e-3)
+    value = whole_job_rate(interactions * K, world, total_ms * 1e-3)
     elog = log.cpu().numpy()[:, 0, 0]
     drift = float(np.abs(elog - E0).max() / abs(E0))
 
@@ -295,12 +401,8 @@ def run_ours(args):
     t0 = time.perf_counter()
     for _ in range(ke):
         nb.nbody_step_host(ctx, xh, vh, mh, ah, True, 1, lh)
-    e2e_s = time.perf_counter() - t0
-    if pg:
-        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = {"value": world * interactions * ke / e2e_s, "unit": UNIT,
+    e2e_s = reduce_max(time.perf_counter() - t0, pg, dev)
+    e2e = {"value": whole_job_rate(interactions * ke, world, e2e_s), "unit": UNIT,
            "h2d_bytes_per_step": n * 10 * 8, "d2h_bytes_per_step": n * 9 * 8 + 9 * 8,
            "call": "nbody_step_host (1 KDK step per call, pinned host x, v, m, a in; x, v, a, energy out)"}
 
@@ -309,6 +411,11 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         base, ferr = cpu_baseline(x, m, G, eps, a0)
     ctx.close()
+    aux = None
+    if rank == 0 and world == 1 and not args.no_aux:
+        del xt, vt, mt, at, flush
+        torch.cuda.empty_cache()
+        aux = aux_measurements(dev)
 
     if rank == 0:
         line = {
@@ -337,6 +444,7 @@ def run_ours(args):
             "e2e": e2e,
             "clocks": clk,
             "gpu_launches": int(launches),
+            "aux": aux,
         }
         print(json.dumps(line), flush=True)
     if pg:

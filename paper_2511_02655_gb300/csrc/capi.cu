@@ -24,6 +24,8 @@ namespace {
 constexpr int64_t kMaxBodies = int64_t(1) << 29;      // 3 * N fits in int32 index arithmetic
 constexpr size_t kMaxPartialBytes = size_t(1) << 30;  // cap on per-slice partial-sum memory
 constexpr int kMinTilesPerSlice = 4;
+constexpr double kTuneLargePairs = 4.0e10;  // above this many pairs per force pass, tune on short slices
+constexpr int kTuneSlice = 8192;
 
 struct Tiling {
   int block = 0, ipt = 0, jtile = 0, slice = 0, n_ctas = 0;
@@ -515,15 +517,13 @@ nbody_status fill_synthetic(nbody_ctx* c, bool with_w) {
 }
 
 // Times the installed tiling; returns seconds per interaction slot (lower is
-// better). When the whole work list is timed, the O(N) pass that adds the
-// slices is timed with it, so that longer lists of shorter slices pay for
-// their partial-sum traffic.
+// better), the best of three timed launches. Short work lists are timed whole,
+// together with the O(N) pass that adds the slices, so that lists of shorter
+// slices pay for their partial-sum traffic and the tail of the schedule
+// counts; long lists are timed on a prefix of two items per persistent CTA.
 nbody_status time_tiling(nbody_ctx* c, bool vjp, double* cost) {
   PairLaunch L = pair_launch(c, vjp);
   const Tiling& t = vjp ? c->vt : c->ft;
-  cudaEvent_t e0, e1;
-  NB_CUDA(c, cudaEventCreate(&e0));
-  NB_CUDA(c, cudaEventCreate(&e1));
   auto launch = [&](const PairLaunch& P) {
     return vjp ? launch_vjp(c->cfg.precision, P, c->stream) : launch_force(c->cfg.precision, P, c->stream);
   };
@@ -536,35 +536,35 @@ nbody_status time_tiling(nbody_ctx* c, bool vjp, double* cost) {
   C.a = static_cast<double*>(c->a_scratch.p);
   C.mode = kCombine;
   C.status = c->status;
-  // warm-up on a prefix of at most 2 items per CTA
+  cudaEvent_t ev[4];
+  for (auto& e : ev) NB_CUDA(c, cudaEventCreate(&e));
+  auto timed = [&](const PairLaunch& P, bool combine, float* best_ms) -> cudaError_t {
+    cudaError_t err = launch(P);  // warm-up; also writes every partial the combine reads
+    if (err == cudaSuccess && combine) err = launch_post(C, c->stream);
+    *best_ms = 1e30f;
+    for (int rep = 0; rep < 3 && err == cudaSuccess; ++rep) {
+      err = cudaEventRecord(ev[0], c->stream);
+      if (err == cudaSuccess) err = launch(P);
+      if (err == cudaSuccess && combine) err = launch_post(C, c->stream);
+      if (err == cudaSuccess) err = cudaEventRecord(ev[1], c->stream);
+      if (err == cudaSuccess) err = cudaEventSynchronize(ev[1]);
+      float ms = 0.f;
+      if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, ev[0], ev[1]);
+      if (err == cudaSuccess) *best_ms = std::min(*best_ms, ms);
+    }
+    c->launches += 4 * (combine ? 2 : 1);
+    return err;
+  };
   PairLaunch P = L;
   P.n_items = std::min(L.n_items, 2 * t.n_ctas);
-  cudaError_t err = launch(P);
   float ms = 0.f;
-  if (err == cudaSuccess) err = cudaEventRecord(e0, c->stream);
-  if (err == cudaSuccess) err = launch(P);
-  if (err == cudaSuccess) err = cudaEventRecord(e1, c->stream);
-  if (err == cudaSuccess) err = cudaEventSynchronize(e1);
-  if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
-  // whole list if it is short enough (captures the tail of the schedule and the slice combine)
-  int timed_launches = 2;
-  if (err == cudaSuccess && ms * (double)L.n_items / std::max(1, P.n_items) < 60.0) {
+  cudaError_t err = cudaSuccess;
+  if (P.n_items < L.n_items) err = timed(P, false, &ms);
+  if (err == cudaSuccess && (P.n_items == L.n_items || ms * (double)L.n_items / std::max(1, P.n_items) < 60.0)) {
     P = L;
-    err = launch(P);  // every (slice, body) partial is written before it is combined
-    if (err == cudaSuccess && !vjp) err = launch_post(C, c->stream);
-    if (err == cudaSuccess) err = cudaEventRecord(e0, c->stream);
-    for (int rep = 0; rep < 2 && err == cudaSuccess; ++rep) {
-      err = launch(P);
-      if (err == cudaSuccess && !vjp) err = launch_post(C, c->stream);
-    }
-    if (err == cudaSuccess) err = cudaEventRecord(e1, c->stream);
-    if (err == cudaSuccess) err = cudaEventSynchronize(e1);
-    if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
-    ms *= 0.5f;
-    timed_launches += vjp ? 3 : 6;
+    err = timed(P, !vjp, &ms);
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
+  for (auto& e : ev) cudaEventDestroy(e);
   if (err != cudaSuccess) return fail(c, NBODY_ECUDA, "autotune launch failed: %s", cudaGetErrorString(err));
   // interaction slots covered by the timed items (the list is longest-first)
   double slots = 0.0;
@@ -573,7 +573,6 @@ nbody_status time_tiling(nbody_ctx* c, bool vjp, double* cost) {
     NB_CUDA(c, cudaMemcpy(h.data(), L.items, h.size() * sizeof(WorkItem), cudaMemcpyDeviceToHost));
     for (const auto& w : h) slots += (double)(w.i_end - w.i_begin) * (double)(w.j_end - w.j_begin);
   }
-  c->launches += timed_launches;
   *cost = slots > 0 ? (ms * 1e-3) / slots : 1e30;
   return NBODY_OK;
 }
@@ -603,17 +602,28 @@ nbody_status autotune(nbody_ctx* c, bool vjp) {
   nbody_status s = fill_synthetic(c, vjp);
   if (s) return s;
   if ((s = ensure(c, c->a_scratch, (size_t)c->n_total * 3 * sizeof(double)))) return s;
+  // Large layouts are compared on work lists of short slices (the cost per
+  // interaction no longer depends on the slice length there), which keeps the
+  // timed prefix short; their final slice is the automatic choice.
+  double pairs = 0.0;
+  for (int k = 0; k < c->n_sys; ++k) {
+    const double n = (double)(c->offsets[k + 1] - c->offsets[k]);
+    pairs += n * n;
+  }
+  const bool large = pairs > kTuneLargePairs;
   double best = 1e300;
   Tiling bt = cands[0];
-  for (const Tiling& t : cands) {
-    if (ctas_per_sm(g.precision, t, vjp) <= 0) continue;
+  for (const Tiling& t0 : cands) {
+    if (ctas_per_sm(g.precision, t0, vjp) <= 0) continue;
+    Tiling t = t0;
+    if (large && t.slice == 0) t.slice = kTuneSlice;
     if ((s = install_tiling(c, t, vjp))) return s;
     double cost = 0;
     if ((s = time_tiling(c, vjp, &cost))) return s;
-    if (cost < best) best = cost, bt = t;
+    if (cost < best) best = cost, bt = t0;
   }
   // slice-length refinement around the automatic choice for the best tiling
-  if (!vjp && g.slice == 0) {
+  if (!vjp && g.slice == 0 && !large) {
     Tiling base = bt;
     base.slice = 0;
     if ((s = install_tiling(c, base, vjp))) return s;
