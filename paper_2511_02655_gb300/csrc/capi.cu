@@ -9,6 +9,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -489,26 +490,50 @@ uint64_t splitmix(uint64_t& s) {
   return z ^ (z >> 31);
 }
 
-// Fills the staging buffers with a synthetic cloud (unit cube, equal masses)
-// so candidate tilings can be timed before any user data exists.
+// Fills the staging buffers with synthetic bodies so that candidate tilings
+// can be timed before any user data exists: each system is a Plummer sphere
+// (scale radius 1, total mass 1, radii truncated at 20), the clustered
+// distribution these kernels are typically run on, which also sets how often
+// the near-pair correction of the mixed kernels fires.
 nbody_status fill_synthetic(nbody_ctx* c, bool with_w) {
   const int64_t n = c->n_total;
   uint64_t seed = 12345;
-  auto u = [&] { return (double)(splitmix(seed) >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0; };
+  auto u01 = [&] { return ((double)(splitmix(seed) >> 11) + 0.5) * (1.0 / 9007199254740992.0); };
+  std::vector<double> pos(3 * (size_t)n), mass((size_t)n);
+  for (int s = 0; s < c->n_sys; ++s) {
+    const int64_t b = c->offsets[s], e = c->offsets[s + 1];
+    for (int64_t i = b; i < e; ++i) {
+      double r;
+      do {
+        r = 1.0 / std::sqrt(std::pow(u01(), -2.0 / 3.0) - 1.0);
+      } while (!(r <= 20.0));
+      const double z = 2.0 * u01() - 1.0, ph = 6.283185307179586 * u01();
+      const double rho = std::sqrt(std::max(0.0, 1.0 - z * z));
+      pos[3 * i + 0] = r * rho * std::cos(ph);
+      pos[3 * i + 1] = r * rho * std::sin(ph);
+      pos[3 * i + 2] = r * z;
+      mass[i] = 1.0 / (double)(e - b);
+    }
+  }
+  // float64 copy for the near-pair refinement while timing (context work buffer)
+  nbody_status st = ensure(c, c->xw, 3 * (size_t)n * sizeof(double));
+  if (st) return st;
+  NB_CUDA(c, cudaMemcpy(c->xw.p, pos.data(), 3 * (size_t)n * sizeof(double), cudaMemcpyHostToDevice));
   if (c->cfg.precision == NBODY_MIXED) {
     std::vector<float4> h(n);
-    for (int64_t i = 0; i < n; ++i) h[i] = make_float4((float)u(), (float)u(), (float)u(), 1.0f / (float)n);
+    for (int64_t i = 0; i < n; ++i)
+      h[i] = make_float4((float)pos[3 * i], (float)pos[3 * i + 1], (float)pos[3 * i + 2], (float)mass[i]);
     NB_CUDA(c, cudaMemcpy(c->stage.p, h.data(), n * sizeof(float4), cudaMemcpyHostToDevice));
     if (with_w) {
-      for (int64_t i = 0; i < n; ++i) h[i] = make_float4((float)u(), (float)u(), (float)u(), 0.f);
+      for (int64_t i = 0; i < n; ++i) h[i] = make_float4((float)u01(), (float)u01(), (float)u01(), 0.f);
       NB_CUDA(c, cudaMemcpy(c->stage_w.p, h.data(), n * sizeof(float4), cudaMemcpyHostToDevice));
     }
   } else {
     std::vector<double4_32a> h(n);
-    for (int64_t i = 0; i < n; ++i) h[i] = make_double4_32a(u(), u(), u(), 1.0 / (double)n);
+    for (int64_t i = 0; i < n; ++i) h[i] = make_double4_32a(pos[3 * i], pos[3 * i + 1], pos[3 * i + 2], mass[i]);
     NB_CUDA(c, cudaMemcpy(c->stage.p, h.data(), n * sizeof(double4_32a), cudaMemcpyHostToDevice));
     if (with_w) {
-      for (int64_t i = 0; i < n; ++i) h[i] = make_double4_32a(u(), u(), u(), 0.0);
+      for (int64_t i = 0; i < n; ++i) h[i] = make_double4_32a(u01(), u01(), u01(), 0.0);
       NB_CUDA(c, cudaMemcpy(c->stage_w.p, h.data(), n * sizeof(double4_32a), cudaMemcpyHostToDevice));
     }
   }
@@ -522,7 +547,7 @@ nbody_status fill_synthetic(nbody_ctx* c, bool with_w) {
 // slices pay for their partial-sum traffic and the tail of the schedule
 // counts; long lists are timed on a prefix of two items per persistent CTA.
 nbody_status time_tiling(nbody_ctx* c, bool vjp, double* cost) {
-  PairLaunch L = pair_launch(c, vjp);
+  PairLaunch L = pair_launch(c, vjp, vjp ? nullptr : static_cast<const double*>(c->xw.p));
   const Tiling& t = vjp ? c->vt : c->ft;
   auto launch = [&](const PairLaunch& P) {
     return vjp ? launch_vjp(c->cfg.precision, P, c->stream) : launch_force(c->cfg.precision, P, c->stream);
@@ -611,6 +636,8 @@ nbody_status autotune(nbody_ctx* c, bool vjp) {
     pairs += n * n;
   }
   const bool large = pairs > kTuneLargePairs;
+  const char* verbose_env = getenv("NBODY_TUNE_VERBOSE");  // tuning log on stderr when set to 1
+  const bool verbose = verbose_env && verbose_env[0] == '1';
   double best = 1e300;
   Tiling bt = cands[0];
   for (const Tiling& t0 : cands) {
@@ -620,6 +647,10 @@ nbody_status autotune(nbody_ctx* c, bool vjp) {
     if ((s = install_tiling(c, t, vjp))) return s;
     double cost = 0;
     if ((s = time_tiling(c, vjp, &cost))) return s;
+    if (verbose)
+      fprintf(stderr, "nbody tune %s: variant=%d block=%d ipt=%d jtile=%d slice=%d ctas=%d items=%d -> %.4g ps/pair\n",
+              vjp ? "vjp" : "force", (vjp ? c->vt : c->ft).variant, t.block, t.ipt, t.jtile,
+              (vjp ? c->vt : c->ft).slice, (vjp ? c->vt : c->ft).n_ctas, vjp ? c->n_vitems : c->n_items, cost * 1e12);
     if (cost < best) best = cost, bt = t0;
   }
   // slice-length refinement around the automatic choice for the best tiling
@@ -637,6 +668,7 @@ nbody_status autotune(nbody_ctx* c, bool vjp) {
       if ((s = install_tiling(c, t, vjp))) return s;
       double cost = 0;
       if ((s = time_tiling(c, vjp, &cost))) return s;
+      if (verbose) fprintf(stderr, "nbody tune slice=%d -> %.4g ps/pair\n", L, cost * 1e12);
       if (cost < bc) bc = cost, bl = L;
     }
     bt = base;

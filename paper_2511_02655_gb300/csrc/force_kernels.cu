@@ -32,9 +32,9 @@ namespace {
 // rounded once. Such pairs are rare, so they are found without a branch per
 // pair: every pair folds its s^2 into a running minimum (one FMNMX), and after
 // each sub-block of kSub j-bodies a thread whose minimum fell below the radius
-// rescans that sub-block and, for each near pair, adds the refined
+// rescans that sub-block (s^2 only) and, for each near pair, adds the refined
 // contribution minus the unrefined one it accumulated in the first pass.
-constexpr int kSub = 32;
+constexpr int kSub = 16;
 
 __device__ __forceinline__ void refine_pair(const double* __restrict__ x64, const int i, const int j, const float eps2,
                                             float& dx, float& dy, float& dz, float& r2) {
@@ -284,15 +284,23 @@ __device__ __forceinline__ void tile_pass_f32x2(const float* tx, const float* ty
         quad_f32x2<R, MASK>(tx, ty, tz, tm, j, jt + j, ig, nx, ny, nz, e2, ax, ay, az, pp, mn0, mn1);
     }
     if (fminf(mn0, mn1) < r2c) {
-      for (int j = jb; j < min(jb + nb, nj); ++j) {
-        const float4 q = make_float4(tx[j], ty[j], tz[j], tm[j]);
+      // rescan two j-bodies at a time: packed s^2, scalar correction of the near ones
+      for (int j = jb; j < jb + nb; j += 2) {
+        const float2 xj = *reinterpret_cast<const float2*>(tx + j);
+        const float2 yj = *reinterpret_cast<const float2*>(ty + j);
+        const float2 zj = *reinterpret_cast<const float2*>(tz + j);
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-          float& cx = (j & 1) ? ax[r].y : ax[r].x;
-          float& cy = (j & 1) ? ay[r].y : ay[r].x;
-          float& cz = (j & 1) ? az[r].y : az[r].x;
-          float& cp = (j & 1) ? pp[r].y : pp[r].x;
-          correct_pair(q, jt + j, ig[r], i_end, -nx[r].x, -ny[r].x, -nz[r].x, e2.x, r2c, x64, cx, cy, cz, cp);
+          const float2 dx = __fadd2_rn(xj, nx[r]);
+          const float2 dy = __fadd2_rn(yj, ny[r]);
+          const float2 dz = __fadd2_rn(zj, nz[r]);
+          const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __ffma2_rn(dz, dz, e2)));
+          if (r2.x < r2c && j < nj)
+            correct_pair(make_float4(tx[j], ty[j], tz[j], tm[j]), jt + j, ig[r], i_end, -nx[r].x, -ny[r].x,
+                         -nz[r].x, e2.x, r2c, x64, ax[r].x, ay[r].x, az[r].x, pp[r].x);
+          if (r2.y < r2c && j + 1 < nj)
+            correct_pair(make_float4(tx[j + 1], ty[j + 1], tz[j + 1], tm[j + 1]), jt + j + 1, ig[r], i_end,
+                         -nx[r].x, -ny[r].x, -nz[r].x, e2.x, r2c, x64, ax[r].y, ay[r].y, az[r].y, pp[r].y);
         }
       }
     }
