@@ -69,7 +69,8 @@ typedef struct {
   int32_t energy_every; /* nbody_step records energies after every k-th step (0 = never) */
   int32_t block;        /* force kernel: threads per CTA, 128 or 256 (0 = autotune) */
   int32_t i_per_thread; /* force kernel: i-bodies kept in registers per thread, 1, 2 or 4 (0 = autotune) */
-  int32_t j_tile;       /* force kernel: j-bodies per shared-memory tile, 128 or 256 (0 = autotune) */
+  int32_t j_tile;       /* force kernel: j-bodies per shared-memory tile, 128 or 256 (512 too for
+                           NBODY_MIXED) (0 = autotune) */
   int32_t slice;        /* force kernel: j-bodies per work item, multiple of j_tile (0 = autotune) */
   uint32_t flags;       /* NBODY_FLAG_* */
   int32_t variant;      /* mixed force kernel: 1 = scalar float32, 2 = packed float32x2 (bit-identical

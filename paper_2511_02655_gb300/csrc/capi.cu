@@ -607,7 +607,9 @@ nbody_status autotune(nbody_ctx* c, bool vjp) {
   std::vector<Tiling> cands;
   const int blocks[] = {128, 256};
   const int ipts_f[] = {1, 2, 4}, ipts_v[] = {1, 2};
-  const int jts_f[] = {128, 256}, jts_v[] = {128};
+  const int jts_v[] = {128};
+  // j-tiles: 128 and 256 for every kernel, 512 for the mixed kernels
+  const std::vector<int> jts_f = g.precision == NBODY_MIXED ? std::vector<int>{128, 256, 512} : std::vector<int>{128, 256};
   std::vector<int> variants = {0};
   if (!vjp && g.precision == NBODY_MIXED) variants = g.variant ? std::vector<int>{g.variant - 1} : std::vector<int>{0, 1};
   for (int var : variants)
@@ -615,7 +617,7 @@ nbody_status autotune(nbody_ctx* c, bool vjp) {
       if (!vjp && g.block && g.block != b) continue;
       for (int r : (vjp ? std::vector<int>(ipts_v, ipts_v + 2) : std::vector<int>(ipts_f, ipts_f + 3))) {
         if (!vjp && g.i_per_thread && g.i_per_thread != r) continue;
-        for (int j : (vjp ? std::vector<int>(jts_v, jts_v + 1) : std::vector<int>(jts_f, jts_f + 2))) {
+        for (int j : (vjp ? std::vector<int>(jts_v, jts_v + 1) : jts_f)) {
           if (!vjp && g.j_tile && g.j_tile != j) continue;
           Tiling t;
           t.block = b, t.ipt = r, t.jtile = j, t.slice = vjp ? 0 : g.slice, t.variant = var;
@@ -690,7 +692,8 @@ nbody_status validate_cfg(const nbody_config* g) {
   if (g->precision == NBODY_FP64 && g->variant > 1) return NBODY_EINVAL;
   if (g->block && g->block != 128 && g->block != 256) return NBODY_EINVAL;
   if (g->i_per_thread && g->i_per_thread != 1 && g->i_per_thread != 2 && g->i_per_thread != 4) return NBODY_EINVAL;
-  if (g->j_tile && g->j_tile != 128 && g->j_tile != 256) return NBODY_EINVAL;
+  if (g->j_tile && g->j_tile != 128 && g->j_tile != 256 && g->j_tile != 512) return NBODY_EINVAL;
+  if (g->j_tile == 512 && g->precision != NBODY_MIXED) return NBODY_EINVAL;
   if (g->slice < 0) return NBODY_EINVAL;
   if (g->flags & ~(NBODY_FLAG_GRAPH | NBODY_FLAG_NOCHECK)) return NBODY_EINVAL;
   return NBODY_OK;

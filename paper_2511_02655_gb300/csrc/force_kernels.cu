@@ -131,7 +131,7 @@ __device__ __forceinline__ void tile_pass_f32(const float4* tile, const int jt, 
 template <int BLOCK, int R, int J>
 __global__ void __launch_bounds__(BLOCK) k_force_mixed(const PairLaunch L) {
   constexpr int LPT = (J + BLOCK - 1) / BLOCK;  // tile entries loaded per thread
-  __shared__ __align__(16) float4 tile[J];
+  __shared__ __align__(16) float4 tile[2][J];   // double buffer: one barrier per tile
   __shared__ int s_item;
   const float4* __restrict__ st = static_cast<const float4*>(L.stage_x);
   double4_32a* __restrict__ part = reinterpret_cast<double4_32a*>(L.part);
@@ -140,7 +140,7 @@ __global__ void __launch_bounds__(BLOCK) k_force_mixed(const PairLaunch L) {
   const double* __restrict__ x64 = L.x64;
 
   for (;;) {
-    const int it = next_item(L.counter, &s_item);
+    const int it = next_item(L.counter, &s_item);  // also a barrier: the buffers are free
     if (it >= L.n_items) break;
     const WorkItem w = L.items[it];
 
@@ -156,23 +156,20 @@ __global__ void __launch_bounds__(BLOCK) k_force_mixed(const PairLaunch L) {
       lx[r] = ly[r] = lz[r] = lp[r] = 0.f;
     }
 
-    float4 pre[LPT];
+    // first tile straight into buffer 0
 #pragma unroll
     for (int k = 0; k < LPT; ++k) {
-      const int jj = w.j_begin + (int)threadIdx.x + k * BLOCK;
-      if ((int)threadIdx.x + k * BLOCK < J && jj < w.j_end) pre[k] = st[jj];
+      const int t = (int)threadIdx.x + k * BLOCK;
+      if (t < J && w.j_begin + t < w.j_end) tile[0][t] = st[w.j_begin + t];
     }
+    __syncthreads();
 
-    for (int jt = w.j_begin; jt < w.j_end; jt += J) {
+    int buf = 0;
+    for (int jt = w.j_begin; jt < w.j_end; jt += J, buf ^= 1) {
       const int nj = min(J, w.j_end - jt);
-      __syncthreads();  // all threads are done reading the previous tile
-#pragma unroll
-      for (int k = 0; k < LPT; ++k) {
-        const int t = (int)threadIdx.x + k * BLOCK;
-        if (t < nj) tile[t] = pre[k];
-      }
-      __syncthreads();
-      if (jt + J < w.j_end) {  // prefetch the next tile while this one is consumed
+      const bool more = jt + J < w.j_end;
+      float4 pre[LPT];
+      if (more) {  // next tile's loads are in flight while this one is consumed
 #pragma unroll
         for (int k = 0; k < LPT; ++k) {
           const int jj = jt + J + (int)threadIdx.x + k * BLOCK;
@@ -185,9 +182,9 @@ __global__ void __launch_bounds__(BLOCK) k_force_mixed(const PairLaunch L) {
       for (int r = 0; r < R; ++r) ax[r] = ay[r] = az[r] = pp[r] = 0.f;
       const bool diag = (jt < w.i_end) && (w.i_begin < jt + nj);
       if (diag)
-        tile_pass_f32<R, true>(tile, jt, nj, xi, yi, zi, ig, w.i_end, eps2, r2c, x64, ax, ay, az, pp);
+        tile_pass_f32<R, true>(tile[buf], jt, nj, xi, yi, zi, ig, w.i_end, eps2, r2c, x64, ax, ay, az, pp);
       else
-        tile_pass_f32<R, false>(tile, jt, nj, xi, yi, zi, ig, w.i_end, eps2, r2c, x64, ax, ay, az, pp);
+        tile_pass_f32<R, false>(tile[buf], jt, nj, xi, yi, zi, ig, w.i_end, eps2, r2c, x64, ax, ay, az, pp);
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         two_sum_acc(hx[r], lx[r], ax[r]);
@@ -195,6 +192,14 @@ __global__ void __launch_bounds__(BLOCK) k_force_mixed(const PairLaunch L) {
         two_sum_acc(hz[r], lz[r], az[r]);
         two_sum_acc(hp[r], lp[r], pp[r]);
       }
+      if (more) {  // the other buffer was last read before the previous barrier
+#pragma unroll
+        for (int k = 0; k < LPT; ++k) {
+          const int t = (int)threadIdx.x + k * BLOCK;
+          if (t < J && jt + J + t < w.j_end) tile[buf ^ 1][t] = pre[k];
+        }
+      }
+      __syncthreads();
     }
 
     double4_32a* out = part + (int64_t)w.slice * L.n_total;
@@ -311,10 +316,10 @@ template <int BLOCK, int R, int J>
 __global__ void __launch_bounds__(BLOCK) k_force_mixed2(const PairLaunch L) {
   static_assert(J % 4 == 0, "tiles hold whole quads of j-bodies");
   constexpr int LPT = (J + BLOCK - 1) / BLOCK;
-  __shared__ __align__(16) float tx[J];
-  __shared__ __align__(16) float ty[J];
-  __shared__ __align__(16) float tz[J];
-  __shared__ __align__(16) float tm[J];
+  __shared__ __align__(16) float tx[2][J];  // double buffer: one barrier per tile
+  __shared__ __align__(16) float ty[2][J];
+  __shared__ __align__(16) float tz[2][J];
+  __shared__ __align__(16) float tm[2][J];
   __shared__ int s_item;
   const float4* __restrict__ st = static_cast<const float4*>(L.stage_x);
   double4_32a* __restrict__ part = reinterpret_cast<double4_32a*>(L.part);
@@ -324,7 +329,7 @@ __global__ void __launch_bounds__(BLOCK) k_force_mixed2(const PairLaunch L) {
   const double* __restrict__ x64 = L.x64;
 
   for (;;) {
-    const int it = next_item(L.counter, &s_item);
+    const int it = next_item(L.counter, &s_item);  // also a barrier: the buffers are free
     if (it >= L.n_items) break;
     const WorkItem w = L.items[it];
 
@@ -342,28 +347,28 @@ __global__ void __launch_bounds__(BLOCK) k_force_mixed2(const PairLaunch L) {
       lx[r] = ly[r] = lz[r] = lp[r] = 0.f;
     }
 
-    float4 pre[LPT];
-#pragma unroll
-    for (int k = 0; k < LPT; ++k) {
-      const int jj = w.j_begin + (int)threadIdx.x + k * BLOCK;
-      if ((int)threadIdx.x + k * BLOCK < J && jj < w.j_end) pre[k] = st[jj];
-    }
-
-    for (int jt = w.j_begin; jt < w.j_end; jt += J) {
-      const int nj = min(J, w.j_end - jt);
-      const int nj4 = (nj + 3) & ~3;
-      __syncthreads();
+    // first tile straight into buffer 0 (padded to a whole quad with far, massless bodies)
+    {
+      const int nj = min(J, w.j_end - w.j_begin), nj4 = (nj + 3) & ~3;
 #pragma unroll
       for (int k = 0; k < LPT; ++k) {
         const int t = (int)threadIdx.x + k * BLOCK;
         if (t < nj) {
-          tx[t] = pre[k].x, ty[t] = pre[k].y, tz[t] = pre[k].z, tm[t] = pre[k].w;
+          const float4 q = st[w.j_begin + t];
+          tx[0][t] = q.x, ty[0][t] = q.y, tz[0][t] = q.z, tm[0][t] = q.w;
         } else if (t < nj4) {
-          tx[t] = kFarAway, ty[t] = kFarAway, tz[t] = kFarAway, tm[t] = 0.f;
+          tx[0][t] = kFarAway, ty[0][t] = kFarAway, tz[0][t] = kFarAway, tm[0][t] = 0.f;
         }
       }
-      __syncthreads();
-      if (jt + J < w.j_end) {
+    }
+    __syncthreads();
+
+    int buf = 0;
+    for (int jt = w.j_begin; jt < w.j_end; jt += J, buf ^= 1) {
+      const int nj = min(J, w.j_end - jt);
+      const bool more = jt + J < w.j_end;
+      float4 pre[LPT];
+      if (more) {
 #pragma unroll
         for (int k = 0; k < LPT; ++k) {
           const int jj = jt + J + (int)threadIdx.x + k * BLOCK;
@@ -376,9 +381,11 @@ __global__ void __launch_bounds__(BLOCK) k_force_mixed2(const PairLaunch L) {
       for (int r = 0; r < R; ++r) ax[r] = ay[r] = az[r] = pp[r] = make_float2(0.f, 0.f);
       const bool diag = (jt < w.i_end) && (w.i_begin < jt + nj);
       if (diag)
-        tile_pass_f32x2<R, true>(tx, ty, tz, tm, jt, nj, ig, nx, ny, nz, w.i_end, e2, r2c, x64, ax, ay, az, pp);
+        tile_pass_f32x2<R, true>(tx[buf], ty[buf], tz[buf], tm[buf], jt, nj, ig, nx, ny, nz, w.i_end, e2, r2c, x64,
+                                 ax, ay, az, pp);
       else
-        tile_pass_f32x2<R, false>(tx, ty, tz, tm, jt, nj, ig, nx, ny, nz, w.i_end, e2, r2c, x64, ax, ay, az, pp);
+        tile_pass_f32x2<R, false>(tx[buf], ty[buf], tz[buf], tm[buf], jt, nj, ig, nx, ny, nz, w.i_end, e2, r2c,
+                                  x64, ax, ay, az, pp);
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         two_sum_acc(hx[r], lx[r], ax[r].x + ax[r].y);
@@ -386,6 +393,20 @@ __global__ void __launch_bounds__(BLOCK) k_force_mixed2(const PairLaunch L) {
         two_sum_acc(hz[r], lz[r], az[r].x + az[r].y);
         two_sum_acc(hp[r], lp[r], pp[r].x + pp[r].y);
       }
+      if (more) {  // the other buffer was last read before the previous barrier
+        const int nn = min(J, w.j_end - jt - J), nn4 = (nn + 3) & ~3;
+        const int b = buf ^ 1;
+#pragma unroll
+        for (int k = 0; k < LPT; ++k) {
+          const int t = (int)threadIdx.x + k * BLOCK;
+          if (t < nn) {
+            tx[b][t] = pre[k].x, ty[b][t] = pre[k].y, tz[b][t] = pre[k].z, tm[b][t] = pre[k].w;
+          } else if (t < nn4) {
+            tx[b][t] = kFarAway, ty[b][t] = kFarAway, tz[b][t] = kFarAway, tm[b][t] = 0.f;
+          }
+        }
+      }
+      __syncthreads();
     }
 
     double4_32a* out = part + (int64_t)w.slice * L.n_total;
@@ -498,34 +519,36 @@ int occupancy_of(K kern, int block) {
   return n;
 }
 
-// Tilings compiled: BLOCK in {128, 256}, R in {1, 2, 4}, J in {128, 256}
-// (the packed mixed kernel, variant 1, for R in {1, 2, 4} too).
+// Tilings compiled: BLOCK in {128, 256}, R in {1, 2, 4}, J in {128, 256} for
+// every kernel, and J = 512 for the two mixed kernels.
 #define NBODY_FORCE_TILINGS(X) \
   X(128, 1, 128) X(128, 2, 128) X(128, 4, 128) X(128, 1, 256) X(128, 2, 256) X(128, 4, 256) \
   X(256, 1, 128) X(256, 2, 128) X(256, 4, 128) X(256, 1, 256) X(256, 2, 256) X(256, 4, 256)
-#define NBODY_PACKED_TILINGS(X) NBODY_FORCE_TILINGS(X)
+#define NBODY_MIXED_TILINGS(X) \
+  NBODY_FORCE_TILINGS(X) X(128, 1, 512) X(128, 2, 512) X(128, 4, 512) X(256, 1, 512) X(256, 2, 512) X(256, 4, 512)
 
 }  // namespace
 
 cudaError_t launch_force(int precision, const PairLaunch& L, cudaStream_t st) {
   if (L.n_ctas <= 0) return cudaErrorInvalidConfiguration;
-  if (precision == 1 && L.variant == 1) {
+  if (precision == 1) {
 #define NBODY_X(B, R, J)                                               \
   if (L.block == B && L.ipt == R && L.jtile == J) {                    \
-    k_force_mixed2<B, R, J><<<L.n_ctas, B, 0, st>>>(L);                \
+    if (L.variant == 1)                                                \
+      k_force_mixed2<B, R, J><<<L.n_ctas, B, 0, st>>>(L);              \
+    else                                                               \
+      k_force_mixed<B, R, J><<<L.n_ctas, B, 0, st>>>(L);               \
     return cudaGetLastError();                                         \
   }
-    NBODY_PACKED_TILINGS(NBODY_X)
+    if (L.variant != 0 && L.variant != 1) return cudaErrorInvalidConfiguration;
+    NBODY_MIXED_TILINGS(NBODY_X)
 #undef NBODY_X
     return cudaErrorInvalidConfiguration;
   }
   if (L.variant != 0) return cudaErrorInvalidConfiguration;
 #define NBODY_X(B, R, J)                                               \
   if (L.block == B && L.ipt == R && L.jtile == J) {                    \
-    if (precision == 1)                                                \
-      k_force_mixed<B, R, J><<<L.n_ctas, B, 0, st>>>(L);               \
-    else                                                               \
-      k_force_fp64<B, R, J><<<L.n_ctas, B, 0, st>>>(L);                \
+    k_force_fp64<B, R, J><<<L.n_ctas, B, 0, st>>>(L);                  \
     return cudaGetLastError();                                         \
   }
   NBODY_FORCE_TILINGS(NBODY_X)
@@ -534,17 +557,18 @@ cudaError_t launch_force(int precision, const PairLaunch& L, cudaStream_t st) {
 }
 
 int force_ctas_per_sm(int precision, int variant, int block, int ipt, int jtile) {
-  if (precision == 1 && variant == 1) {
-#define NBODY_X(B, R, J) \
-  if (block == B && ipt == R && jtile == J) return occupancy_of(k_force_mixed2<B, R, J>, B);
-    NBODY_PACKED_TILINGS(NBODY_X)
+  if (precision == 1) {
+    if (variant != 0 && variant != 1) return 0;
+#define NBODY_X(B, R, J)                                                                          \
+  if (block == B && ipt == R && jtile == J)                                                       \
+    return variant == 1 ? occupancy_of(k_force_mixed2<B, R, J>, B) : occupancy_of(k_force_mixed<B, R, J>, B);
+    NBODY_MIXED_TILINGS(NBODY_X)
 #undef NBODY_X
     return 0;
   }
   if (variant != 0) return 0;
-#define NBODY_X(B, R, J)                                                                     \
-  if (block == B && ipt == R && jtile == J)                                                  \
-    return precision == 1 ? occupancy_of(k_force_mixed<B, R, J>, B) : occupancy_of(k_force_fp64<B, R, J>, B);
+#define NBODY_X(B, R, J) \
+  if (block == B && ipt == R && jtile == J) return occupancy_of(k_force_fp64<B, R, J>, B);
   NBODY_FORCE_TILINGS(NBODY_X)
 #undef NBODY_X
   return 0;
