@@ -15,6 +15,9 @@ Sec. II-A and Sec. V-B, Sec. VI):
 * ``kdk``         leapfrog kick-drift-kick steps, one force evaluation per step
 * ``force_vjp``   w -> (dL/dx, dL/dm) through a(x, m) for dL/da = w
 * ``adjoint``     gradients of a final-state loss w.r.t. x0, v0, m through KDK
+* ``lj_*``         the same for the paper's Lennard-Jones pair law (Eq. 1):
+                   a_i = F_i / m_i, phi_i = sum_j V(r_ij) / m_i, and KDK with
+                   reflecting walls of the box [0, box]^3
 """
 
 from __future__ import annotations
@@ -58,8 +61,13 @@ def _load():
             lib.oracle_kdk.argtypes = [i64, p, p, p, d, d, d, i32, p, i32, i32, p, i32]
             lib.oracle_force_vjp.argtypes = [i64, p, p, p, d, d, p, p, i32]
             lib.oracle_adjoint.argtypes = [i64, p, p, p, d, d, d, i32, p, p, p, p, p, i32]
+            lib.oracle_lj_forces.argtypes = [i64, p, p, d, d, d, p, p, i32]
+            lib.oracle_lj_forces_at.argtypes = [i64, p, p, d, d, d, p, i64, p, p, i32]
+            lib.oracle_lj_energy.argtypes = [i64, p, p, p, d, d, d, p, i32]
+            lib.oracle_lj_kdk.argtypes = [i64, p, p, p, d, d, d, d, d, i32, p, i32, i32, p, i32]
             for f in ("oracle_forces", "oracle_forces_at", "oracle_energy", "oracle_kdk",
-                      "oracle_force_vjp", "oracle_adjoint"):
+                      "oracle_force_vjp", "oracle_adjoint", "oracle_lj_forces", "oracle_lj_forces_at",
+                      "oracle_lj_energy", "oracle_lj_kdk"):
                 getattr(lib, f).restype = i32
             _lib = lib
     return _lib
@@ -165,3 +173,51 @@ def trajectory_loss(x0, v0, m, G, eps, dt, n_steps, target, threads=0):
     """L = sum_i |x_i(T) - t_i|^2 after n_steps KDK steps from (x0, v0)."""
     xT, _, _, _ = kdk(x0, v0, m, G, eps, dt, n_steps, threads=threads)
     return float(((xT - target) ** 2).sum())
+
+
+def lj_forces(x, m, eps_lj=1.0, sigma=1.0, soft=0.0, threads=0):
+    """Lennard-Jones accelerations a [N,3] and potentials per unit mass phi [N]."""
+    m = _f64(m)
+    n = m.shape[0]
+    x = _f64(x, (n, 3))
+    a, phi = np.zeros((n, 3)), np.zeros(n)
+    _check(_load().oracle_lj_forces(n, _ptr(x), _ptr(m), eps_lj, sigma, soft, _ptr(a), _ptr(phi), threads),
+           "oracle_lj_forces")
+    return a, phi
+
+
+def lj_forces_at(x, m, idx, eps_lj=1.0, sigma=1.0, soft=0.0, threads=0):
+    m = _f64(m)
+    n = m.shape[0]
+    x = _f64(x, (n, 3))
+    idx = np.ascontiguousarray(idx, dtype=np.int64)
+    k = idx.shape[0]
+    a, phi = np.zeros((k, 3)), np.zeros(k)
+    _check(_load().oracle_lj_forces_at(n, _ptr(x), _ptr(m), eps_lj, sigma, soft, _ptr(idx), k, _ptr(a), _ptr(phi),
+                                       threads), "oracle_lj_forces_at")
+    return a, phi
+
+
+def lj_energy(x, v, m, eps_lj=1.0, sigma=1.0, soft=0.0, threads=0):
+    """[E, K, U, Px, Py, Pz, Lx, Ly, Lz] with U the Lennard-Jones pair sum."""
+    m = _f64(m)
+    n = m.shape[0]
+    x, v = _f64(x, (n, 3)), _f64(v, (n, 3))
+    out = np.zeros(9)
+    _check(_load().oracle_lj_energy(n, _ptr(x), _ptr(v), _ptr(m), eps_lj, sigma, soft, _ptr(out), threads),
+           "oracle_lj_energy")
+    return out
+
+
+def lj_kdk(x, v, m, eps_lj, sigma, soft, box, dt, n_steps, a=None, energy_every=0, threads=0):
+    """KDK leapfrog of the Lennard-Jones gas with reflecting walls (box > 0); returns (x, v, a, log)."""
+    m = _f64(m)
+    n = m.shape[0]
+    x, v = _f64(x, (n, 3)).copy(), _f64(v, (n, 3)).copy()
+    a_valid = a is not None
+    a = _f64(a, (n, 3)).copy() if a_valid else np.zeros((n, 3))
+    nrec = n_steps // energy_every if energy_every > 0 else 0
+    log = np.zeros((nrec, 9)) if nrec else None
+    _check(_load().oracle_lj_kdk(n, _ptr(x), _ptr(v), _ptr(m), eps_lj, sigma, soft, box, dt, int(n_steps),
+                                 _ptr(a), int(a_valid), int(energy_every), _ptr(log), threads), "oracle_lj_kdk")
+    return x, v, a, log

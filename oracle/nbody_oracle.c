@@ -349,3 +349,169 @@ int oracle_adjoint(int64_t n, const double* x0, const double* v0, const double* 
   free(traj), free(v), free(a), free(gx), free(gmv), free(lam_vh);
   return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Lennard-Jones gas (the paper's pair law, Eq. 1)                            */
+/*
+ *   V(r) = 4 eps_lj [ (sigma / r)^12 - (sigma / r)^6 ]
+ *   F_i  = -dV/dx_i = 24 eps_lj [ 2 sigma^12 / r^14 - sigma^6 / r^8 ] (x_i - x_j)
+ * summed over every j != i (no cutoff: all N^2 pairs, Sec. V-B). Accelerations
+ * are F_i / m_i; phi_i = sum_{j != i} V(r_ij) / m_i (potential energy per unit
+ * mass of body i, so that U = 1/2 sum m_i phi_i = sum_{i<j} V(r_ij)).
+ * r^2 may be softened as r^2 + soft^2 (soft = 0 gives the plain law).
+ */
+static void body_force_lj(int64_t n, const double* x, const double* m, double eps_lj, double sigma, double soft,
+                          int64_t i, double* ai, double* phii) {
+  double fx = 0.0, fy = 0.0, fz = 0.0, v = 0.0;
+  const double s2 = sigma * sigma;
+  for (int64_t j = 0; j < n; ++j) {
+    if (j == i) continue;
+    double dx = x[3 * i + 0] - x[3 * j + 0]; /* x_i - x_j */
+    double dy = x[3 * i + 1] - x[3 * j + 1];
+    double dz = x[3 * i + 2] - x[3 * j + 2];
+    double r2 = dx * dx + dy * dy + dz * dz + soft * soft;
+    double sr2 = s2 / r2;
+    double sr6 = sr2 * sr2 * sr2;
+    double sr12 = sr6 * sr6;
+    double coef = 24.0 * eps_lj * (2.0 * sr12 - sr6) / r2; /* 24 eps [2 s^12/r^14 - s^6/r^8] */
+    fx += coef * dx;
+    fy += coef * dy;
+    fz += coef * dz;
+    v += 4.0 * eps_lj * (sr12 - sr6);
+  }
+  ai[0] = fx / m[i];
+  ai[1] = fy / m[i];
+  ai[2] = fz / m[i];
+  if (phii) *phii = v / m[i];
+}
+
+typedef struct {
+  int64_t n;
+  const double *x, *m;
+  double eps_lj, sigma, soft;
+  const int64_t* idx;
+  double *a, *phi;
+} lj_args;
+
+static void lj_rows(int64_t lo, int64_t hi, void* p) {
+  lj_args* f = (lj_args*)p;
+  for (int64_t r = lo; r < hi; ++r) {
+    int64_t i = f->idx ? f->idx[r] : r;
+    body_force_lj(f->n, f->x, f->m, f->eps_lj, f->sigma, f->soft, i, f->a + 3 * r, f->phi ? f->phi + r : NULL);
+  }
+}
+
+int oracle_lj_forces(int64_t n, const double* x, const double* m, double eps_lj, double sigma, double soft,
+                     double* a, double* phi, int nthreads) {
+  if (n < 0 || (n > 0 && (!x || !m || !a))) return 1;
+  lj_args f = {n, x, m, eps_lj, sigma, soft, NULL, a, phi};
+  parallel_rows(n, nthreads, lj_rows, &f);
+  return 0;
+}
+
+int oracle_lj_forces_at(int64_t n, const double* x, const double* m, double eps_lj, double sigma, double soft,
+                        const int64_t* idx, int64_t k, double* a, double* phi, int nthreads) {
+  if (n < 0 || k < 0 || (k > 0 && (!x || !m || !a || !idx))) return 1;
+  for (int64_t r = 0; r < k; ++r)
+    if (idx[r] < 0 || idx[r] >= n) return 1;
+  lj_args f = {n, x, m, eps_lj, sigma, soft, idx, a, phi};
+  parallel_rows(k, nthreads, lj_rows, &f);
+  return 0;
+}
+
+typedef struct {
+  int64_t n;
+  const double* x;
+  double eps_lj, sigma, soft;
+  double* row_u;
+} lj_pot_args;
+
+static void lj_pot_rows(int64_t lo, int64_t hi, void* p) {
+  lj_pot_args* f = (lj_pot_args*)p;
+  const double s2 = f->sigma * f->sigma;
+  for (int64_t i = lo; i < hi; ++i) {
+    csum u = {0.0, 0.0};
+    for (int64_t j = i + 1; j < f->n; ++j) {
+      double dx = f->x[3 * j + 0] - f->x[3 * i + 0];
+      double dy = f->x[3 * j + 1] - f->x[3 * i + 1];
+      double dz = f->x[3 * j + 2] - f->x[3 * i + 2];
+      double sr2 = s2 / (dx * dx + dy * dy + dz * dz + f->soft * f->soft);
+      double sr6 = sr2 * sr2 * sr2;
+      csum_add(&u, 4.0 * f->eps_lj * (sr6 * sr6 - sr6));
+    }
+    f->row_u[i] = csum_get(&u);
+  }
+}
+
+/* out[9] = {E, K, U, Px, Py, Pz, Lx, Ly, Lz} with U = sum_{i<j} V(r_ij). */
+int oracle_lj_energy(int64_t n, const double* x, const double* v, const double* m, double eps_lj, double sigma,
+                     double soft, double* out, int nthreads) {
+  if (n < 0 || !out || (n > 0 && (!x || !v || !m))) return 1;
+  double* row_u = (double*)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+  if (!row_u) return 2;
+  lj_pot_args f = {n, x, eps_lj, sigma, soft, row_u};
+  parallel_rows(n, nthreads, lj_pot_rows, &f);
+  csum K = {0, 0}, U = {0, 0}, P[3] = {{0, 0}, {0, 0}, {0, 0}}, L[3] = {{0, 0}, {0, 0}, {0, 0}};
+  for (int64_t i = 0; i < n; ++i) {
+    const double* xi = x + 3 * i;
+    const double* vi = v + 3 * i;
+    csum_add(&K, 0.5 * m[i] * (vi[0] * vi[0] + vi[1] * vi[1] + vi[2] * vi[2]));
+    csum_add(&U, row_u[i]);
+    for (int c = 0; c < 3; ++c) csum_add(&P[c], m[i] * vi[c]);
+    csum_add(&L[0], m[i] * (xi[1] * vi[2] - xi[2] * vi[1]));
+    csum_add(&L[1], m[i] * (xi[2] * vi[0] - xi[0] * vi[2]));
+    csum_add(&L[2], m[i] * (xi[0] * vi[1] - xi[1] * vi[0]));
+  }
+  free(row_u);
+  out[1] = csum_get(&K);
+  out[2] = csum_get(&U);
+  out[0] = out[1] + out[2];
+  for (int c = 0; c < 3; ++c) {
+    out[3 + c] = csum_get(&P[c]);
+    out[6 + c] = csum_get(&L[c]);
+  }
+  return 0;
+}
+
+/*
+ * Reflecting walls of the box [0, box]^3 ("boundary checking", Fig. 3/4
+ * captions): after the drift, a coordinate that left the box is mirrored back
+ * across the wall it crossed and that velocity component changes sign
+ * (specular reflection; repeated while it is still outside, for large steps).
+ */
+static void reflect(double* xc, double* vc, double box) {
+  for (int guard = 0; guard < 64; ++guard) {
+    if (*xc < 0.0) {
+      *xc = -*xc;
+      *vc = -*vc;
+    } else if (*xc > box) {
+      *xc = 2.0 * box - *xc;
+      *vc = -*vc;
+    } else {
+      return;
+    }
+  }
+}
+
+/* KDK leapfrog for the Lennard-Jones gas, with reflecting walls when box > 0. */
+int oracle_lj_kdk(int64_t n, double* x, double* v, const double* m, double eps_lj, double sigma, double soft,
+                  double box, double dt, int n_steps, double* a, int a_valid, int energy_every, double* energy_log,
+                  int nthreads) {
+  if (n < 0 || n_steps < 0 || (n > 0 && (!x || !v || !m || !a))) return 1;
+  if (!a_valid) oracle_lj_forces(n, x, m, eps_lj, sigma, soft, a, NULL, nthreads);
+  int rec = 0;
+  for (int s = 0; s < n_steps; ++s) {
+    for (int64_t k = 0; k < 3 * n; ++k) v[k] += 0.5 * dt * a[k];
+    for (int64_t k = 0; k < 3 * n; ++k) x[k] += dt * v[k];
+    if (box > 0.0)
+      for (int64_t k = 0; k < 3 * n; ++k) reflect(&x[k], &v[k], box);
+    oracle_lj_forces(n, x, m, eps_lj, sigma, soft, a, NULL, nthreads);
+    for (int64_t k = 0; k < 3 * n; ++k) v[k] += 0.5 * dt * a[k];
+    if (energy_every > 0 && energy_log && (s + 1) % energy_every == 0) {
+      int rc = oracle_lj_energy(n, x, v, m, eps_lj, sigma, soft, energy_log + 9 * rec, nthreads);
+      if (rc) return rc;
+      ++rec;
+    }
+  }
+  return 0;
+}

@@ -20,6 +20,9 @@ self-gravitating Plummer spheres instead, in units G = M = a = 1:
 * ``ensemble``      -- many independent Plummer systems with sizes drawn
                        log-uniformly in [n_min, n_max].
 * ``kepler_pair``   -- an isolated two-body orbit with a closed-form solution.
+* ``lj_gas``        -- the paper's own system (Sec. II-A): a Lennard-Jones gas in
+                       reduced units, lattice start inside a cubic box, Maxwell
+                       velocities.
 
 All state is float64, shaped ``[N, 3]`` (positions, velocities) and ``[N]``
 (masses), C-contiguous.
@@ -194,3 +197,26 @@ def targets(n: int, seed: int) -> np.ndarray:
     """Per-body target points t_i ~ N(0, 1)^3 for the final-position loss."""
     rng = np.random.default_rng(seed)
     return np.ascontiguousarray(rng.standard_normal((n, 3)))
+
+
+def lj_gas(n: int, seed: int, *, density: float = 0.05, temperature: float = 2.0, mass: float = 1.0,
+           jitter: float = 0.1):
+    """A Lennard-Jones gas in reduced units (sigma = epsilon = k_B = 1) in the cube [0, box]^3.
+
+    box = (n / density)^{1/3}. Bodies start on the first n sites of a simple
+    cubic lattice of spacing box / ceil(n^{1/3}) (offset by half a spacing,
+    each displaced uniformly by up to +-jitter spacings), with Maxwell
+    velocities at the given temperature, the centre-of-mass velocity removed.
+    Returns ``(x, v, m, box)``.
+    """
+    rng = np.random.default_rng(seed)
+    box = (n / density) ** (1.0 / 3.0)
+    k = int(math.ceil(n ** (1.0 / 3.0) - 1e-9))
+    h = box / k
+    g = np.arange(k)
+    lat = np.stack(np.meshgrid(g, g, g, indexing="ij"), axis=-1).reshape(-1, 3)[:n].astype(np.float64)
+    x = (lat + 0.5 + rng.uniform(-jitter, jitter, (n, 3))) * h
+    v = rng.standard_normal((n, 3)) * math.sqrt(temperature / mass)
+    v -= v.mean(axis=0)
+    m = np.full(n, mass)
+    return np.ascontiguousarray(x), np.ascontiguousarray(v), m, box

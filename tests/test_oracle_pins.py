@@ -318,3 +318,83 @@ def test_adjoint_matches_finite_differences():
         mm_[k] -= h
         fd = (L(x0, v0, mp) - L(x0, v0, mm_)) / (2 * h)
         assert abs(fd - gm[k]) <= 1e-7 * max(abs(fd), np.abs(gm).max() * 1e-2), (k, fd, gm[k])
+
+
+# --------------------------------------------------------------------------------------
+# Lennard-Jones gas (the paper's pair law, Eq. 1)
+
+
+def test_lj_forces_match_symbolic_gradient():
+    sp = pytest.importorskip("sympy")
+    X = sp.Matrix(3, 3, lambda i, c: sp.Symbol(f"x{i}{c}"))
+    eps_lj, sig = sp.Rational(3, 2), sp.Rational(4, 5)
+    U = 0
+    for i in range(3):
+        for j in range(i + 1, 3):
+            r2 = sum((X[j, c] - X[i, c]) ** 2 for c in range(3))
+            U += 4 * eps_lj * ((sig ** 2 / r2) ** 6 - (sig ** 2 / r2) ** 3)
+    xs = [[sp.Rational(1, 3), sp.Rational(-1, 2), sp.Rational(1, 5)],
+          [sp.Rational(-2, 7), sp.Rational(3, 4), sp.Rational(0)],
+          [sp.Rational(5, 6), sp.Rational(1, 8), sp.Rational(-3, 5)]]
+    ms = [2.0, 0.5, 1.25]
+    subs = {X[i, c]: xs[i][c] for i in range(3) for c in range(3)}
+    F = np.array([[float(sp.N(-sp.diff(U, X[i, c]).subs(subs), 30)) for c in range(3)] for i in range(3)])
+    Uv = float(sp.N(U.subs(subs), 30))
+    x = np.array(xs, dtype=float)
+    a, phi = oracle.lj_forces(x, ms, eps_lj=1.5, sigma=0.8, threads=1)
+    np.testing.assert_allclose(a * np.array(ms)[:, None], F, rtol=1e-12, atol=1e-12 * np.abs(F).max())
+    assert abs(0.5 * (np.array(ms) * phi).sum() - Uv) <= 1e-12 * abs(Uv)
+    E = oracle.lj_energy(x, np.zeros((3, 3)), ms, eps_lj=1.5, sigma=0.8)
+    assert abs(E[2] - Uv) <= 1e-12 * abs(Uv)
+
+
+def test_lj_pair_minimum_and_zero_crossing():
+    # V has its minimum -eps at r = 2^{1/6} sigma (zero force) and crosses zero at r = sigma
+    sig, e = 1.3, 0.7
+    for r, V, sign in ((2 ** (1 / 6) * sig, -e, 0), (sig, 0.0, +1), (1.5 * sig, None, -1)):
+        x = np.array([[0.0, 0.0, 0.0], [r, 0.0, 0.0]])
+        a, phi = oracle.lj_forces(x, [1.0, 1.0], eps_lj=e, sigma=sig)
+        if V is not None:
+            assert abs(phi[0] - V) <= 1e-14
+        if sign == 0:
+            assert np.abs(a).max() <= 1e-12
+        else:  # repulsive inside the minimum (body 0 pushed to -x), attractive outside
+            assert np.sign(-a[0, 0]) == sign
+
+
+def test_lj_newton_third_law_and_energy_drift_order():
+    x, v, m, box = inputs.lj_gas(64, seed=3, density=0.2, temperature=1.0)
+    m = m * np.exp(0.2 * np.random.default_rng(2).standard_normal(64))
+    a, _ = oracle.lj_forces(x, m)
+    assert np.abs((m[:, None] * a).sum(0)).max() <= 1e-12 * (m[:, None] * np.abs(a)).sum()
+    E0 = oracle.lj_energy(x, v, m)[0]
+    drifts = []
+    for dt in (2e-3, 1e-3):
+        n = int(round(0.2 / dt))
+        _, _, _, log = oracle.lj_kdk(x, v, m, 1.0, 1.0, 0.0, 0.0, dt, n, energy_every=1)
+        drifts.append(np.abs(log[:, 0] - E0).max() / abs(E0))
+    assert 3.0 < drifts[0] / drifts[1] < 5.0, drifts
+
+
+def test_lj_reflecting_walls_free_particle():
+    # two far-apart, effectively free particles bouncing in a box: triangle-wave closed form
+    box, dt, n = 10.0, 1e-3, 7000
+    x = np.array([[1.0, 2.0, 3.0], [9.0, 8.0, 7.0]])
+    v = np.array([[3.0, -1.7, 0.9], [-2.2, 0.5, 4.1]])
+    xf, vf, _, _ = oracle.lj_kdk(x, v, [1.0, 1.0], 1e-30, 1.0, 0.0, box, dt, n)
+    t = dt * n
+    u = np.mod(x + v * t, 2 * box)
+    xe = np.where(u > box, 2 * box - u, u)
+    ve = np.where(u > box, -v, v)
+    np.testing.assert_allclose(xf, xe, atol=1e-9)
+    np.testing.assert_allclose(vf, ve, atol=1e-12)
+
+
+def test_lj_gas_generator():
+    x, v, m, box = inputs.lj_gas(1000, seed=1, density=0.05, temperature=2.0)
+    assert abs(box - (1000 / 0.05) ** (1 / 3)) < 1e-12
+    assert x.min() > 0 and x.max() < box
+    np.testing.assert_allclose(v.mean(0), 0.0, atol=1e-12)
+    assert abs((v ** 2).mean() - 2.0) < 0.15
+    d = np.linalg.norm(x[:, None, :] - x[None, :, :], axis=-1) + np.eye(1000) * 1e9
+    assert d.min() > 0.5  # no overlapping pairs at the start
