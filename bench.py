@@ -247,6 +247,31 @@ def aux_measurements(dev):
                            "fp64_per_system_interactions_per_s": pairs / sec64,
                            "graph_over_fp64_per_system": (pairs * 50 / sec) / (pairs / sec64),
                            "pairs_per_step": pairs, "launches_per_50_steps": int(launches)}
+    # the paper's own system: Lennard-Jones gas, 10 000 particles, 2500 KDK steps with the total
+    # energy reduced every step, reflecting walls (reduced units, density 0.05, T = 2, dt = 5e-3)
+    n, steps = 10000, 2500
+    x, v, m, box = inputs.lj_gas(n, seed=9)
+    lj = {}
+    for prec, flags, name in ((nb.MIXED, nb.FLAG_GRAPH, "mixed_graph"), (nb.FP64, 0, "fp64")):
+        ctx = nb.nbody_init(law=nb.LENNARD_JONES, precision=prec, n=n, dt=5e-3, box=box, energy_every=1,
+                            flags=flags)
+        xt, vt, mt = (torch.from_numpy(a).to(dev) for a in (x, v, m))
+        at = torch.empty_like(xt)
+        logt = torch.empty((steps, 1, 9), dtype=torch.float64, device=dev)
+        if flags:  # capture once on a copy of the state, replay on the real one
+            x2, v2, a2 = xt.clone(), vt.clone(), torch.empty_like(xt)
+            nb.nbody_step(ctx, x2, v2, mt, a2, False, steps, logt)
+            nb.nbody_sync(ctx)
+            x2.copy_(xt), v2.copy_(vt)
+            xt, vt, at = x2, v2, a2
+        sec = _event_time(lambda: nb.nbody_step(ctx, xt, vt, mt, at, False, steps, logt), stream)
+        nb.nbody_sync(ctx)
+        e = logt.cpu().numpy()[:, 0, 0]
+        lj[name] = {"seconds": sec, "interactions_per_s": float(n) * n * (steps + 1) / sec,
+                    "energy_drift_max_rel": float(np.abs(e - e[0]).max() / abs(e[0]))}
+        ctx.close()
+    out["paper_lj_gas_10000x2500"] = dict(lj, context="paper (Sec. VI): 19.02 s median, RAJA, 4x A100, FP64, "
+                                                      "with energy reduction; other hardware, context only")
     # adjoint: N = 16384 Plummer, 200 KDK steps, dt = 1e-3, checkpoints every 20, loss sum |x_T - t|^2
     n = 16384
     x, v, m = inputs.plummer(n, seed=5)

@@ -6,12 +6,16 @@
  * (arXiv 2511.02655): an all-pairs force evaluation over every pair of
  * particles (Sec. V-B, "N_p^2 operations"), Verlet half-step time integration
  * (Sec. II-A) and a total-energy reduction fused with the force calculation
- * (Sec. VI). The pair law is softened Newtonian gravity instead of the paper's
- * Lennard-Jones law (Eq. 1):
+ * (Sec. VI). Two pair laws:
  *
+ *   softened gravity (default):
  *     d_ij = x_j - x_i,   s_ij = sqrt(|d_ij|^2 + eps^2)
  *     a_i   =  G sum_{j != i} m_j d_ij / s_ij^3
  *     phi_i = -G sum_{j != i} m_j / s_ij
+ *   Lennard-Jones, the paper's Eq. 1 (law = NBODY_LAW_LJ), with u = sigma^2 / s_ij^2:
+ *     a_i   =  (24 epsilon / m_i) sum_{j != i} (u^3 - 2 u^6) d_ij / s_ij^2   (= F_i / m_i)
+ *     phi_i =  ( 4 epsilon / m_i) sum_{j != i} (u^6 - u^3)                   (= sum_j V(r_ij) / m_i)
+ * so that U = 1/2 sum m_i phi_i in both cases. No cutoff: every pair counts.
  *
  * Conventions shared by every call:
  *   - All array arguments are DEVICE pointers (CUDA global memory of the
@@ -57,6 +61,11 @@ typedef enum {
                      state and reductions float64 */
 } nbody_precision;
 
+typedef enum {
+  NBODY_LAW_GRAVITY = 0, /* softened Newtonian gravity (G, eps) */
+  NBODY_LAW_LJ = 1       /* Lennard-Jones, the paper's Eq. 1 (lj_epsilon, lj_sigma; eps softens r^2) */
+} nbody_law;
+
 /* Flags for nbody_config.flags */
 #define NBODY_FLAG_GRAPH 1u   /* replay nbody_step as a captured CUDA graph (same pointers) */
 #define NBODY_FLAG_NOCHECK 2u /* skip the non-finite scan in nbody_sync */
@@ -73,8 +82,14 @@ typedef struct {
                            NBODY_MIXED) (0 = autotune) */
   int32_t slice;        /* force kernel: j-bodies per work item, multiple of j_tile (0 = autotune) */
   uint32_t flags;       /* NBODY_FLAG_* */
-  int32_t variant;      /* mixed force kernel: 1 = scalar float32, 2 = packed float32x2 (bit-identical
-                           results), 0 = autotune; must be 0 or 1 for NBODY_FP64 */
+  int32_t variant;      /* mixed force kernel: 1 = scalar float32, 2 = packed float32x2, 0 = autotune;
+                           must be 0 or 1 for NBODY_FP64; NBODY_LAW_LJ with NBODY_MIXED uses 2 */
+  int32_t law;          /* nbody_law */
+  int32_t reserved;     /* must be 0 */
+  double lj_epsilon;    /* Lennard-Jones well depth (finite; law = NBODY_LAW_LJ) */
+  double lj_sigma;      /* Lennard-Jones length scale (> 0; law = NBODY_LAW_LJ) */
+  double box;           /* > 0: reflecting walls of the cube [0, box]^3 applied after each drift
+                           ("boundary checking"); 0: open space. Finite, >= 0. */
 } nbody_config;
 
 /*
@@ -137,7 +152,8 @@ nbody_status nbody_energy(nbody_ctx* ctx, const double* x, const double* v, cons
  * vector-Jacobian product of a(x, m),
  *     g_x,k = G sum_{j != k} J(d_kj) (m_k w_j - m_j w_k),  J(d) = I/s^3 - 3 d d^T / s^5
  *     g_m,j = G sum_{i != j} w_i . d_ij / s_ij^3
- * in the context's precision. x0/v0/m are not modified.
+ * in the context's precision. x0/v0/m are not modified. Softened gravity
+ * without walls only (NBODY_EUNSUPPORTED otherwise).
  */
 nbody_status nbody_adjoint(nbody_ctx* ctx, const double* x0, const double* v0, const double* m, int32_t n_steps,
                            int32_t checkpoint_every, const double* lam_xT, const double* lam_vT, double* g_x0,

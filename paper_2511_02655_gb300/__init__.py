@@ -20,13 +20,14 @@ import os
 import threading
 
 __all__ = [
-    "FP64", "MIXED", "FLAG_GRAPH", "FLAG_NOCHECK", "NBodyError", "Context", "load", "lib_path",
+    "FP64", "MIXED", "GRAVITY", "LENNARD_JONES", "FLAG_GRAPH", "FLAG_NOCHECK", "NBodyError", "Context", "load", "lib_path",
     "nbody_init", "nbody_forces", "nbody_step", "nbody_energy", "nbody_adjoint", "nbody_step_host",
     "nbody_sync", "nbody_get_tuning", "nbody_launch_count", "nbody_last_error", "nbody_destroy",
     "nbody_version", "nbody_profile", "nbody_kernel_time", "NBodyAdjoint", "ENERGY_FIELDS",
 ]
 
 FP64, MIXED = 0, 1
+GRAVITY, LENNARD_JONES = 0, 1
 FLAG_GRAPH, FLAG_NOCHECK = 1, 2
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "ENONFINITE", 6: "EUNSUPPORTED"}
 ENERGY_FIELDS = ("E", "K", "U", "Px", "Py", "Pz", "Lx", "Ly", "Lz")
@@ -52,7 +53,9 @@ class _Config(ctypes.Structure):
         ("G", ctypes.c_double), ("eps", ctypes.c_double), ("dt", ctypes.c_double),
         ("precision", ctypes.c_int32), ("energy_every", ctypes.c_int32), ("block", ctypes.c_int32),
         ("i_per_thread", ctypes.c_int32), ("j_tile", ctypes.c_int32), ("slice", ctypes.c_int32),
-        ("flags", ctypes.c_uint32), ("variant", ctypes.c_int32),
+        ("flags", ctypes.c_uint32), ("variant", ctypes.c_int32), ("law", ctypes.c_int32),
+        ("reserved", ctypes.c_int32), ("lj_epsilon", ctypes.c_double), ("lj_sigma", ctypes.c_double),
+        ("box", ctypes.c_double),
     ]
 
 
@@ -173,11 +176,14 @@ def _dev(t, name, shape, ctx: Context, allow_none=False):
 
 
 def nbody_init(*, G=1.0, eps=0.0, dt=0.0, precision=MIXED, offsets=None, n=None, energy_every=0, block=0,
-               i_per_thread=0, j_tile=0, slice=0, flags=0, variant=0, stream=None) -> Context:
+               i_per_thread=0, j_tile=0, slice=0, flags=0, variant=0, law=GRAVITY, lj_epsilon=1.0, lj_sigma=1.0,
+               box=0.0, stream=None) -> Context:
     """Creates a context for systems with row ranges ``offsets`` (or one system of ``n`` bodies).
 
     Tile parameters (and the mixed kernel ``variant``: 1 scalar, 2 packed) left at 0
-    are chosen by the autotuner during init.
+    are chosen by the autotuner during init. ``law``: GRAVITY (G, eps) or
+    LENNARD_JONES (lj_epsilon, lj_sigma; eps softens r^2); ``box`` > 0 adds
+    reflecting walls of the cube [0, box]^3.
     ``stream``: a torch.cuda.Stream (default: the current stream).
     """
     torch = _torch()
@@ -188,7 +194,8 @@ def nbody_init(*, G=1.0, eps=0.0, dt=0.0, precision=MIXED, offsets=None, n=None,
         offsets = [0, int(n)]
     offs = (ctypes.c_int64 * len(offsets))(*[int(o) for o in offsets])
     cfg = _Config(float(G), float(eps), float(dt), int(precision), int(energy_every), int(block),
-                  int(i_per_thread), int(j_tile), int(slice), int(flags), int(variant))
+                  int(i_per_thread), int(j_tile), int(slice), int(flags), int(variant), int(law), 0,
+                  float(lj_epsilon), float(lj_sigma), float(box))
     s = (stream or torch.cuda.current_stream()).cuda_stream
     h = ctypes.c_void_p()
     _check(lib.nbody_init(ctypes.byref(h), ctypes.byref(cfg), len(offsets) - 1, offs, ctx_ptr(s)))

@@ -33,8 +33,11 @@ struct Tiling {
   int variant = 0;  // force (mixed): 0 scalar, 1 packed float32x2
 };
 
-// Near-pair refinement radius of the mixed force kernel, in softening lengths.
+// Near-pair refinement radius of the mixed force kernels: 4 softening lengths
+// for gravity, 4 sigma for Lennard-Jones (the neighbour shells that carry its
+// force in a dilute gas).
 constexpr double kNearRadiusEps = 4.0;
+constexpr double kNearRadiusSigma = 4.0;
 
 struct DevBuf {
   void* p = nullptr;
@@ -224,9 +227,10 @@ nbody_status check_dev(nbody_ctx* c, const void* p, size_t bytes, const char* na
 // ---------------------------------------------------------------------------
 // work lists
 
-int ctas_per_sm(int prec, const Tiling& t, bool vjp) {
+int ctas_per_sm(int prec, const Tiling& t, bool vjp, int law) {
+  if (!vjp) return force_ctas_per_sm(prec, t.variant, t.block, t.ipt, t.jtile, law);
   return vjp ? vjp_ctas_per_sm(prec, t.block, t.ipt, t.jtile)
-             : force_ctas_per_sm(prec, t.variant, t.block, t.ipt, t.jtile);
+             : force_ctas_per_sm(prec, t.variant, t.block, t.ipt, t.jtile, 0);
 }
 
 // Slice length for tiling t: the largest power-of-two multiple of jtile that
@@ -326,7 +330,7 @@ nbody_status upload_chunks(nbody_ctx* c, const std::vector<int>& sys_slices, Chu
 // Installs tiling t for the force (vjp=false) or VJP (vjp=true) pass.
 nbody_status install_tiling(nbody_ctx* c, Tiling t, bool vjp) {
   const int prec = c->cfg.precision;
-  const int occ = ctas_per_sm(prec, t, vjp);
+  const int occ = ctas_per_sm(prec, t, vjp, c->cfg.law);
   if (occ <= 0)
     return fail(c, NBODY_EINVAL, "unsupported tiling block=%d ipt=%d jtile=%d variant=%d", t.block, t.ipt, t.jtile,
                 t.variant);
@@ -355,9 +359,13 @@ nbody_status install_tiling(nbody_ctx* c, Tiling t, bool vjp) {
 PairLaunch pair_launch(nbody_ctx* c, bool vjp, const double* x64 = nullptr) {
   PairLaunch L{};
   L.x64 = x64;
-  L.r2_near = (!vjp && x64 && c->cfg.precision == NBODY_MIXED)
-                  ? (float)(kNearRadiusEps * kNearRadiusEps * c->cfg.eps * c->cfg.eps)
-                  : 0.f;
+  L.law = vjp ? 0 : c->cfg.law;
+  L.sigma2 = c->cfg.lj_sigma * c->cfg.lj_sigma;
+  L.r2_near = 0.f;
+  if (!vjp && x64 && c->cfg.precision == NBODY_MIXED)
+    L.r2_near = c->cfg.law == NBODY_LAW_LJ
+                    ? (float)(kNearRadiusSigma * kNearRadiusSigma * L.sigma2 + c->cfg.eps * c->cfg.eps)
+                    : (float)(kNearRadiusEps * kNearRadiusEps * c->cfg.eps * c->cfg.eps);
   L.stage_x = c->stage.p;
   L.stage_w = c->stage_w.p;
   L.items = vjp ? c->d_vitems : c->d_items;
@@ -423,6 +431,9 @@ PostLaunch post_launch(nbody_ctx* c, unsigned mode, double* x, double* v, const 
   P.x_copy = nullptr;
   P.mode = mode;
   P.precision = c->cfg.precision;
+  P.law = c->cfg.law;
+  P.lj_eps = c->cfg.lj_epsilon;
+  P.box = c->cfg.box;
   P.stage = c->stage.p;
   P.centre = static_cast<const double*>(c->centre.p);
   P.epart = static_cast<double*>(c->epart.p);
@@ -491,10 +502,11 @@ uint64_t splitmix(uint64_t& s) {
 }
 
 // Fills the staging buffers with synthetic bodies so that candidate tilings
-// can be timed before any user data exists: each system is a Plummer sphere
-// (scale radius 1, total mass 1, radii truncated at 20), the clustered
-// distribution these kernels are typically run on, which also sets how often
-// the near-pair correction of the mixed kernels fires.
+// can be timed before any user data exists: for gravity each system is a
+// Plummer sphere (scale radius 1, total mass 1, radii truncated at 20), for
+// Lennard-Jones a gas on a jittered lattice, the distributions these kernels
+// are typically run on, which also set how often the near-pair correction of
+// the mixed kernels fires.
 nbody_status fill_synthetic(nbody_ctx* c, bool with_w) {
   const int64_t n = c->n_total;
   uint64_t seed = 12345;
@@ -502,6 +514,20 @@ nbody_status fill_synthetic(nbody_ctx* c, bool with_w) {
   std::vector<double> pos(3 * (size_t)n), mass((size_t)n);
   for (int s = 0; s < c->n_sys; ++s) {
     const int64_t b = c->offsets[s], e = c->offsets[s + 1];
+    if (c->cfg.law == NBODY_LAW_LJ) {
+      // a Lennard-Jones gas: jittered cubic lattice at the box's density (0.05 / sigma^3 without walls)
+      const double sig = c->cfg.lj_sigma, nn = (double)(e - b);
+      const double side = c->cfg.box > 0 ? c->cfg.box : std::cbrt(nn / 0.05) * sig;
+      const int64_t k = std::max<int64_t>(1, (int64_t)std::ceil(std::cbrt(nn) - 1e-9));
+      const double h = side / (double)k;
+      for (int64_t i = b; i < e; ++i) {
+        const int64_t q = i - b;
+        const int64_t lat[3] = {q % k, (q / k) % k, q / (k * k)};
+        for (int d = 0; d < 3; ++d) pos[3 * i + d] = ((double)lat[d] + 0.5 + 0.2 * (u01() - 0.5)) * h - 0.5 * side;
+        mass[i] = 1.0;
+      }
+      continue;
+    }
     for (int64_t i = b; i < e; ++i) {
       double r;
       do {
@@ -611,7 +637,10 @@ nbody_status autotune(nbody_ctx* c, bool vjp) {
   // j-tiles: 128 and 256 for every kernel, 512 for the mixed kernels
   const std::vector<int> jts_f = g.precision == NBODY_MIXED ? std::vector<int>{128, 256, 512} : std::vector<int>{128, 256};
   std::vector<int> variants = {0};
-  if (!vjp && g.precision == NBODY_MIXED) variants = g.variant ? std::vector<int>{g.variant - 1} : std::vector<int>{0, 1};
+  if (!vjp && g.precision == NBODY_MIXED) {
+    variants = g.variant ? std::vector<int>{g.variant - 1} : std::vector<int>{0, 1};
+    if (g.law == NBODY_LAW_LJ) variants = {1};  // Lennard-Jones: packed kernel only
+  }
   for (int var : variants)
     for (int b : blocks) {
       if (!vjp && g.block && g.block != b) continue;
@@ -643,7 +672,7 @@ nbody_status autotune(nbody_ctx* c, bool vjp) {
   double best = 1e300;
   Tiling bt = cands[0];
   for (const Tiling& t0 : cands) {
-    if (ctas_per_sm(g.precision, t0, vjp) <= 0) continue;
+    if (ctas_per_sm(g.precision, t0, vjp, g.law) <= 0) continue;
     Tiling t = t0;
     if (large && t.slice == 0) t.slice = kTuneSlice;
     if ((s = install_tiling(c, t, vjp))) return s;
@@ -696,6 +725,13 @@ nbody_status validate_cfg(const nbody_config* g) {
   if (g->j_tile == 512 && g->precision != NBODY_MIXED) return NBODY_EINVAL;
   if (g->slice < 0) return NBODY_EINVAL;
   if (g->flags & ~(NBODY_FLAG_GRAPH | NBODY_FLAG_NOCHECK)) return NBODY_EINVAL;
+  if (g->law != NBODY_LAW_GRAVITY && g->law != NBODY_LAW_LJ) return NBODY_EINVAL;
+  if (g->reserved != 0) return NBODY_EINVAL;
+  if (!finite(g->box) || g->box < 0) return NBODY_EINVAL;
+  if (g->law == NBODY_LAW_LJ) {
+    if (!finite(g->lj_epsilon) || !finite(g->lj_sigma) || !(g->lj_sigma > 0)) return NBODY_EINVAL;
+    if (g->precision == NBODY_MIXED && g->variant == 1) return NBODY_EINVAL;
+  }
   return NBODY_OK;
 }
 
@@ -820,7 +856,7 @@ nbody_status nbody_init(nbody_ctx** out, const nbody_config* cfg, int64_t n_syst
           cudaSuccess)
     return bail(fail(c, NBODY_ECUDA, "upload of layout tables failed"));
 
-  const bool fixed_variant = cfg->precision == NBODY_FP64 || cfg->variant != 0;
+  const bool fixed_variant = cfg->precision == NBODY_FP64 || cfg->variant != 0 || cfg->law == NBODY_LAW_LJ;
   if (c->n_total > 0 && (cfg->block == 0 || cfg->i_per_thread == 0 || cfg->j_tile == 0 || !fixed_variant)) {
     if ((s = autotune(c, false))) return bail(s);
   } else {
@@ -829,7 +865,7 @@ nbody_status nbody_init(nbody_ctx** out, const nbody_config* cfg, int64_t n_syst
     t.ipt = cfg->i_per_thread ? cfg->i_per_thread : 2;
     t.jtile = cfg->j_tile ? cfg->j_tile : 128;
     t.slice = cfg->slice;
-    t.variant = (cfg->precision == NBODY_MIXED && cfg->variant == 2) ? 1 : 0;
+    t.variant = (cfg->precision == NBODY_MIXED && (cfg->variant == 2 || cfg->law == NBODY_LAW_LJ)) ? 1 : 0;
     if ((s = install_tiling(c, t, false))) return bail(s);
   }
   if (cudaDeviceSynchronize() != cudaSuccess) return bail(fail(c, NBODY_ECUDA, "init synchronisation failed"));
@@ -933,6 +969,8 @@ nbody_status nbody_adjoint(nbody_ctx* c, const double* x0, const double* v0, con
                            double* g_m) {
   if (!c) return fail(nullptr, NBODY_EINVAL, "ctx is NULL");
   if (T < 0 || K < 1) return fail(c, NBODY_EINVAL, "need n_steps >= 0 and checkpoint_every >= 1");
+  if (c->cfg.law != NBODY_LAW_GRAVITY || c->cfg.box > 0)
+    return fail(c, NBODY_EUNSUPPORTED, "nbody_adjoint supports softened gravity without walls only");
   if (T > 0 && !(c->cfg.dt > 0)) return fail(c, NBODY_EINVAL, "dt must be > 0");
   if (c->n_total == 0) return NBODY_OK;
   const size_t n = (size_t)c->n_total, n3b = n * 3 * sizeof(double);

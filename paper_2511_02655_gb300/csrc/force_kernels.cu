@@ -34,7 +34,7 @@ namespace {
 // each sub-block of kSub j-bodies a thread whose minimum fell below the radius
 // rescans that sub-block (s^2 only) and, for each near pair, adds the refined
 // contribution minus the unrefined one it accumulated in the first pass.
-constexpr int kSub = 16;
+constexpr int kSub = 16;  // j-bodies per near-pair check
 
 __device__ __forceinline__ void refine_pair(const double* __restrict__ x64, const int i, const int j, const float eps2,
                                             float& dx, float& dy, float& dz, float& r2) {
@@ -48,27 +48,42 @@ __device__ __forceinline__ void refine_pair(const double* __restrict__ x64, cons
 // flagged sub-block: if it is near and not the self pair, replace its
 // unrefined contribution in (ax, ay, az, pp) by the refined one. The
 // unrefined terms are recomputed with exactly the first pass's operations.
+// LAW 0: softened gravity (q.w = m_j); LAW 1: Lennard-Jones (s2 = sigma^2).
+template <int LAW = 0>
 __device__ __forceinline__ void correct_pair(const float4 q, const int jg, const int ig, const int i_end,
                                              const float xi, const float yi, const float zi, const float eps2,
                                              const float r2c, const double* __restrict__ x64, float& ax, float& ay,
-                                             float& az, float& pp) {
+                                             float& az, float& pp, const float s2 = 0.f) {
   const float dx = q.x - xi;
   const float dy = q.y - yi;
   const float dz = q.z - zi;
   const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
   if (!(r2 < r2c) || ig >= i_end || jg < 0 || ig == jg) return;
-  const float iu = rsq_approx(r2);
-  const float msu = q.w * iu;
-  const float wu = msu * (iu * iu);
   float rx, ry, rz, rr2;
   refine_pair(x64, ig, jg, eps2, rx, ry, rz, rr2);
-  const float ir = rsq_approx(rr2);
-  const float msr = q.w * ir;
-  const float wr = msr * (ir * ir);
-  ax += fmaf(rx, wr, -(dx * wu));
-  ay += fmaf(ry, wr, -(dy * wu));
-  az += fmaf(rz, wr, -(dz * wu));
-  pp += msr - msu;
+  if (LAW == 0) {
+    const float iu = rsq_approx(r2);
+    const float msu = q.w * iu;
+    const float wu = msu * (iu * iu);
+    const float ir = rsq_approx(rr2);
+    const float msr = q.w * ir;
+    const float wr = msr * (ir * ir);
+    ax += fmaf(rx, wr, -(dx * wu));
+    ay += fmaf(ry, wr, -(dy * wu));
+    az += fmaf(rz, wr, -(dz * wu));
+    pp += msr - msu;
+  } else {
+    const float iu = rcp_approx(r2);
+    const float su2 = s2 * iu, su6 = su2 * (su2 * su2), su12 = su6 * su6;
+    const float wu = fmaf(su12, -2.f, su6) * iu;
+    const float ir = rcp_approx(rr2);
+    const float sr2 = s2 * ir, sr6 = sr2 * (sr2 * sr2), sr12 = sr6 * sr6;
+    const float wr = fmaf(sr12, -2.f, sr6) * ir;
+    ax += fmaf(rx, wr, -(dx * wu));
+    ay += fmaf(ry, wr, -(dy * wu));
+    az += fmaf(rz, wr, -(dz * wu));
+    pp += fmaf(sr6, -1.f, sr12) - fmaf(su6, -1.f, su12);
+  }
 }
 
 // ---- scalar kernel: one j-body against the thread's R i-bodies per step
@@ -250,32 +265,75 @@ __device__ __forceinline__ void pair2_f32x2(const float2 xj, const float2 yj, co
   pp = __fadd2_rn(pp, ms);
 }
 
+// Lennard-Jones pair (Eq. 1) on two j-bodies: with u = sigma^2 / r^2,
+//   sum (u^3 - 2 u^6) / r^2 d  (a_i = 24 eps / m_i times this)
+//   sum (u^6 - u^3)            (phi_i = 4 eps / m_i times this),
+// 17 float32 operations (8.5 packed) and one MUFU.RCP per interaction.
+template <bool MASK>
+__device__ __forceinline__ void pair2_lj_f32x2(const float2 xj, const float2 yj, const float2 zj, const int jg0,
+                                               const int ig, const float2 nx, const float2 ny, const float2 nz,
+                                               const float2 e2, const float2 s2, float2& ax, float2& ay, float2& az,
+                                               float2& pp, float& mn0, float& mn1) {
+  const float2 dx = __fadd2_rn(xj, nx);
+  const float2 dy = __fadd2_rn(yj, ny);
+  const float2 dz = __fadd2_rn(zj, nz);
+  const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __ffma2_rn(dz, dz, e2)));
+  mn0 = fminf(mn0, r2.x);
+  mn1 = fminf(mn1, r2.y);
+  float2 inv2 = make_float2(rcp_approx(r2.x), rcp_approx(r2.y));
+  if (MASK) {
+    inv2.x = (jg0 == ig) ? 0.f : inv2.x;
+    inv2.y = (jg0 + 1 == ig) ? 0.f : inv2.y;
+  }
+  const float2 u = __fmul2_rn(s2, inv2);
+  const float2 u3 = __fmul2_rn(u, __fmul2_rn(u, u));
+  const float2 u6 = __fmul2_rn(u3, u3);
+  const float2 w = __fmul2_rn(__ffma2_rn(u6, make_float2(-2.f, -2.f), u3), inv2);
+  ax = __ffma2_rn(dx, w, ax);
+  ay = __ffma2_rn(dy, w, ay);
+  az = __ffma2_rn(dz, w, az);
+  pp = __fadd2_rn(pp, __ffma2_rn(u3, make_float2(-1.f, -1.f), u6));
+}
+
 // Four j-bodies (tile entries j..j+3) against the thread's R i-bodies.
-template <int R, bool MASK>
+template <int LAW, int R, bool MASK>
 __device__ __forceinline__ void quad_f32x2(const float* tx, const float* ty, const float* tz, const float* tm,
                                            const int j, const int jg, const int (&ig)[R], const float2 (&nx)[R],
                                            const float2 (&ny)[R], const float2 (&nz)[R], const float2 e2,
-                                           float2 (&ax)[R], float2 (&ay)[R], float2 (&az)[R], float2 (&pp)[R],
-                                           float& mn0, float& mn1) {
+                                           const float2 s2, float2 (&ax)[R], float2 (&ay)[R], float2 (&az)[R],
+                                           float2 (&pp)[R], float& mn0, float& mn1) {
   const float4 X = *reinterpret_cast<const float4*>(tx + j);
   const float4 Y = *reinterpret_cast<const float4*>(ty + j);
   const float4 Z = *reinterpret_cast<const float4*>(tz + j);
-  const float4 M = *reinterpret_cast<const float4*>(tm + j);
+  if (LAW == 0) {
+    const float4 M = *reinterpret_cast<const float4*>(tm + j);
 #pragma unroll
-  for (int r = 0; r < R; ++r) {
-    pair2_f32x2<MASK>(make_float2(X.x, X.y), make_float2(Y.x, Y.y), make_float2(Z.x, Z.y), make_float2(M.x, M.y),
-                      jg, ig[r], nx[r], ny[r], nz[r], e2, ax[r], ay[r], az[r], pp[r], mn0, mn1);
-    pair2_f32x2<MASK>(make_float2(X.z, X.w), make_float2(Y.z, Y.w), make_float2(Z.z, Z.w), make_float2(M.z, M.w),
-                      jg + 2, ig[r], nx[r], ny[r], nz[r], e2, ax[r], ay[r], az[r], pp[r], mn0, mn1);
+    for (int r = 0; r < R; ++r) {
+      pair2_f32x2<MASK>(make_float2(X.x, X.y), make_float2(Y.x, Y.y), make_float2(Z.x, Z.y),
+                        make_float2(M.x, M.y), jg, ig[r], nx[r], ny[r], nz[r], e2, ax[r], ay[r], az[r], pp[r], mn0,
+                        mn1);
+      pair2_f32x2<MASK>(make_float2(X.z, X.w), make_float2(Y.z, Y.w), make_float2(Z.z, Z.w),
+                        make_float2(M.z, M.w), jg + 2, ig[r], nx[r], ny[r], nz[r], e2, ax[r], ay[r], az[r], pp[r],
+                        mn0, mn1);
+    }
+  } else {
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      pair2_lj_f32x2<MASK>(make_float2(X.x, X.y), make_float2(Y.x, Y.y), make_float2(Z.x, Z.y), jg, ig[r], nx[r],
+                           ny[r], nz[r], e2, s2, ax[r], ay[r], az[r], pp[r], mn0, mn1);
+      pair2_lj_f32x2<MASK>(make_float2(X.z, X.w), make_float2(Y.z, Y.w), make_float2(Z.z, Z.w), jg + 2, ig[r],
+                           nx[r], ny[r], nz[r], e2, s2, ax[r], ay[r], az[r], pp[r], mn0, mn1);
+    }
   }
 }
 
-template <int R, bool MASK>
+template <int LAW, int R, bool MASK>
 __device__ __forceinline__ void tile_pass_f32x2(const float* tx, const float* ty, const float* tz, const float* tm,
                                                 const int jt, const int nj, const int (&ig)[R], const float2 (&nx)[R],
                                                 const float2 (&ny)[R], const float2 (&nz)[R], const int i_end,
-                                                const float2 e2, const float r2c, const double* __restrict__ x64,
-                                                float2 (&ax)[R], float2 (&ay)[R], float2 (&az)[R], float2 (&pp)[R]) {
+                                                const float2 e2, const float2 s2, const float r2c,
+                                                const double* __restrict__ x64, float2 (&ax)[R], float2 (&ay)[R],
+                                                float2 (&az)[R], float2 (&pp)[R]) {
   const int nj4 = (nj + 3) & ~3;  // the tile is padded to a multiple of four
   for (int jb = 0; jb < nj4; jb += kSub) {
     const int nb = min(kSub, nj4 - jb);
@@ -283,10 +341,10 @@ __device__ __forceinline__ void tile_pass_f32x2(const float* tx, const float* ty
     if (nb == kSub) {
 #pragma unroll 4
       for (int j = jb; j < jb + kSub; j += 4)
-        quad_f32x2<R, MASK>(tx, ty, tz, tm, j, jt + j, ig, nx, ny, nz, e2, ax, ay, az, pp, mn0, mn1);
+        quad_f32x2<LAW, R, MASK>(tx, ty, tz, tm, j, jt + j, ig, nx, ny, nz, e2, s2, ax, ay, az, pp, mn0, mn1);
     } else {
       for (int j = jb; j < jb + nb; j += 4)
-        quad_f32x2<R, MASK>(tx, ty, tz, tm, j, jt + j, ig, nx, ny, nz, e2, ax, ay, az, pp, mn0, mn1);
+        quad_f32x2<LAW, R, MASK>(tx, ty, tz, tm, j, jt + j, ig, nx, ny, nz, e2, s2, ax, ay, az, pp, mn0, mn1);
     }
     if (fminf(mn0, mn1) < r2c) {
       // rescan two j-bodies at a time: packed s^2, scalar correction of the near ones
@@ -301,18 +359,19 @@ __device__ __forceinline__ void tile_pass_f32x2(const float* tx, const float* ty
           const float2 dz = __fadd2_rn(zj, nz[r]);
           const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __ffma2_rn(dz, dz, e2)));
           if (r2.x < r2c && j < nj)
-            correct_pair(make_float4(tx[j], ty[j], tz[j], tm[j]), jt + j, ig[r], i_end, -nx[r].x, -ny[r].x,
-                         -nz[r].x, e2.x, r2c, x64, ax[r].x, ay[r].x, az[r].x, pp[r].x);
+            correct_pair<LAW>(make_float4(tx[j], ty[j], tz[j], tm[j]), jt + j, ig[r], i_end, -nx[r].x, -ny[r].x,
+                              -nz[r].x, e2.x, r2c, x64, ax[r].x, ay[r].x, az[r].x, pp[r].x, s2.x);
           if (r2.y < r2c && j + 1 < nj)
-            correct_pair(make_float4(tx[j + 1], ty[j + 1], tz[j + 1], tm[j + 1]), jt + j + 1, ig[r], i_end,
-                         -nx[r].x, -ny[r].x, -nz[r].x, e2.x, r2c, x64, ax[r].y, ay[r].y, az[r].y, pp[r].y);
+            correct_pair<LAW>(make_float4(tx[j + 1], ty[j + 1], tz[j + 1], tm[j + 1]), jt + j + 1, ig[r], i_end,
+                              -nx[r].x, -ny[r].x, -nz[r].x, e2.x, r2c, x64, ax[r].y, ay[r].y, az[r].y, pp[r].y,
+                              s2.x);
         }
       }
     }
   }
 }
 
-template <int BLOCK, int R, int J>
+template <int LAW, int BLOCK, int R, int J>
 __global__ void __launch_bounds__(BLOCK) k_force_mixed2(const PairLaunch L) {
   static_assert(J % 4 == 0, "tiles hold whole quads of j-bodies");
   constexpr int LPT = (J + BLOCK - 1) / BLOCK;
@@ -325,6 +384,7 @@ __global__ void __launch_bounds__(BLOCK) k_force_mixed2(const PairLaunch L) {
   double4_32a* __restrict__ part = reinterpret_cast<double4_32a*>(L.part);
   const float eps2 = (float)L.eps2;
   const float2 e2 = make_float2(eps2, eps2);
+  const float2 s2 = make_float2((float)L.sigma2, (float)L.sigma2);
   const float r2c = L.r2_near;
   const double* __restrict__ x64 = L.x64;
 
@@ -381,11 +441,11 @@ __global__ void __launch_bounds__(BLOCK) k_force_mixed2(const PairLaunch L) {
       for (int r = 0; r < R; ++r) ax[r] = ay[r] = az[r] = pp[r] = make_float2(0.f, 0.f);
       const bool diag = (jt < w.i_end) && (w.i_begin < jt + nj);
       if (diag)
-        tile_pass_f32x2<R, true>(tx[buf], ty[buf], tz[buf], tm[buf], jt, nj, ig, nx, ny, nz, w.i_end, e2, r2c, x64,
-                                 ax, ay, az, pp);
+        tile_pass_f32x2<LAW, R, true>(tx[buf], ty[buf], tz[buf], tm[buf], jt, nj, ig, nx, ny, nz, w.i_end, e2, s2,
+                                      r2c, x64, ax, ay, az, pp);
       else
-        tile_pass_f32x2<R, false>(tx[buf], ty[buf], tz[buf], tm[buf], jt, nj, ig, nx, ny, nz, w.i_end, e2, r2c,
-                                  x64, ax, ay, az, pp);
+        tile_pass_f32x2<LAW, R, false>(tx[buf], ty[buf], tz[buf], tm[buf], jt, nj, ig, nx, ny, nz, w.i_end, e2, s2,
+                                       r2c, x64, ax, ay, az, pp);
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         two_sum_acc(hx[r], lx[r], ax[r].x + ax[r].y);
@@ -420,25 +480,36 @@ __global__ void __launch_bounds__(BLOCK) k_force_mixed2(const PairLaunch L) {
   retire_cta(L.counter);
 }
 
-template <bool MASK>
+template <int LAW, bool MASK>
 __device__ __forceinline__ void pair_f64(const double4_32a q, const double xi, const double yi, const double zi,
-                                         const double eps2, double& ax, double& ay, double& az, double& pp,
-                                         const bool self) {
+                                         const double eps2, const double s2, double& ax, double& ay, double& az,
+                                         double& pp, const bool self) {
   const double dx = q.x - xi;
   const double dy = q.y - yi;
   const double dz = q.z - zi;
   const double r2 = fma(dx, dx, fma(dy, dy, fma(dz, dz, eps2)));
-  double inv = rsqrt(r2);
-  if (MASK) inv = self ? 0.0 : inv;
-  const double ms = q.w * inv;
-  const double w = ms * (inv * inv);
-  ax = fma(dx, w, ax);
-  ay = fma(dy, w, ay);
-  az = fma(dz, w, az);
-  pp += ms;
+  if (LAW == 0) {
+    double inv = rsqrt(r2);
+    if (MASK) inv = self ? 0.0 : inv;
+    const double ms = q.w * inv;
+    const double w = ms * (inv * inv);
+    ax = fma(dx, w, ax);
+    ay = fma(dy, w, ay);
+    az = fma(dz, w, az);
+    pp += ms;
+  } else {  // Lennard-Jones, u = sigma^2 / r^2
+    double inv2 = 1.0 / r2;
+    if (MASK) inv2 = self ? 0.0 : inv2;
+    const double u = s2 * inv2, u3 = u * u * u, u6 = u3 * u3;
+    const double w = (u3 - 2.0 * u6) * inv2;
+    ax = fma(dx, w, ax);
+    ay = fma(dy, w, ay);
+    az = fma(dz, w, az);
+    pp += u6 - u3;
+  }
 }
 
-template <int BLOCK, int R, int J>
+template <int LAW, int BLOCK, int R, int J>
 __global__ void __launch_bounds__(BLOCK) k_force_fp64(const PairLaunch L) {
   constexpr int LPT = (J + BLOCK - 1) / BLOCK;
   __shared__ __align__(32) double4_32a tile[J];
@@ -446,6 +517,7 @@ __global__ void __launch_bounds__(BLOCK) k_force_fp64(const PairLaunch L) {
   const double4_32a* __restrict__ st = static_cast<const double4_32a*>(L.stage_x);
   double4_32a* __restrict__ part = reinterpret_cast<double4_32a*>(L.part);
   const double eps2 = L.eps2;
+  const double s2 = L.sigma2;
 
   for (;;) {
     const int it = next_item(L.counter, &s_item);
@@ -491,7 +563,7 @@ __global__ void __launch_bounds__(BLOCK) k_force_fp64(const PairLaunch L) {
           const double4_32a q = tile[j];
 #pragma unroll
           for (int r = 0; r < R; ++r)
-            pair_f64<true>(q, xi[r], yi[r], zi[r], eps2, ax[r], ay[r], az[r], pp[r], jt + j == ig[r]);
+            pair_f64<LAW, true>(q, xi[r], yi[r], zi[r], eps2, s2, ax[r], ay[r], az[r], pp[r], jt + j == ig[r]);
         }
       } else {
 #pragma unroll 4
@@ -499,7 +571,7 @@ __global__ void __launch_bounds__(BLOCK) k_force_fp64(const PairLaunch L) {
           const double4_32a q = tile[j];
 #pragma unroll
           for (int r = 0; r < R; ++r)
-            pair_f64<false>(q, xi[r], yi[r], zi[r], eps2, ax[r], ay[r], az[r], pp[r], false);
+            pair_f64<LAW, false>(q, xi[r], yi[r], zi[r], eps2, s2, ax[r], ay[r], az[r], pp[r], false);
         }
       }
     }
@@ -519,23 +591,50 @@ int occupancy_of(K kern, int block) {
   return n;
 }
 
-// Tilings compiled: BLOCK in {128, 256}, R in {1, 2, 4}, J in {128, 256} for
-// every kernel, and J = 512 for the two mixed kernels.
+// Tilings compiled. Softened gravity: BLOCK in {128, 256}, R in {1, 2, 4},
+// J in {128, 256} for every kernel, and J = 512 for the two mixed kernels.
+// Lennard-Jones: the packed mixed kernel and the FP64 kernel on the subsets below.
 #define NBODY_FORCE_TILINGS(X) \
   X(128, 1, 128) X(128, 2, 128) X(128, 4, 128) X(128, 1, 256) X(128, 2, 256) X(128, 4, 256) \
   X(256, 1, 128) X(256, 2, 128) X(256, 4, 128) X(256, 1, 256) X(256, 2, 256) X(256, 4, 256)
 #define NBODY_MIXED_TILINGS(X) \
   NBODY_FORCE_TILINGS(X) X(128, 1, 512) X(128, 2, 512) X(128, 4, 512) X(256, 1, 512) X(256, 2, 512) X(256, 4, 512)
+#define NBODY_LJ_MIXED_TILINGS(X) \
+  X(128, 1, 256) X(256, 1, 256) X(128, 2, 256) X(128, 1, 512) X(256, 1, 512) X(256, 2, 512)
+#define NBODY_LJ_FP64_TILINGS(X) X(128, 1, 128) X(256, 1, 128) X(128, 2, 128) X(256, 2, 128)
 
 }  // namespace
 
 cudaError_t launch_force(int precision, const PairLaunch& L, cudaStream_t st) {
   if (L.n_ctas <= 0) return cudaErrorInvalidConfiguration;
+  if (L.law == 1) {
+#define NBODY_X(B, R, J)                                               \
+  if (L.block == B && L.ipt == R && L.jtile == J) {                    \
+    k_force_mixed2<1, B, R, J><<<L.n_ctas, B, 0, st>>>(L);             \
+    return cudaGetLastError();                                         \
+  }
+    if (precision == 1) {
+      if (L.variant != 1) return cudaErrorInvalidConfiguration;
+      NBODY_LJ_MIXED_TILINGS(NBODY_X)
+      return cudaErrorInvalidConfiguration;
+    }
+#undef NBODY_X
+#define NBODY_X(B, R, J)                                               \
+  if (L.block == B && L.ipt == R && L.jtile == J) {                    \
+    k_force_fp64<1, B, R, J><<<L.n_ctas, B, 0, st>>>(L);               \
+    return cudaGetLastError();                                         \
+  }
+    if (L.variant != 0) return cudaErrorInvalidConfiguration;
+    NBODY_LJ_FP64_TILINGS(NBODY_X)
+#undef NBODY_X
+    return cudaErrorInvalidConfiguration;
+  }
+  if (L.law != 0) return cudaErrorInvalidConfiguration;
   if (precision == 1) {
 #define NBODY_X(B, R, J)                                               \
   if (L.block == B && L.ipt == R && L.jtile == J) {                    \
     if (L.variant == 1)                                                \
-      k_force_mixed2<B, R, J><<<L.n_ctas, B, 0, st>>>(L);              \
+      k_force_mixed2<0, B, R, J><<<L.n_ctas, B, 0, st>>>(L);           \
     else                                                               \
       k_force_mixed<B, R, J><<<L.n_ctas, B, 0, st>>>(L);               \
     return cudaGetLastError();                                         \
@@ -548,7 +647,7 @@ cudaError_t launch_force(int precision, const PairLaunch& L, cudaStream_t st) {
   if (L.variant != 0) return cudaErrorInvalidConfiguration;
 #define NBODY_X(B, R, J)                                               \
   if (L.block == B && L.ipt == R && L.jtile == J) {                    \
-    k_force_fp64<B, R, J><<<L.n_ctas, B, 0, st>>>(L);                  \
+    k_force_fp64<0, B, R, J><<<L.n_ctas, B, 0, st>>>(L);               \
     return cudaGetLastError();                                         \
   }
   NBODY_FORCE_TILINGS(NBODY_X)
@@ -556,19 +655,36 @@ cudaError_t launch_force(int precision, const PairLaunch& L, cudaStream_t st) {
   return cudaErrorInvalidConfiguration;
 }
 
-int force_ctas_per_sm(int precision, int variant, int block, int ipt, int jtile) {
+int force_ctas_per_sm(int precision, int variant, int block, int ipt, int jtile, int law) {
+  if (law == 1) {
+    if (precision == 1) {
+      if (variant != 1) return 0;
+#define NBODY_X(B, R, J) \
+  if (block == B && ipt == R && jtile == J) return occupancy_of(k_force_mixed2<1, B, R, J>, B);
+      NBODY_LJ_MIXED_TILINGS(NBODY_X)
+#undef NBODY_X
+      return 0;
+    }
+    if (variant != 0) return 0;
+#define NBODY_X(B, R, J) \
+  if (block == B && ipt == R && jtile == J) return occupancy_of(k_force_fp64<1, B, R, J>, B);
+    NBODY_LJ_FP64_TILINGS(NBODY_X)
+#undef NBODY_X
+    return 0;
+  }
+  if (law != 0) return 0;
   if (precision == 1) {
     if (variant != 0 && variant != 1) return 0;
-#define NBODY_X(B, R, J)                                                                          \
-  if (block == B && ipt == R && jtile == J)                                                       \
-    return variant == 1 ? occupancy_of(k_force_mixed2<B, R, J>, B) : occupancy_of(k_force_mixed<B, R, J>, B);
+#define NBODY_X(B, R, J)                                                                             \
+  if (block == B && ipt == R && jtile == J)                                                          \
+    return variant == 1 ? occupancy_of(k_force_mixed2<0, B, R, J>, B) : occupancy_of(k_force_mixed<B, R, J>, B);
     NBODY_MIXED_TILINGS(NBODY_X)
 #undef NBODY_X
     return 0;
   }
   if (variant != 0) return 0;
 #define NBODY_X(B, R, J) \
-  if (block == B && ipt == R && jtile == J) return occupancy_of(k_force_fp64<B, R, J>, B);
+  if (block == B && ipt == R && jtile == J) return occupancy_of(k_force_fp64<0, B, R, J>, B);
   NBODY_FORCE_TILINGS(NBODY_X)
 #undef NBODY_X
   return 0;

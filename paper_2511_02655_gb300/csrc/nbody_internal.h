@@ -49,6 +49,8 @@ struct PairLaunch {
   const double* x64;     // force (mixed): caller's float64 positions [N,3] for near-pair refinement
   float r2_near;         // force (mixed): refine pairs with s^2 below this (0 = never)
   int variant;           // force (mixed): 0 scalar float32, 1 packed float32x2
+  int law;               // 0 softened gravity, 1 Lennard-Jones
+  double sigma2;         // Lennard-Jones sigma^2
   int block, ipt, jtile; // tiling
   int n_ctas;            // persistent grid size
 };
@@ -57,7 +59,7 @@ struct PairLaunch {
 cudaError_t launch_force(int precision, const PairLaunch& L, cudaStream_t st);
 cudaError_t launch_vjp(int precision, const PairLaunch& L, cudaStream_t st);
 // CTAs of the force kernel that fit on one SM for the tiling (0 if unsupported).
-int force_ctas_per_sm(int precision, int variant, int block, int ipt, int jtile);
+int force_ctas_per_sm(int precision, int variant, int block, int ipt, int jtile, int law);
 int vjp_ctas_per_sm(int precision, int block, int ipt, int jtile);
 
 // ---------------------------------------------------------------------------
@@ -85,6 +87,9 @@ struct PostLaunch {
   double* x_copy;          // nullable: copy of x after the drift
   unsigned mode;
   int precision;
+  int law;                 // 0 gravity: a = G S, phi = -G S_phi; 1 Lennard-Jones: a = 24 eps S / m, phi = 4 eps S_phi / m
+  double lj_eps;
+  double box;              // > 0: reflecting walls of [0, box]^3 applied after the drift
   void* stage;             // float4 / double4_32a [N]
   const double* centre;    // [n_sys][3] staging origin (mixed)
   double* epart;           // [n_chunks][kEnergyVals]

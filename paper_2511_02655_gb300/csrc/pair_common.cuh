@@ -16,6 +16,13 @@ __device__ __forceinline__ float rsq_approx(float x) {
   return y;
 }
 
+// Hardware approximate reciprocal (MUFU), flush-to-zero input; rcp(+0) = +inf.
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 // Knuth's TwoSum: hi + lo absorbs t, with the rounding error of hi + t carried
 // into lo (Knuth, TAOCP vol. 2, 4.2.2). Six float32 additions, no branches.
 __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float t) {

@@ -38,6 +38,21 @@ __device__ __forceinline__ void block_sum(double (&v)[NV]) {
   }
 }
 
+// Reflecting walls of [0, box] ("boundary checking"): a coordinate that left
+// the box is mirrored back across the wall and its velocity component flips;
+// repeated (bounded) for steps that cross the box more than once.
+__device__ __forceinline__ void reflect(double& x, double& v, const double box) {
+  for (int k = 0; k < 64; ++k) {
+    if (x < 0.0) {
+      x = -x, v = -v;
+    } else if (x > box) {
+      x = 2.0 * box - x, v = -v;
+    } else {
+      return;
+    }
+  }
+}
+
 __device__ __forceinline__ void stage_store(int precision, void* stage, int i, double x, double y, double z,
                                             double m, const double* c) {
   if (precision == 1) {
@@ -67,7 +82,13 @@ __global__ void __launch_bounds__(kPostThreads) k_post(const PostLaunch P) {
         const double4_32a q = part[(int64_t)s * P.n_total + i];
         sx += q.x, sy += q.y, sz += q.z, sp += q.w;
       }
-      ax = P.G * sx, ay = P.G * sy, az = P.G * sz, ph = -P.G * sp;
+      if (P.law == 0) {  // softened gravity
+        ax = P.G * sx, ay = P.G * sy, az = P.G * sz, ph = -P.G * sp;
+      } else {  // Lennard-Jones: per unit mass of body i
+        const double mi = P.m[i];
+        const double ca = 24.0 * P.lj_eps / mi, cp = 4.0 * P.lj_eps / mi;
+        ax = ca * sx, ay = ca * sy, az = ca * sz, ph = cp * sp;
+      }
       P.a[3 * i + 0] = ax, P.a[3 * i + 1] = ay, P.a[3 * i + 2] = az;
       if (P.phi) P.phi[i] = ph;
       bad |= !(isfinite(ax) && isfinite(ay) && isfinite(az) && isfinite(ph));
@@ -93,6 +114,11 @@ __global__ void __launch_bounds__(kPostThreads) k_post(const PostLaunch P) {
       if (mode & kDrift) {
         v0 += P.half_dt * ax, v1 += P.half_dt * ay, v2 += P.half_dt * az;
         x0 += P.dt * v0, x1 += P.dt * v1, x2 += P.dt * v2;
+        if (P.box > 0.0) {
+          reflect(x0, v0, P.box);
+          reflect(x1, v1, P.box);
+          reflect(x2, v2, P.box);
+        }
         P.x[3 * i + 0] = x0, P.x[3 * i + 1] = x1, P.x[3 * i + 2] = x2;
         if (P.x_copy) P.x_copy[3 * i + 0] = x0, P.x_copy[3 * i + 1] = x1, P.x_copy[3 * i + 2] = x2;
       }

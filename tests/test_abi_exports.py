@@ -46,12 +46,12 @@ def test_status_codes_and_constants_match_header():
     assert {nbody.STATUS[v]: v for v in nbody.STATUS} == codes
     assert int(re.search(r"NBODY_MIXED\s*=\s*(\d)", text).group(1)) == nbody.MIXED
     assert int(re.search(r"NBODY_FLAG_GRAPH\s+(\d+)u", text).group(1)) == nbody.FLAG_GRAPH
-    assert ctypes.sizeof(nbody._Config) == 3 * 8 + 8 * 4
+    assert ctypes.sizeof(nbody._Config) == 3 * 8 + 10 * 4 + 3 * 8
 
 
 def _cfg(**kw):
     import paper_2511_02655_gb300 as nbody
-    c = nbody._Config(1.0, 0.01, 1e-3, 1, 0, 0, 0, 0, 0, 0, 0)
+    c = nbody._Config(1.0, 0.01, 1e-3, 1, 0, 0, 0, 0, 0, 0, 0, 0, 0, 1.0, 1.0, 0.0)
     for k, v in kw.items():
         setattr(c, k, v)
     return c
@@ -59,7 +59,8 @@ def _cfg(**kw):
 
 @pytest.mark.parametrize("bad", [dict(eps=-1.0), dict(precision=7), dict(block=96), dict(i_per_thread=3),
                                  dict(j_tile=100), dict(energy_every=-1), dict(flags=64), dict(G=float("nan")),
-                                 dict(variant=3), dict(variant=2, precision=0)])
+                                 dict(variant=3), dict(variant=2, precision=0), dict(law=2), dict(reserved=1),
+                                 dict(box=-1.0), dict(law=1, lj_sigma=0.0), dict(law=1, variant=1)])
 def test_init_rejects_bad_config_before_touching_a_device(lib, bad):
     h = ctypes.c_void_p(123)
     offs = (ctypes.c_int64 * 2)(0, 16)

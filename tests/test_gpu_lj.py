@@ -1,0 +1,87 @@
+"""GPU parity of the Lennard-Jones pair law (the paper's Eq. 1) with reflecting
+walls ("boundary checking"), against the FP64 CPU oracle."""
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2511_02655_gb300 import inputs
+from helpers import force_rel_err, to_dev, to_np
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL, MIX_MED, MIX_MAX = 1e-12, 1e-6, 1e-4
+
+
+def _lj_forces(nb, prec, x, m, **kw):
+    ctx = nb.nbody_init(law=nb.LENNARD_JONES, precision=prec, n=len(m), dt=5e-3, **kw)
+    xt, mt = to_dev(x, m)
+    a, phi = nb.nbody_forces(ctx, xt, mt)
+    nb.nbody_sync(ctx)
+    return a.cpu().numpy(), phi.cpu().numpy()
+
+
+@pytest.mark.parametrize("density", [0.05, 0.5])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_lj_forces(nb, prec, density):
+    x, v, m, box = inputs.lj_gas(2000, seed=7, density=density, temperature=2.0)
+    m = m * np.exp(0.2 * np.random.default_rng(1).standard_normal(len(m)))
+    a, phi = _lj_forces(nb, prec, x, m, lj_epsilon=1.3, lj_sigma=0.9)
+    a_ref, phi_ref = oracle.lj_forces(x, m, eps_lj=1.3, sigma=0.9)
+    e = force_rel_err(a, a_ref)
+    if prec == nb.FP64:
+        assert e.max() <= FP64_TOL
+        assert np.abs(phi - phi_ref).max() <= FP64_TOL * np.abs(phi_ref).max()
+    else:
+        assert np.median(e) <= MIX_MED and e.max() <= MIX_MAX, (np.median(e), e.max())
+        assert np.abs(phi - phi_ref).max() <= 1e-5 * np.abs(phi_ref).max()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_lj_kdk_with_walls(nb, prec):
+    import torch
+    x, v, m, box = inputs.lj_gas(1000, seed=8, density=0.1, temperature=2.0)
+    dt, T = 5e-3, 60
+    ctx = nb.nbody_init(law=nb.LENNARD_JONES, precision=prec, n=1000, dt=dt, box=box, energy_every=10)
+    xt, vt, mt = to_dev(x, v, m)
+    at = torch.empty_like(xt)
+    log = nb.nbody_step(ctx, xt, vt, mt, at, False, T)
+    nb.nbody_sync(ctx)
+    xr, vr, ar, logr = oracle.lj_kdk(x, v, m, 1.0, 1.0, 0.0, box, dt, T, energy_every=10)
+    xg, vg, ag, lg = to_np(xt, vt, at, log)
+    assert xg.min() >= 0 and xg.max() <= box
+    if prec == nb.FP64:
+        assert np.abs(xg - xr).max() <= 1e-10
+        assert force_rel_err(ag, ar).max() <= 1e-9
+        np.testing.assert_allclose(lg[:, 0, 0:3], logr[:, 0:3], rtol=1e-10)
+    else:
+        assert np.abs(xg - xr).max() <= 1e-5
+        np.testing.assert_allclose(lg[:, 0, 0], logr[:, 0], rtol=1e-5)
+    # walls reflect, so momentum is not conserved; energy is (to the leapfrog's accuracy)
+    assert np.abs(lg[:, 0, 0] - lg[0, 0, 0]).max() <= 1e-3 * abs(lg[0, 0, 0])
+
+
+def test_lj_paper_configuration_short_run(nb):
+    """The paper's system size (10 000 particles), 20 KDK steps, FP64 GPU vs oracle."""
+    import torch
+    x, v, m, box = inputs.lj_gas(10000, seed=9)
+    dt, T = 5e-3, 20
+    ctx = nb.nbody_init(law=nb.LENNARD_JONES, precision=nb.FP64, n=10000, dt=dt, box=box)
+    xt, vt, mt = to_dev(x, v, m)
+    at = torch.empty_like(xt)
+    nb.nbody_step(ctx, xt, vt, mt, at, False, T)
+    nb.nbody_sync(ctx)
+    xr, vr, ar, _ = oracle.lj_kdk(x, v, m, 1.0, 1.0, 0.0, box, dt, T)
+    assert np.abs(xt.cpu().numpy() - xr).max() <= 1e-10
+    idx = inputs.sample_indices(10000, 512, seed=3)
+    e = force_rel_err(at.cpu().numpy()[idx], ar[idx])
+    assert e.max() <= 1e-9
+
+
+def test_lj_adjoint_unsupported(nb):
+    x, v, m, box = inputs.lj_gas(64, seed=1)
+    ctx = nb.nbody_init(law=nb.LENNARD_JONES, precision=nb.FP64, n=64, dt=1e-3)
+    xt, vt, mt = to_dev(x, v, m)
+    with pytest.raises(nb.NBodyError) as ei:
+        nb.nbody_adjoint(ctx, xt, vt, mt, 5, 2, xt.clone(), vt.clone())
+    assert ei.value.status == 6
