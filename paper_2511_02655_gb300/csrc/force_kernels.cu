@@ -34,7 +34,24 @@ namespace {
 // each sub-block of kSub j-bodies a thread whose minimum fell below the radius
 // rescans that sub-block (s^2 only) and, for each near pair, adds the refined
 // contribution minus the unrefined one it accumulated in the first pass.
-constexpr int kSub = 16;  // j-bodies per near-pair check
+// Compile-time tuning of the mixed kernels. The defaults won a sweep on GB300
+// (Plummer N = 65 536 and two spheres N = 1 048 576): 32-body sub-blocks were
+// 2-5% faster than 16 or 8; unroll depth 2 vs 4 within 1%; requesting a minimum
+// number of resident CTAs did not help.
+//   NBODY_SUB          j-bodies per near-pair check (sub-block)
+//   NBODY_QUAD_UNROLL  quads of j-bodies unrolled per packed sub-block loop
+//   NBODY_MIN_CTAS     minimum resident CTAs per SM requested in __launch_bounds__ (0: none)
+#ifndef NBODY_SUB
+#define NBODY_SUB 32
+#endif
+#ifndef NBODY_QUAD_UNROLL
+#define NBODY_QUAD_UNROLL 2
+#endif
+#ifndef NBODY_MIN_CTAS
+#define NBODY_MIN_CTAS 0
+#endif
+constexpr int kSub = NBODY_SUB;  // j-bodies per near-pair check
+constexpr int kQuadUnroll = NBODY_QUAD_UNROLL;
 
 __device__ __forceinline__ void refine_pair(const double* __restrict__ x64, const int i, const int j, const float eps2,
                                             float& dx, float& dy, float& dz, float& r2) {
@@ -339,7 +356,7 @@ __device__ __forceinline__ void tile_pass_f32x2(const float* tx, const float* ty
     const int nb = min(kSub, nj4 - jb);
     float mn0 = 3.0e38f, mn1 = 3.0e38f;
     if (nb == kSub) {
-#pragma unroll 4
+#pragma unroll(kQuadUnroll)
       for (int j = jb; j < jb + kSub; j += 4)
         quad_f32x2<LAW, R, MASK>(tx, ty, tz, tm, j, jt + j, ig, nx, ny, nz, e2, s2, ax, ay, az, pp, mn0, mn1);
     } else {
@@ -372,7 +389,7 @@ __device__ __forceinline__ void tile_pass_f32x2(const float* tx, const float* ty
 }
 
 template <int LAW, int BLOCK, int R, int J>
-__global__ void __launch_bounds__(BLOCK) k_force_mixed2(const PairLaunch L) {
+__global__ void __launch_bounds__(BLOCK, (NBODY_MIN_CTAS > 0 ? NBODY_MIN_CTAS : 1)) k_force_mixed2(const PairLaunch L) {
   static_assert(J % 4 == 0, "tiles hold whole quads of j-bodies");
   constexpr int LPT = (J + BLOCK - 1) / BLOCK;
   __shared__ __align__(16) float tx[2][J];  // double buffer: one barrier per tile
