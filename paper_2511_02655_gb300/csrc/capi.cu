@@ -438,6 +438,10 @@ PostLaunch post_launch(nbody_ctx* c, unsigned mode, double* x, double* v, const 
   P.centre = static_cast<const double*>(c->centre.p);
   P.epart = static_cast<double*>(c->epart.p);
   P.status = c->status;
+  P.eout = nullptr;
+  P.sys_chunk = c->d_sys_chunk;
+  P.n_sys = c->n_sys;
+  P.done = c->counter + 4;
   return P;
 }
 
@@ -451,16 +455,11 @@ nbody_status run_post(nbody_ctx* c, const PostLaunch& P, cudaStream_t st) {
 nbody_status run_centre(nbody_ctx* c, const double* x, const double* m, cudaStream_t st) {
   if (c->cfg.precision != NBODY_MIXED || c->n_total == 0) return NBODY_OK;
   NB_CUDA(c, launch_centre(c->d_chunks, (int)c->chunks.size(), c->d_sys_chunk, c->d_off, c->n_sys, x, m,
-                           static_cast<double*>(c->epart.p), static_cast<double*>(c->centre.p), st));
-  c->launches += c->chunks.empty() ? 1 : 2;
+                           static_cast<double*>(c->epart.p), static_cast<double*>(c->centre.p), c->counter + 5, st));
+  c->launches += c->chunks.empty() ? 0 : 1;
   return NBODY_OK;
 }
 
-nbody_status run_energy_final(nbody_ctx* c, double* out, cudaStream_t st) {
-  NB_CUDA(c, launch_energy_final(c->d_sys_chunk, c->n_sys, static_cast<const double*>(c->epart.p), out, st));
-  ++c->launches;
-  return NBODY_OK;
-}
 
 // The KDK sequence of nbody_step, enqueued on st (eager or under capture).
 nbody_status enqueue_step(nbody_ctx* c, double* x, double* v, const double* m, double* a, int a_valid, int n_steps,
@@ -482,11 +481,9 @@ nbody_status enqueue_step(nbody_ctx* c, double* x, double* v, const double* m, d
     unsigned mode = kCombine | kKickEnd;
     if (rec_now) mode |= kEnergy;
     if (k + 1 < n_steps) mode |= kDrift | kStage;
-    if ((s = run_post(c, post_launch(c, mode, x, v, m, a, nullptr), st))) return s;
-    if (rec_now) {
-      if ((s = run_energy_final(c, elog + (int64_t)rec * c->n_sys * 9, st))) return s;
-      ++rec;
-    }
+    PostLaunch P = post_launch(c, mode, x, v, m, a, nullptr);
+    if (rec_now) P.eout = elog + (int64_t)rec++ * c->n_sys * 9;
+    if ((s = run_post(c, P, st))) return s;
   }
   return NBODY_OK;
 }
@@ -840,10 +837,11 @@ nbody_status nbody_init(nbody_ctx** out, const nbody_config* cfg, int64_t n_syst
   if ((s = ensure(c, c->stage, stage_bytes))) return bail(s);
   if ((s = ensure(c, c->centre, (size_t)c->n_sys * 3 * sizeof(double)))) return bail(s);
   if ((s = ensure(c, c->epart, std::max<size_t>(1, c->chunks.size()) * kEnergyVals * sizeof(double)))) return bail(s);
-  if ((s = ensure(c, c->status_counter, 4 * sizeof(unsigned)))) return bail(s);
+  // [0..1] work counter, [2] status word, [3] unused, [4] energy ticket, [5] centre ticket
+  if ((s = ensure(c, c->status_counter, 8 * sizeof(unsigned)))) return bail(s);
   c->counter = static_cast<unsigned*>(c->status_counter.p);
   c->status = c->counter + 2;
-  if (cudaMemset(c->status_counter.p, 0, 4 * sizeof(unsigned)) != cudaSuccess) return bail(fail(c, NBODY_ECUDA, "memset failed"));
+  if (cudaMemset(c->status_counter.p, 0, 8 * sizeof(unsigned)) != cudaSuccess) return bail(fail(c, NBODY_ECUDA, "memset failed"));
   if (cudaMemset(c->centre.p, 0, (size_t)c->n_sys * 3 * sizeof(double)) != cudaSuccess)
     return bail(fail(c, NBODY_ECUDA, "memset failed"));
   if (cudaMalloc(&c->d_off, (n_systems + 1) * sizeof(int64_t)) != cudaSuccess ||
@@ -959,9 +957,10 @@ nbody_status nbody_energy(nbody_ctx* c, const double* x, const double* v, const 
   if ((s = run_centre(c, x, m, c->stream))) return s;
   if ((s = run_post(c, post_launch(c, kStage, xm, vm, m, as, nullptr), c->stream))) return s;
   if ((s = run_force(c, c->stream, x))) return s;
-  if ((s = run_post(c, post_launch(c, kCombine | kEnergy, xm, vm, m, as, nullptr), c->stream))) return s;
-  // systems without bodies have no chunks and get all-zero records
-  return run_energy_final(c, out, c->stream);
+  // the last CTA writes every system's record (systems without bodies get zeros)
+  PostLaunch P = post_launch(c, kCombine | kEnergy, xm, vm, m, as, nullptr);
+  P.eout = out;
+  return run_post(c, P, c->stream);
 }
 
 nbody_status nbody_adjoint(nbody_ctx* c, const double* x0, const double* v0, const double* m, int32_t T,

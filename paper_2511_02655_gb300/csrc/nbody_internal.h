@@ -94,17 +94,19 @@ struct PostLaunch {
   const double* centre;    // [n_sys][3] staging origin (mixed)
   double* epart;           // [n_chunks][kEnergyVals]
   unsigned* status;        // device status word
+  double* eout;            // kEnergy: nullable [n_sys][9] record formed by the last CTA
+  const int32_t* sys_chunk;  // [n_sys + 1] chunk range of each system
+  int n_sys;
+  unsigned* done;          // last-CTA ticket (zero between launches)
 };
 cudaError_t launch_post(const PostLaunch& P, cudaStream_t st);
 
-// centre[s] = mass-weighted mean position of system s (plain mean if the mass is 0);
-// two passes: per-chunk sums into cpart [n_chunks][kEnergyVals], then per system in order.
+// centre[s] = mass-weighted mean position of system s (plain mean if the mass is 0):
+// per-chunk sums into cpart [n_chunks][kEnergyVals], then per system in a fixed
+// order by the last CTA (ticket `done`, zero between launches).
 cudaError_t launch_centre(const Chunk* chunks, int n_chunks, const int32_t* sys_chunk, const int64_t* off, int n_sys,
-                          const double* x, const double* m, double* cpart, double* centre, cudaStream_t st);
-
-// out[s][9] = {E, K, U, P, L} from the chunk partials, chunk range of s = sys_chunk[s] .. sys_chunk[s+1]-1
-cudaError_t launch_energy_final(const int32_t* sys_chunk, int n_sys, const double* epart, double* out,
-                                cudaStream_t st);
+                          const double* x, const double* m, double* cpart, double* centre, unsigned* done,
+                          cudaStream_t st);
 
 struct AdjLaunch {
   const Chunk* chunks;

@@ -63,6 +63,50 @@ __device__ __forceinline__ void stage_store(int precision, void* stage, int i, d
   }
 }
 
+// Final per-system sums of chunk partials [n_chunks][kEnergyVals], one warp per
+// system, lanes striding over the system's chunks, then a fixed xor-shuffle
+// reduction: the same order whichever CTA runs it.
+template <int NV, typename Emit>
+__device__ __forceinline__ void systems_final(const int32_t* sys_chunk, const int n_sys, const double* cpart,
+                                              Emit emit) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int sy = wid; sy < n_sys; sy += kPostThreads / 32) {
+    double v[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] = 0.0;
+    for (int c = sys_chunk[sy] + lane; c < sys_chunk[sy + 1]; c += 32) {
+#pragma unroll
+      for (int k = 0; k < NV; ++k) v[k] += cpart[(int64_t)c * kEnergyVals + k];
+    }
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] = warp_sum(v[k]);
+    if (lane == 0) emit(sy, v);
+  }
+}
+
+// True in every thread of the CTA that retires last among the grid's CTAs (its
+// partials were published with a fence before the ticket); it resets the ticket.
+__device__ __forceinline__ bool last_cta(unsigned* done) {
+  __shared__ bool s_last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    s_last = atomicAdd(done, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (s_last && threadIdx.x == 0) *done = 0u;
+  return s_last;
+}
+
+__device__ __forceinline__ void emit_energy(double* out, const int sy, const double (&v)[kEnergyVals]) {
+  double* o = out + 9 * (int64_t)sy;
+  o[0] = v[0] + v[1];
+  o[1] = v[0];
+  o[2] = v[1];
+#pragma unroll
+  for (int k = 2; k < kEnergyVals; ++k) o[k + 1] = v[k];
+}
+
 __global__ void __launch_bounds__(kPostThreads) k_post(const PostLaunch P) {
   const Chunk c = P.chunks[blockIdx.x];
   const double4_32a* part = reinterpret_cast<const double4_32a*>(P.part);
@@ -126,19 +170,29 @@ __global__ void __launch_bounds__(kPostThreads) k_post(const PostLaunch P) {
     }
     if (mode & kStage) stage_store(P.precision, P.stage, i, x0, x1, x2, m, cen);
   }
+  if (bad) atomicOr(P.status, kFlagNonFinite);
   if (mode & kEnergy) {
     block_sum<kEnergyVals, kPostThreads>(e);
     if (threadIdx.x == 0) {
 #pragma unroll
       for (int k = 0; k < kEnergyVals; ++k) P.epart[(int64_t)blockIdx.x * kEnergyVals + k] = e[k];
     }
+    // the last CTA to finish forms the per-system records (no separate launch)
+    if (P.eout && last_cta(P.done)) {
+      __threadfence();
+      systems_final<kEnergyVals>(P.sys_chunk, P.n_sys, P.epart,
+                                 [&](int sy, const double (&v)[kEnergyVals]) { emit_energy(P.eout, sy, v); });
+    }
   }
-  if (bad) atomicOr(P.status, kFlagNonFinite);
 }
 
-// Staging origin, pass 1: per chunk, sum m x (3), sum m, sum x (3) into cpart[chunk][8].
-__global__ void __launch_bounds__(kPostThreads) k_centre_part(const Chunk* chunks, const double* x, const double* m,
-                                                              double* cpart) {
+// Staging origin: per chunk, sum m x (3), sum m, sum x (3) into cpart[chunk][8];
+// the last CTA then forms, per system in a fixed order, the mass-weighted mean
+// position (plain mean if the mass is not positive; 0 for an empty system).
+__global__ void __launch_bounds__(kPostThreads) k_centre(const Chunk* chunks, const int32_t* sys_chunk,
+                                                         const int64_t* off, const int n_sys, const double* x,
+                                                         const double* m, double* cpart, double* centre,
+                                                         unsigned* done) {
   const Chunk c = chunks[blockIdx.x];
   double v[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
   for (int i = c.begin + (int)threadIdx.x; i < c.end; i += kPostThreads) {
@@ -152,53 +206,19 @@ __global__ void __launch_bounds__(kPostThreads) k_centre_part(const Chunk* chunk
 #pragma unroll
     for (int k = 0; k < 7; ++k) cpart[(int64_t)blockIdx.x * kEnergyVals + k] = v[k];
   }
-}
-
-// Pass 2: per system, the chunk sums in a fixed order -> mass-weighted mean
-// position (plain mean if the mass is not positive; 0 for an empty system).
-__global__ void __launch_bounds__(32) k_centre_final(const int32_t* sys_chunk, const int64_t* off,
-                                                     const double* cpart, double* centre) {
-  const int s = blockIdx.x;
-  double v[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-  for (int c = sys_chunk[s] + (int)threadIdx.x; c < sys_chunk[s + 1]; c += 32) {
-#pragma unroll
-    for (int k = 0; k < 7; ++k) v[k] += cpart[(int64_t)c * kEnergyVals + k];
-  }
-#pragma unroll
-  for (int k = 0; k < 7; ++k) v[k] = warp_sum(v[k]);
-  if (threadIdx.x == 0) {
-    const int64_t n = off[s + 1] - off[s];
+  if (!last_cta(done)) return;
+  __threadfence();
+  systems_final<7>(sys_chunk, n_sys, cpart, [&](int sy, const double (&w)[7]) {
+    const int64_t n = off[sy + 1] - off[sy];
     double c0 = 0.0, c1 = 0.0, c2 = 0.0;
-    if (v[3] > 0.0 && isfinite(v[3])) {
-      c0 = v[0] / v[3], c1 = v[1] / v[3], c2 = v[2] / v[3];
+    if (w[3] > 0.0 && isfinite(w[3])) {
+      c0 = w[0] / w[3], c1 = w[1] / w[3], c2 = w[2] / w[3];
     } else if (n > 0) {
-      c0 = v[4] / (double)n, c1 = v[5] / (double)n, c2 = v[6] / (double)n;
+      c0 = w[4] / (double)n, c1 = w[5] / (double)n, c2 = w[6] / (double)n;
     }
     if (!(isfinite(c0) && isfinite(c1) && isfinite(c2))) c0 = c1 = c2 = 0.0;
-    centre[3 * s + 0] = c0, centre[3 * s + 1] = c1, centre[3 * s + 2] = c2;
-  }
-}
-
-__global__ void __launch_bounds__(32) k_energy_final(const int32_t* sys_chunk, const double* epart, double* out) {
-  const int s = blockIdx.x;
-  const int lane = threadIdx.x;
-  double v[kEnergyVals];
-#pragma unroll
-  for (int k = 0; k < kEnergyVals; ++k) v[k] = 0.0;
-  for (int c = sys_chunk[s] + lane; c < sys_chunk[s + 1]; c += 32) {
-#pragma unroll
-    for (int k = 0; k < kEnergyVals; ++k) v[k] += epart[(int64_t)c * kEnergyVals + k];
-  }
-#pragma unroll
-  for (int k = 0; k < kEnergyVals; ++k) v[k] = warp_sum(v[k]);
-  if (lane == 0) {
-    double* o = out + 9 * (int64_t)s;
-    o[0] = v[0] + v[1];
-    o[1] = v[0];
-    o[2] = v[1];
-#pragma unroll
-    for (int k = 2; k < kEnergyVals; ++k) o[k + 1] = v[k];
-  }
+    centre[3 * sy + 0] = c0, centre[3 * sy + 1] = c1, centre[3 * sy + 2] = c2;
+  });
 }
 
 __global__ void __launch_bounds__(kPostThreads) k_adj_update(const AdjLaunch A) {
@@ -268,21 +288,10 @@ cudaError_t launch_post(const PostLaunch& P, cudaStream_t st) {
 }
 
 cudaError_t launch_centre(const Chunk* chunks, int n_chunks, const int32_t* sys_chunk, const int64_t* off, int n_sys,
-                          const double* x, const double* m, double* cpart, double* centre, cudaStream_t st) {
-  if (n_sys <= 0) return cudaSuccess;
-  if (n_chunks > 0) {
-    k_centre_part<<<n_chunks, kPostThreads, 0, st>>>(chunks, x, m, cpart);
-    const cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-  }
-  k_centre_final<<<n_sys, 32, 0, st>>>(sys_chunk, off, cpart, centre);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_energy_final(const int32_t* sys_chunk, int n_sys, const double* epart, double* out,
-                                cudaStream_t st) {
-  if (n_sys <= 0) return cudaSuccess;
-  k_energy_final<<<n_sys, 32, 0, st>>>(sys_chunk, epart, out);
+                          const double* x, const double* m, double* cpart, double* centre, unsigned* done,
+                          cudaStream_t st) {
+  if (n_sys <= 0 || n_chunks <= 0) return cudaSuccess;
+  k_centre<<<n_chunks, kPostThreads, 0, st>>>(chunks, sys_chunk, off, n_sys, x, m, cpart, centre, done);
   return cudaGetLastError();
 }
 
