@@ -172,13 +172,18 @@ def cpu_baseline(x, m, G, eps, a_gpu, budget_s=12.0):
     return base, {"median": float(np.median(err)), "max": float(err.max()), "bodies": int(k)}
 
 
-def _event_time(fn, stream):
+def _event_time(fn, stream, nvtx=None):
+    """CUDA-event seconds of fn() on stream; the launches sit in NVTX range `nvtx` (for ncu filters)."""
     import torch
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
+    if nvtx:
+        torch.cuda.nvtx.range_push(nvtx)
     e0.record(stream)
     fn()
     e1.record(stream)
+    if nvtx:
+        torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     return e0.elapsed_time(e1) * 1e-3
 
@@ -202,7 +207,7 @@ def aux_measurements(dev):
     nb.nbody_forces(ctx, xt, mt, at, None, with_phi=False)
     nb.nbody_profile(ctx, True)
     k = 3
-    sec = _event_time(lambda: nb.nbody_step(ctx, xt, vt, mt, at, True, k), stream)
+    sec = _event_time(lambda: nb.nbody_step(ctx, xt, vt, mt, at, True, k), stream, "aux_two_spheres")
     kms, kl = nb.nbody_kernel_time(ctx, 0)
     nb.nbody_sync(ctx)
     out["two_spheres_1m"] = {"interactions_per_s": float(n) * n * k / sec, "steps": k,
@@ -221,7 +226,7 @@ def aux_measurements(dev):
     nb.nbody_forces(ctx, xt, mt, at, None, with_phi=False)
     nb.nbody_step(ctx, xt, vt, mt, at, True, 50, log)  # captures the graph
     l0 = nb.nbody_launch_count(ctx)
-    sec = _event_time(lambda: nb.nbody_step(ctx, xt, vt, mt, at, True, 50, log), stream)
+    sec = _event_time(lambda: nb.nbody_step(ctx, xt, vt, mt, at, True, 50, log), stream, "aux_ensemble")
     nb.nbody_sync(ctx)
     launches = nb.nbody_launch_count(ctx) - l0
     ctx.close()
@@ -240,7 +245,7 @@ def aux_measurements(dev):
         for c1, (xs, vs, ms, a1) in zip(ctxs, bufs):
             nb.nbody_step(c1, xs, vs, ms, a1, True, 1)
 
-    sec64 = _event_time(per_system, stream)
+    sec64 = _event_time(per_system, stream, "aux_ensemble_fp64")
     for c1 in ctxs:
         c1.close()
     out["ensemble_512"] = {"mixed_graph_interactions_per_s": pairs * 50 / sec, "steps": 50,
@@ -264,7 +269,7 @@ def aux_measurements(dev):
             nb.nbody_sync(ctx)
             x2.copy_(xt), v2.copy_(vt)
             xt, vt, at = x2, v2, a2
-        sec = _event_time(lambda: nb.nbody_step(ctx, xt, vt, mt, at, False, steps, logt), stream)
+        sec = _event_time(lambda: nb.nbody_step(ctx, xt, vt, mt, at, False, steps, logt), stream, f"aux_lj_{name}")
         nb.nbody_sync(ctx)
         e = logt.cpu().numpy()[:, 0, 0]
         lj[name] = {"seconds": sec, "interactions_per_s": float(n) * n * (steps + 1) / sec,
@@ -283,7 +288,8 @@ def aux_measurements(dev):
         nb.nbody_step(ctx, xs, vs, mt, at, False, 200)
         lam = 2 * (xs - t)
         nb.nbody_adjoint(ctx, xt, vt, mt, 200, 20, lam, torch.zeros_like(vs))  # tunes the VJP tiling
-        sec = _event_time(lambda: nb.nbody_adjoint(ctx, xt, vt, mt, 200, 20, lam, torch.zeros_like(vs)), stream)
+        sec = _event_time(lambda: nb.nbody_adjoint(ctx, xt, vt, mt, 200, 20, lam, torch.zeros_like(vs)), stream,
+                          f"aux_{name}")
         nb.nbody_sync(ctx)
         out[name] = {"seconds": sec, "steps": 200, "checkpoint_every": 20,
                      "force_equivalent_passes": "1 forward + 1 recompute force pass and 1 VJP pass per step"}
@@ -407,9 +413,11 @@ def run_ours(args):
     k64 = 3
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("fp64_path")
     e0.record(stream)
     nb.nbody_step(ctx64, x64, v64, mt, a64, True, k64)
     e1.record(stream)
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     fp64_value = interactions * k64 / (e0.elapsed_time(e1) * 1e-3)
     ctx64.close()
