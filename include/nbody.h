@@ -112,10 +112,10 @@ nbody_status nbody_set_stream(nbody_ctx* ctx, void* cuda_stream);
 /*
  * All-pairs force evaluation (Sec. V-B): a [N,3] = accelerations, phi [N] =
  * potentials (phi may be NULL). x [N,3], m [N] are read only. Self pairs are
- * excluded from both sums. In NBODY_MIXED, pairs closer than 4 eps take their
- * separation from x in float64 (rounded once to float32) instead of from the
- * float32 staging copy, so that the staging rounding of |x - c| 2^-24 does not
- * dominate close-pair forces.
+ * excluded from both sums. In NBODY_MIXED, pairs closer than 4 eps (4 sigma for
+ * Lennard-Jones) take their separation from the float32 staging copy plus its
+ * staged float32 remainder, (hi_j - hi_i) + (lo_j - lo_i), so that the staging
+ * rounding of |x - c| 2^-24 does not dominate close-pair forces.
  */
 nbody_status nbody_forces(nbody_ctx* ctx, const double* x, const double* m, double* a, double* phi);
 

@@ -106,7 +106,7 @@ struct nbody_ctx {
   bool vjp_ready = false;
 
   // scratch
-  DevBuf stage, stage_w, part, centre, epart, status_counter, a_scratch;
+  DevBuf stage, stage_lo, stage_w, part, centre, epart, status_counter, a_scratch;
   unsigned* counter = nullptr;  // [2]
   unsigned* status = nullptr;   // [1]
 
@@ -356,13 +356,15 @@ nbody_status install_tiling(nbody_ctx* c, Tiling t, bool vjp) {
   return NBODY_OK;
 }
 
-PairLaunch pair_launch(nbody_ctx* c, bool vjp, const double* x64 = nullptr) {
+// refine: the mixed force kernel may use the staged remainders (near pairs).
+PairLaunch pair_launch(nbody_ctx* c, bool vjp, bool refine = false) {
   PairLaunch L{};
-  L.x64 = x64;
+  const bool lo = refine && !vjp && c->cfg.precision == NBODY_MIXED && c->stage_lo.p;
+  L.stage_lo = lo ? static_cast<const float4*>(c->stage_lo.p) : nullptr;
   L.law = vjp ? 0 : c->cfg.law;
   L.sigma2 = c->cfg.lj_sigma * c->cfg.lj_sigma;
   L.r2_near = 0.f;
-  if (!vjp && x64 && c->cfg.precision == NBODY_MIXED)
+  if (lo)
     L.r2_near = c->cfg.law == NBODY_LAW_LJ
                     ? (float)(kNearRadiusSigma * kNearRadiusSigma * L.sigma2 + c->cfg.eps * c->cfg.eps)
                     : (float)(kNearRadiusEps * kNearRadiusEps * c->cfg.eps * c->cfg.eps);
@@ -396,9 +398,9 @@ cudaEvent_t pooled_event(nbody_ctx* c) {
 
 // Launches an all-pairs kernel, bracketed by an event pair when profiling an
 // eager (non-capturing) stream.
-nbody_status run_pair(nbody_ctx* c, cudaStream_t st, bool vjp, const double* x64) {
+nbody_status run_pair(nbody_ctx* c, cudaStream_t st, bool vjp) {
   if (c->n_total == 0) return NBODY_OK;
-  PairLaunch L = pair_launch(c, vjp, x64);
+  PairLaunch L = pair_launch(c, vjp, !vjp);
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (c->profiling && !c->capturing) {
     e0 = pooled_event(c);
@@ -414,9 +416,8 @@ nbody_status run_pair(nbody_ctx* c, cudaStream_t st, bool vjp, const double* x64
   return NBODY_OK;
 }
 
-// x64: the float64 positions the staging was taken from (near-pair refinement).
-nbody_status run_force(nbody_ctx* c, cudaStream_t st, const double* x64) { return run_pair(c, st, false, x64); }
-nbody_status run_vjp(nbody_ctx* c, cudaStream_t st) { return run_pair(c, st, true, nullptr); }
+nbody_status run_force(nbody_ctx* c, cudaStream_t st) { return run_pair(c, st, false); }
+nbody_status run_vjp(nbody_ctx* c, cudaStream_t st) { return run_pair(c, st, true); }
 
 PostLaunch post_launch(nbody_ctx* c, unsigned mode, double* x, double* v, const double* m, double* a, double* phi) {
   PostLaunch P{};
@@ -435,6 +436,7 @@ PostLaunch post_launch(nbody_ctx* c, unsigned mode, double* x, double* v, const 
   P.lj_eps = c->cfg.lj_epsilon;
   P.box = c->cfg.box;
   P.stage = c->stage.p;
+  P.stage_lo = c->stage_lo.p;
   P.centre = static_cast<const double*>(c->centre.p);
   P.epart = static_cast<double*>(c->epart.p);
   P.status = c->status;
@@ -468,7 +470,7 @@ nbody_status enqueue_step(nbody_ctx* c, double* x, double* v, const double* m, d
   if ((s = run_centre(c, x, m, st))) return s;
   if (!a_valid) {
     if ((s = run_post(c, post_launch(c, kStage, x, v, m, a, nullptr), st))) return s;
-    if ((s = run_force(c, st, x))) return s;
+    if ((s = run_force(c, st))) return s;
     if ((s = run_post(c, post_launch(c, kCombine, x, v, m, a, nullptr), st))) return s;
   }
   if (n_steps == 0) return NBODY_OK;
@@ -476,7 +478,7 @@ nbody_status enqueue_step(nbody_ctx* c, double* x, double* v, const double* m, d
   const int every = c->cfg.energy_every;
   int rec = 0;
   for (int k = 0; k < n_steps; ++k) {
-    if ((s = run_force(c, st, x))) return s;
+    if ((s = run_force(c, st))) return s;
     const bool rec_now = elog && every > 0 && (k + 1) % every == 0;
     unsigned mode = kCombine | kKickEnd;
     if (rec_now) mode |= kEnergy;
@@ -538,15 +540,15 @@ nbody_status fill_synthetic(nbody_ctx* c, bool with_w) {
       mass[i] = 1.0 / (double)(e - b);
     }
   }
-  // float64 copy for the near-pair refinement while timing (context work buffer)
-  nbody_status st = ensure(c, c->xw, 3 * (size_t)n * sizeof(double));
-  if (st) return st;
-  NB_CUDA(c, cudaMemcpy(c->xw.p, pos.data(), 3 * (size_t)n * sizeof(double), cudaMemcpyHostToDevice));
   if (c->cfg.precision == NBODY_MIXED) {
-    std::vector<float4> h(n);
-    for (int64_t i = 0; i < n; ++i)
-      h[i] = make_float4((float)pos[3 * i], (float)pos[3 * i + 1], (float)pos[3 * i + 2], (float)mass[i]);
+    std::vector<float4> h(n), hl(n);
+    for (int64_t i = 0; i < n; ++i) {
+      const float hx = (float)pos[3 * i], hy = (float)pos[3 * i + 1], hz = (float)pos[3 * i + 2];
+      h[i] = make_float4(hx, hy, hz, (float)mass[i]);
+      hl[i] = make_float4((float)(pos[3 * i] - hx), (float)(pos[3 * i + 1] - hy), (float)(pos[3 * i + 2] - hz), 0.f);
+    }
     NB_CUDA(c, cudaMemcpy(c->stage.p, h.data(), n * sizeof(float4), cudaMemcpyHostToDevice));
+    if (c->stage_lo.p) NB_CUDA(c, cudaMemcpy(c->stage_lo.p, hl.data(), n * sizeof(float4), cudaMemcpyHostToDevice));
     if (with_w) {
       for (int64_t i = 0; i < n; ++i) h[i] = make_float4((float)u01(), (float)u01(), (float)u01(), 0.f);
       NB_CUDA(c, cudaMemcpy(c->stage_w.p, h.data(), n * sizeof(float4), cudaMemcpyHostToDevice));
@@ -570,7 +572,7 @@ nbody_status fill_synthetic(nbody_ctx* c, bool with_w) {
 // slices pay for their partial-sum traffic and the tail of the schedule
 // counts; long lists are timed on a prefix of two items per persistent CTA.
 nbody_status time_tiling(nbody_ctx* c, bool vjp, double* cost) {
-  PairLaunch L = pair_launch(c, vjp, vjp ? nullptr : static_cast<const double*>(c->xw.p));
+  PairLaunch L = pair_launch(c, vjp, !vjp);
   const Tiling& t = vjp ? c->vt : c->ft;
   auto launch = [&](const PairLaunch& P) {
     return vjp ? launch_vjp(c->cfg.precision, P, c->stream) : launch_force(c->cfg.precision, P, c->stream);
@@ -739,7 +741,7 @@ void free_ctx(nbody_ctx* c) {
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   for (auto& u : c->ev_used) cudaEventDestroy(u.second.first), cudaEventDestroy(u.second.second);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
-  for (DevBuf* b : {&c->stage, &c->stage_w, &c->part, &c->centre, &c->epart, &c->status_counter, &c->a_scratch,
+  for (DevBuf* b : {&c->stage, &c->stage_lo, &c->stage_w, &c->part, &c->centre, &c->epart, &c->status_counter, &c->a_scratch,
                     &c->xw, &c->vw, &c->aw, &c->ckpt, &c->traj, &c->hx, &c->hv, &c->hm, &c->ha, &c->hlog})
     release(*b);
   if (c->d_chunks) cudaFree(c->d_chunks);
@@ -835,6 +837,7 @@ nbody_status nbody_init(nbody_ctx** out, const nbody_config* cfg, int64_t n_syst
   const size_t n = (size_t)c->n_total;
   const size_t stage_bytes = n * (cfg->precision == NBODY_MIXED ? sizeof(float4) : sizeof(double4_32a));
   if ((s = ensure(c, c->stage, stage_bytes))) return bail(s);
+  if (cfg->precision == NBODY_MIXED && (s = ensure(c, c->stage_lo, n * sizeof(float4)))) return bail(s);
   if ((s = ensure(c, c->centre, (size_t)c->n_sys * 3 * sizeof(double)))) return bail(s);
   if ((s = ensure(c, c->epart, std::max<size_t>(1, c->chunks.size()) * kEnergyVals * sizeof(double)))) return bail(s);
   // [0..1] work counter, [2] status word, [3] unused, [4] energy ticket, [5] centre ticket
@@ -886,7 +889,7 @@ nbody_status nbody_forces(nbody_ctx* c, const double* x, const double* m, double
   double* xm = const_cast<double*>(x);
   if ((s = run_centre(c, x, m, c->stream))) return s;
   if ((s = run_post(c, post_launch(c, kStage, xm, nullptr, m, a, nullptr), c->stream))) return s;
-  if ((s = run_force(c, c->stream, x))) return s;
+  if ((s = run_force(c, c->stream))) return s;
   return run_post(c, post_launch(c, kCombine, xm, nullptr, m, a, phi), c->stream);
 }
 
@@ -956,7 +959,7 @@ nbody_status nbody_energy(nbody_ctx* c, const double* x, const double* v, const 
   double* as = static_cast<double*>(c->a_scratch.p);
   if ((s = run_centre(c, x, m, c->stream))) return s;
   if ((s = run_post(c, post_launch(c, kStage, xm, vm, m, as, nullptr), c->stream))) return s;
-  if ((s = run_force(c, c->stream, x))) return s;
+  if ((s = run_force(c, c->stream))) return s;
   // the last CTA writes every system's record (systems without bodies get zeros)
   PostLaunch P = post_launch(c, kCombine | kEnergy, xm, vm, m, as, nullptr);
   P.eout = out;
@@ -1012,7 +1015,7 @@ nbody_status nbody_adjoint(nbody_ctx* c, const double* x0, const double* v0, con
   NB_CUDA(c, cudaMemcpyAsync(xw, x0, n3b, cudaMemcpyDeviceToDevice, st));
   NB_CUDA(c, cudaMemcpyAsync(vw, v0, n3b, cudaMemcpyDeviceToDevice, st));
   if ((s = run_post(c, post_launch(c, kStage, xw, vw, m, aw, nullptr), st))) return s;
-  if ((s = run_force(c, st, xw))) return s;
+  if ((s = run_force(c, st))) return s;
   if ((s = run_post(c, post_launch(c, kCombine, xw, vw, m, aw, nullptr), st))) return s;
 
   // one KDK step on (xw, vw, aw), optionally copying x after the drift
@@ -1021,7 +1024,7 @@ nbody_status nbody_adjoint(nbody_ctx* c, const double* x0, const double* v0, con
     PostLaunch P = post_launch(c, kDrift | kStage, xw, vw, m, aw, nullptr);
     P.x_copy = xcopy;
     if ((r = run_post(c, P, st))) return r;
-    if ((r = run_force(c, st, xw))) return r;
+    if ((r = run_force(c, st))) return r;
     return run_post(c, post_launch(c, kCombine | kKickEnd, xw, vw, m, aw, nullptr), st);
   };
 

@@ -28,8 +28,7 @@ namespace {
 // Near-pair refinement. The float32 staging coordinates carry an absolute
 // rounding error of about |x - c| 2^-24, harmless for distant pairs but
 // dominant for pairs closer than a few softening lengths. Pairs with s^2 below
-// the refinement radius get d recomputed from the caller's float64 positions,
-// rounded once. Such pairs are rare, so they are found without a branch per
+// the refinement radius get d recomputed with the staged remainders (below). Such pairs are rare, so they are found without a branch per
 // pair: every pair folds its s^2 into a running minimum (one FMNMX), and after
 // each sub-block of kSub j-bodies a thread whose minimum fell below the radius
 // rescans that sub-block (s^2 only) and, for each near pair, adds the refined
@@ -53,11 +52,17 @@ namespace {
 constexpr int kSub = NBODY_SUB;  // j-bodies per near-pair check
 constexpr int kQuadUnroll = NBODY_QUAD_UNROLL;
 
-__device__ __forceinline__ void refine_pair(const double* __restrict__ x64, const int i, const int j, const float eps2,
-                                            float& dx, float& dy, float& dz, float& r2) {
-  dx = (float)(x64[3 * (int64_t)j + 0] - x64[3 * (int64_t)i + 0]);
-  dy = (float)(x64[3 * (int64_t)j + 1] - x64[3 * (int64_t)i + 1]);
-  dz = (float)(x64[3 * (int64_t)j + 2] - x64[3 * (int64_t)i + 2]);
+// d of a near pair from the staged float32 parts x - c = hi + lo (lo is the
+// float32 remainder of the float64 value): the hi difference is exact for close
+// pairs (Sterbenz) and the lo difference restores the bits the staging dropped,
+// so d is good to a rounding of |d| itself, in float32 arithmetic only.
+__device__ __forceinline__ void refine_pair(const float4* __restrict__ lo, const int i, const int j, const float dhx,
+                                            const float dhy, const float dhz, const float eps2, float& dx, float& dy,
+                                            float& dz, float& r2) {
+  const float4 lj = lo[j], li = lo[i];
+  dx = dhx + (lj.x - li.x);
+  dy = dhy + (lj.y - li.y);
+  dz = dhz + (lj.z - li.z);
   r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
 }
 
@@ -69,7 +74,7 @@ __device__ __forceinline__ void refine_pair(const double* __restrict__ x64, cons
 template <int LAW = 0>
 __device__ __forceinline__ void correct_pair(const float4 q, const int jg, const int ig, const int i_end,
                                              const float xi, const float yi, const float zi, const float eps2,
-                                             const float r2c, const double* __restrict__ x64, float& ax, float& ay,
+                                             const float r2c, const float4* __restrict__ lo, float& ax, float& ay,
                                              float& az, float& pp, const float s2 = 0.f) {
   const float dx = q.x - xi;
   const float dy = q.y - yi;
@@ -77,7 +82,7 @@ __device__ __forceinline__ void correct_pair(const float4 q, const int jg, const
   const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
   if (!(r2 < r2c) || ig >= i_end || jg < 0 || ig == jg) return;
   float rx, ry, rz, rr2;
-  refine_pair(x64, ig, jg, eps2, rx, ry, rz, rr2);
+  refine_pair(lo, ig, jg, dx, dy, dz, eps2, rx, ry, rz, rr2);
   if (LAW == 0) {
     const float iu = rsq_approx(r2);
     const float msu = q.w * iu;
@@ -128,7 +133,7 @@ template <int R, bool MASK>
 __device__ __forceinline__ void tile_pass_f32(const float4* tile, const int jt, const int nj, const float (&xi)[R],
                                               const float (&yi)[R], const float (&zi)[R], const int (&ig)[R],
                                               const int i_end, const float eps2, const float r2c,
-                                              const double* __restrict__ x64, float (&ax)[R], float (&ay)[R],
+                                              const float4* __restrict__ lo, float (&ax)[R], float (&ay)[R],
                                               float (&az)[R], float (&pp)[R]) {
   for (int jb = 0; jb < nj; jb += kSub) {
     const int nb = min(kSub, nj - jb);
@@ -154,7 +159,7 @@ __device__ __forceinline__ void tile_pass_f32(const float4* tile, const int jt, 
         const float4 q = tile[j];
 #pragma unroll
         for (int r = 0; r < R; ++r)
-          correct_pair(q, jt + j, ig[r], i_end, xi[r], yi[r], zi[r], eps2, r2c, x64, ax[r], ay[r], az[r], pp[r]);
+          correct_pair(q, jt + j, ig[r], i_end, xi[r], yi[r], zi[r], eps2, r2c, lo, ax[r], ay[r], az[r], pp[r]);
       }
     }
   }
@@ -169,7 +174,7 @@ __global__ void __launch_bounds__(BLOCK) k_force_mixed(const PairLaunch L) {
   double4_32a* __restrict__ part = reinterpret_cast<double4_32a*>(L.part);
   const float eps2 = (float)L.eps2;
   const float r2c = L.r2_near;
-  const double* __restrict__ x64 = L.x64;
+  const float4* __restrict__ lo = L.stage_lo;
 
   for (;;) {
     const int it = next_item(L.counter, &s_item);  // also a barrier: the buffers are free
@@ -214,9 +219,9 @@ __global__ void __launch_bounds__(BLOCK) k_force_mixed(const PairLaunch L) {
       for (int r = 0; r < R; ++r) ax[r] = ay[r] = az[r] = pp[r] = 0.f;
       const bool diag = (jt < w.i_end) && (w.i_begin < jt + nj);
       if (diag)
-        tile_pass_f32<R, true>(tile[buf], jt, nj, xi, yi, zi, ig, w.i_end, eps2, r2c, x64, ax, ay, az, pp);
+        tile_pass_f32<R, true>(tile[buf], jt, nj, xi, yi, zi, ig, w.i_end, eps2, r2c, lo, ax, ay, az, pp);
       else
-        tile_pass_f32<R, false>(tile[buf], jt, nj, xi, yi, zi, ig, w.i_end, eps2, r2c, x64, ax, ay, az, pp);
+        tile_pass_f32<R, false>(tile[buf], jt, nj, xi, yi, zi, ig, w.i_end, eps2, r2c, lo, ax, ay, az, pp);
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         two_sum_acc(hx[r], lx[r], ax[r]);
@@ -349,7 +354,7 @@ __device__ __forceinline__ void tile_pass_f32x2(const float* tx, const float* ty
                                                 const int jt, const int nj, const int (&ig)[R], const float2 (&nx)[R],
                                                 const float2 (&ny)[R], const float2 (&nz)[R], const int i_end,
                                                 const float2 e2, const float2 s2, const float r2c,
-                                                const double* __restrict__ x64, float2 (&ax)[R], float2 (&ay)[R],
+                                                const float4* __restrict__ lo, float2 (&ax)[R], float2 (&ay)[R],
                                                 float2 (&az)[R], float2 (&pp)[R]) {
   const int nj4 = (nj + 3) & ~3;  // the tile is padded to a multiple of four
   for (int jb = 0; jb < nj4; jb += kSub) {
@@ -377,10 +382,10 @@ __device__ __forceinline__ void tile_pass_f32x2(const float* tx, const float* ty
           const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __ffma2_rn(dz, dz, e2)));
           if (r2.x < r2c && j < nj)
             correct_pair<LAW>(make_float4(tx[j], ty[j], tz[j], tm[j]), jt + j, ig[r], i_end, -nx[r].x, -ny[r].x,
-                              -nz[r].x, e2.x, r2c, x64, ax[r].x, ay[r].x, az[r].x, pp[r].x, s2.x);
+                              -nz[r].x, e2.x, r2c, lo, ax[r].x, ay[r].x, az[r].x, pp[r].x, s2.x);
           if (r2.y < r2c && j + 1 < nj)
             correct_pair<LAW>(make_float4(tx[j + 1], ty[j + 1], tz[j + 1], tm[j + 1]), jt + j + 1, ig[r], i_end,
-                              -nx[r].x, -ny[r].x, -nz[r].x, e2.x, r2c, x64, ax[r].y, ay[r].y, az[r].y, pp[r].y,
+                              -nx[r].x, -ny[r].x, -nz[r].x, e2.x, r2c, lo, ax[r].y, ay[r].y, az[r].y, pp[r].y,
                               s2.x);
         }
       }
@@ -403,7 +408,7 @@ __global__ void __launch_bounds__(BLOCK, (NBODY_MIN_CTAS > 0 ? NBODY_MIN_CTAS : 
   const float2 e2 = make_float2(eps2, eps2);
   const float2 s2 = make_float2((float)L.sigma2, (float)L.sigma2);
   const float r2c = L.r2_near;
-  const double* __restrict__ x64 = L.x64;
+  const float4* __restrict__ lo = L.stage_lo;
 
   for (;;) {
     const int it = next_item(L.counter, &s_item);  // also a barrier: the buffers are free
@@ -459,10 +464,10 @@ __global__ void __launch_bounds__(BLOCK, (NBODY_MIN_CTAS > 0 ? NBODY_MIN_CTAS : 
       const bool diag = (jt < w.i_end) && (w.i_begin < jt + nj);
       if (diag)
         tile_pass_f32x2<LAW, R, true>(tx[buf], ty[buf], tz[buf], tm[buf], jt, nj, ig, nx, ny, nz, w.i_end, e2, s2,
-                                      r2c, x64, ax, ay, az, pp);
+                                      r2c, lo, ax, ay, az, pp);
       else
         tile_pass_f32x2<LAW, R, false>(tx[buf], ty[buf], tz[buf], tm[buf], jt, nj, ig, nx, ny, nz, w.i_end, e2, s2,
-                                       r2c, x64, ax, ay, az, pp);
+                                       r2c, lo, ax, ay, az, pp);
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         two_sum_acc(hx[r], lx[r], ax[r].x + ax[r].y);

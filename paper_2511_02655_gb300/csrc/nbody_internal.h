@@ -46,7 +46,7 @@ struct PairLaunch {
   double* part;          // force: double4_32a [slices][N]; VJP: 2 x double4_32a [slices][N]
   int64_t n_total;
   double eps2;
-  const double* x64;     // force (mixed): caller's float64 positions [N,3] for near-pair refinement
+  const float4* stage_lo;  // force (mixed): float32 remainders (x - c) - hi [N], near-pair refinement
   float r2_near;         // force (mixed): refine pairs with s^2 below this (0 = never)
   int variant;           // force (mixed): 0 scalar float32, 1 packed float32x2
   int law;               // 0 softened gravity, 1 Lennard-Jones
@@ -91,6 +91,7 @@ struct PostLaunch {
   double lj_eps;
   double box;              // > 0: reflecting walls of [0, box]^3 applied after the drift
   void* stage;             // float4 / double4_32a [N]
+  void* stage_lo;          // mixed: float4 remainders of the staged coordinates [N] (nullable)
   const double* centre;    // [n_sys][3] staging origin (mixed)
   double* epart;           // [n_chunks][kEnergyVals]
   unsigned* status;        // device status word

@@ -53,11 +53,18 @@ __device__ __forceinline__ void reflect(double& x, double& v, const double box) 
   }
 }
 
+// Staging entry of body i. Mixed: float4 (x - c, m) rounded to float32 and,
+// when lo is given, the float32 remainders (x - c) - hi used by the near-pair
+// refinement of the force kernels. FP64: double4 (x, m).
 __device__ __forceinline__ void stage_store(int precision, void* stage, int i, double x, double y, double z,
-                                            double m, const double* c) {
+                                            double m, const double* c, void* lo = nullptr) {
   if (precision == 1) {
-    static_cast<float4*>(stage)[i] =
-        make_float4((float)(x - c[0]), (float)(y - c[1]), (float)(z - c[2]), (float)m);
+    const double X = x - c[0], Y = y - c[1], Z = z - c[2];
+    const float hx = (float)X, hy = (float)Y, hz = (float)Z;
+    static_cast<float4*>(stage)[i] = make_float4(hx, hy, hz, (float)m);
+    if (lo)
+      static_cast<float4*>(lo)[i] =
+          make_float4((float)(X - (double)hx), (float)(Y - (double)hy), (float)(Z - (double)hz), 0.f);
   } else {
     static_cast<double4_32a*>(stage)[i] = make_double4_32a(x, y, z, m);
   }
@@ -168,7 +175,7 @@ __global__ void __launch_bounds__(kPostThreads) k_post(const PostLaunch P) {
       }
       if (mode & (kKickEnd | kDrift)) P.v[3 * i + 0] = v0, P.v[3 * i + 1] = v1, P.v[3 * i + 2] = v2;
     }
-    if (mode & kStage) stage_store(P.precision, P.stage, i, x0, x1, x2, m, cen);
+    if (mode & kStage) stage_store(P.precision, P.stage, i, x0, x1, x2, m, cen, P.stage_lo);
   }
   if (bad) atomicOr(P.status, kFlagNonFinite);
   if (mode & kEnergy) {
