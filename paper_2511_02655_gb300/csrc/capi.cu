@@ -24,7 +24,7 @@ namespace {
 
 constexpr int64_t kMaxBodies = int64_t(1) << 29;      // 3 * N fits in int32 index arithmetic
 constexpr size_t kMaxPartialBytes = size_t(1) << 30;  // cap on per-slice partial-sum memory
-constexpr int kMinTilesPerSlice = 4;
+constexpr int kMinTilesPerSlice = 1;  // shortest slice in j-tiles (small systems need many items)
 constexpr double kTuneLargePairs = 4.0e10;  // above this many pairs per force pass, tune on short slices
 constexpr int kTuneSlice = 8192;
 
@@ -255,6 +255,22 @@ int auto_slice(const nbody_ctx* c, const Tiling& t, int n_ctas) {
     if (items >= 4 * (int64_t)n_ctas) best = L;
   }
   return (int)std::min<int64_t>(best, INT32_MAX / 2);
+}
+
+// Work items of tiling t with slice length L (the count build_items produces).
+int64_t count_items(const nbody_ctx* c, const Tiling& t, int64_t L) {
+  const int64_t itile = (int64_t)t.block * t.ipt;
+  int64_t items = 0;
+  for (int s = 0; s < c->n_sys; ++s) {
+    const int64_t n = c->offsets[s + 1] - c->offsets[s];
+    if (n <= 0) continue;
+    int64_t ns = (n + L - 1) / L;
+    int64_t len = (n + ns - 1) / ns;
+    len = ((len + t.jtile - 1) / t.jtile) * t.jtile;
+    ns = (n + len - 1) / len;
+    items += ((n + itile - 1) / itile) * ns;
+  }
+  return items;
 }
 
 void build_items(const nbody_ctx* c, const Tiling& t, std::vector<WorkItem>& items, std::vector<int>& sys_slices,
@@ -677,6 +693,14 @@ nbody_status autotune(nbody_ctx* c, bool vjp) {
     if ((s = install_tiling(c, t, vjp))) return s;
     double cost = 0;
     if ((s = time_tiling(c, vjp, &cost))) return s;
+    if (large && t0.slice == 0) {
+      // The prefix timing cannot see the last, partly filled wave of the final
+      // (longer-slice) work list: scale by the wave quantisation of that list.
+      const int ctas = (vjp ? c->vt : c->ft).n_ctas;
+      const int64_t items = count_items(c, t0, auto_slice(c, t0, ctas));
+      const double waves = (double)items / std::max(1, ctas);
+      if (waves > 0) cost *= std::ceil(waves) / waves;
+    }
     if (verbose)
       fprintf(stderr, "nbody tune %s: variant=%d block=%d ipt=%d jtile=%d slice=%d ctas=%d items=%d -> %.4g ps/pair\n",
               vjp ? "vjp" : "force", (vjp ? c->vt : c->ft).variant, t.block, t.ipt, t.jtile,

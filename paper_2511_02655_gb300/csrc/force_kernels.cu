@@ -36,7 +36,8 @@ namespace {
 // Compile-time tuning of the mixed kernels. The defaults won a sweep on GB300
 // (Plummer N = 65 536 and two spheres N = 1 048 576): 32-body sub-blocks were
 // 2-5% faster than 16 or 8; unroll depth 2 vs 4 within 1%; requesting a minimum
-// number of resident CTAs did not help.
+// number of resident CTAs did not help; folding both s^2 of a packed pair with one
+// three-input min (min.f32 d, a, b, c) instead of two FMNMX was within noise.
 //   NBODY_SUB          j-bodies per near-pair check (sub-block)
 //   NBODY_QUAD_UNROLL  quads of j-bodies unrolled per packed sub-block loop
 //   NBODY_MIN_CTAS     minimum resident CTAs per SM requested in __launch_bounds__ (0: none)

@@ -85,3 +85,30 @@ def test_lj_adjoint_unsupported(nb):
     with pytest.raises(nb.NBodyError) as ei:
         nb.nbody_adjoint(ctx, xt, vt, mt, 5, 2, xt.clone(), vt.clone())
     assert ei.value.status == 6
+
+
+def test_lj_graph_replay_matches_eager(nb):
+    import torch
+    x, v, m, box = inputs.lj_gas(3000, seed=12, density=0.1)
+    outs = []
+    for flags in (0, nb.FLAG_GRAPH):
+        ctx = nb.nbody_init(law=nb.LENNARD_JONES, precision=nb.MIXED, n=3000, dt=5e-3, box=box, energy_every=5,
+                            flags=flags, block=128, i_per_thread=1, j_tile=256, slice=512)
+        xt, vt, mt = to_dev(x, v, m)
+        at = torch.empty_like(xt)
+        log = torch.empty((4, 1, 9), dtype=torch.float64, device="cuda")
+        for _ in range(2):
+            nb.nbody_step(ctx, xt, vt, mt, at, False, 20, log)
+        nb.nbody_sync(ctx)
+        outs.append((xt.cpu(), vt.cpu(), at.cpu(), log.cpu()))
+    for a, b in zip(*outs):
+        assert torch.equal(a, b)
+
+
+def test_lj_unsoftened_coincident_bodies_flag_nonfinite(nb):
+    x = np.array([[1.0, 1.0, 1.0], [1.0, 1.0, 1.0], [3.0, 1.0, 1.0]])
+    ctx = nb.nbody_init(law=nb.LENNARD_JONES, precision=nb.FP64, n=3, dt=1e-3)
+    nb.nbody_forces(ctx, *to_dev(x, np.ones(3)))
+    with pytest.raises(nb.NBodyError) as ei:
+        nb.nbody_sync(ctx)
+    assert ei.value.status == 5
