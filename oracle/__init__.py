@@ -15,6 +15,8 @@ Sec. II-A and Sec. V-B, Sec. VI):
 * ``kdk``         leapfrog kick-drift-kick steps, one force evaluation per step
 * ``force_vjp``   w -> (dL/dx, dL/dm) through a(x, m) for dL/da = w
 * ``adjoint``     gradients of a final-state loss w.r.t. x0, v0, m through KDK
+* ``param_vjp``   w -> (sum_k w_k . da_k/dG, sum_k w_k . da_k/deps)
+* ``adjoint_params``  ``adjoint`` plus dL/dG and dL/deps
 * ``lj_*``         the same for the paper's Lennard-Jones pair law (Eq. 1):
                    a_i = F_i / m_i, phi_i = sum_j V(r_ij) / m_i, and KDK with
                    reflecting walls of the box [0, box]^3
@@ -61,12 +63,15 @@ def _load():
             lib.oracle_kdk.argtypes = [i64, p, p, p, d, d, d, i32, p, i32, i32, p, i32]
             lib.oracle_force_vjp.argtypes = [i64, p, p, p, d, d, p, p, i32]
             lib.oracle_adjoint.argtypes = [i64, p, p, p, d, d, d, i32, p, p, p, p, p, i32]
+            lib.oracle_param_vjp.argtypes = [i64, p, p, p, d, d, p, i32]
+            lib.oracle_adjoint_params.argtypes = [i64, p, p, p, d, d, d, i32, p, p, p, p, p, p, i32]
             lib.oracle_lj_forces.argtypes = [i64, p, p, d, d, d, p, p, i32]
             lib.oracle_lj_forces_at.argtypes = [i64, p, p, d, d, d, p, i64, p, p, i32]
             lib.oracle_lj_energy.argtypes = [i64, p, p, p, d, d, d, p, i32]
             lib.oracle_lj_kdk.argtypes = [i64, p, p, p, d, d, d, d, d, i32, p, i32, i32, p, i32]
             for f in ("oracle_forces", "oracle_forces_at", "oracle_energy", "oracle_kdk",
-                      "oracle_force_vjp", "oracle_adjoint", "oracle_lj_forces", "oracle_lj_forces_at",
+                      "oracle_force_vjp", "oracle_adjoint", "oracle_param_vjp", "oracle_adjoint_params",
+                      "oracle_lj_forces", "oracle_lj_forces_at",
                       "oracle_lj_energy", "oracle_lj_kdk"):
                 getattr(lib, f).restype = i32
             _lib = lib
@@ -167,6 +172,29 @@ def adjoint(x0, v0, m, G, eps, dt, n_steps, lam_xT, lam_vT, threads=0):
     _check(_load().oracle_adjoint(n, _ptr(x0), _ptr(v0), _ptr(m), G, eps, dt, int(n_steps), _ptr(lx), _ptr(lv),
                                   _ptr(gx), _ptr(gv), _ptr(gm), threads), "oracle_adjoint")
     return gx, gv, gm
+
+
+def param_vjp(x, m, w, G=1.0, eps=0.0, threads=0):
+    """(sum_k w_k . da_k/dG, sum_k w_k . da_k/deps) at positions x."""
+    m = _f64(m)
+    n = m.shape[0]
+    x, w = _f64(x, (n, 3)), _f64(w, (n, 3))
+    out = np.zeros(2)
+    _check(_load().oracle_param_vjp(n, _ptr(x), _ptr(m), _ptr(w), G, eps, _ptr(out), threads), "oracle_param_vjp")
+    return float(out[0]), float(out[1])
+
+
+def adjoint_params(x0, v0, m, G, eps, dt, n_steps, lam_xT, lam_vT, threads=0):
+    """(g_x0, g_v0, g_m, (dL/dG, dL/deps)) for a loss with dL/dx_T = lam_xT, dL/dv_T = lam_vT."""
+    m = _f64(m)
+    n = m.shape[0]
+    x0, v0 = _f64(x0, (n, 3)), _f64(v0, (n, 3))
+    lx, lv = _f64(lam_xT, (n, 3)), _f64(lam_vT, (n, 3))
+    gx, gv, gm, gp = np.zeros((n, 3)), np.zeros((n, 3)), np.zeros(n), np.zeros(2)
+    _check(_load().oracle_adjoint_params(n, _ptr(x0), _ptr(v0), _ptr(m), G, eps, dt, int(n_steps), _ptr(lx),
+                                         _ptr(lv), _ptr(gx), _ptr(gv), _ptr(gm), _ptr(gp), threads),
+           "oracle_adjoint_params")
+    return gx, gv, gm, (float(gp[0]), float(gp[1]))
 
 
 def trajectory_loss(x0, v0, m, G, eps, dt, n_steps, target, threads=0):

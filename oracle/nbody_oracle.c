@@ -23,6 +23,10 @@
  *     J(d)   = I / s^3 - 3 d d^T / s^5               (derivative of d / s^3)
  *     gx_k   = G sum_{j != k} J(d_kj) (m_k w_j - m_j w_k)
  *     gm_j   = G sum_{i != j} w_i . d_ij / s_ij^3
+ *   and for the two model parameters (a depends on G linearly and on eps
+ *   through s^2 = |d|^2 + eps^2):
+ *     dL/dG   = sum_k w_k . sum_{j != k} m_j d_kj / s_kj^3
+ *     dL/deps = sum_k w_k . (-3 G eps) sum_{j != k} m_j d_kj / s_kj^5
  *
  * The pair law (softened Newtonian gravity) replaces the paper's Lennard-Jones
  * law (Eq. 1); the all-pairs structure, the Verlet half-step integrator and the
@@ -295,6 +299,56 @@ int oracle_force_vjp(int64_t n, const double* x, const double* m, const double* 
   return 0;
 }
 
+typedef struct {
+  int64_t n;
+  const double *x, *m, *w;
+  double G, eps;
+  double* rows; /* [n][2]: per-body terms of dL/dG and dL/deps */
+} pvjp_args;
+
+static void param_vjp_rows(int64_t lo, int64_t hi, void* p) {
+  pvjp_args* f = (pvjp_args*)p;
+  const double e2 = f->eps * f->eps;
+  for (int64_t k = lo; k < hi; ++k) {
+    double da_dG[3] = {0.0, 0.0, 0.0}, da_deps[3] = {0.0, 0.0, 0.0};
+    for (int64_t j = 0; j < f->n; ++j) {
+      if (j == k) continue;
+      double d[3];
+      for (int c = 0; c < 3; ++c) d[c] = f->x[3 * j + c] - f->x[3 * k + c];
+      double s2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2] + e2;
+      double inv_s = 1.0 / sqrt(s2);
+      double inv_s3 = inv_s * inv_s * inv_s;
+      double inv_s5 = inv_s3 * inv_s * inv_s;
+      for (int c = 0; c < 3; ++c) {
+        da_dG[c] += f->m[j] * d[c] * inv_s3;                          /* d a_k / dG */
+        da_deps[c] += -3.0 * f->G * f->eps * f->m[j] * d[c] * inv_s5; /* d a_k / d eps */
+      }
+    }
+    const double* wk = f->w + 3 * k;
+    f->rows[2 * k + 0] = wk[0] * da_dG[0] + wk[1] * da_dG[1] + wk[2] * da_dG[2];
+    f->rows[2 * k + 1] = wk[0] * da_deps[0] + wk[1] * da_deps[1] + wk[2] * da_deps[2];
+  }
+}
+
+/* out[0] = sum_k w_k . d a_k / dG, out[1] = sum_k w_k . d a_k / d eps. */
+int oracle_param_vjp(int64_t n, const double* x, const double* m, const double* w, double G, double eps, double* out,
+                     int nthreads) {
+  if (n < 0 || !out || (n > 0 && (!x || !m || !w))) return 1;
+  out[0] = out[1] = 0.0;
+  if (n == 0) return 0;
+  double* rows = (double*)malloc(sizeof(double) * 2 * (size_t)n);
+  if (!rows) return 2;
+  pvjp_args f = {n, x, m, w, G, eps, rows};
+  parallel_rows(n, nthreads, param_vjp_rows, &f);
+  csum acc[2] = {{0.0, 0.0}, {0.0, 0.0}};
+  for (int64_t k = 0; k < n; ++k)
+    for (int c = 0; c < 2; ++c) csum_add(&acc[c], rows[2 * k + c]);
+  out[0] = csum_get(&acc[0]);
+  out[1] = csum_get(&acc[1]);
+  free(rows);
+  return 0;
+}
+
 /*
  * Gradients of a loss L(x_T, v_T) with respect to x0, v0 and m through n_steps
  * KDK steps, given lam_xT = dL/dx_T and lam_vT = dL/dv_T. The forward
@@ -304,9 +358,9 @@ int oracle_force_vjp(int64_t n, const double* x, const double* m, const double* 
  *   lam_vh += dt lam_x'
  *   lam_v   = lam_vh;  lam_x   = lam_x' + dt/2 gx(x; lam_vh);  g_m += dt/2 gm(x; lam_vh)
  */
-int oracle_adjoint(int64_t n, const double* x0, const double* v0, const double* m, double G, double eps, double dt,
-                   int n_steps, const double* lam_xT, const double* lam_vT, double* g_x0, double* g_v0, double* g_m,
-                   int nthreads) {
+static int adjoint_sweep(int64_t n, const double* x0, const double* v0, const double* m, double G, double eps,
+                         double dt, int n_steps, const double* lam_xT, const double* lam_vT, double* g_x0,
+                         double* g_v0, double* g_m, double* g_params, int nthreads) {
   if (n < 0 || n_steps < 0) return 1;
   if (n == 0) return 0;
   if (!x0 || !v0 || !m || !lam_xT || !lam_vT || !g_x0 || !g_v0 || !g_m) return 1;
@@ -336,18 +390,42 @@ int oracle_adjoint(int64_t n, const double* x0, const double* v0, const double* 
   for (int s = n_steps - 1; s >= 0; --s) {
     const double* x_new = traj + sz * (size_t)(s + 1);
     const double* x_old = traj + sz * (size_t)s;
+    double pg[2];
     memcpy(lam_vh, g_v0, sizeof(double) * sz);
     oracle_force_vjp(n, x_new, m, g_v0, G, eps, gx, gmv, nthreads);
+    if (g_params) {
+      oracle_param_vjp(n, x_new, m, g_v0, G, eps, pg, nthreads);
+      g_params[0] += 0.5 * dt * pg[0], g_params[1] += 0.5 * dt * pg[1];
+    }
     for (size_t k = 0; k < sz; ++k) g_x0[k] += 0.5 * dt * gx[k];
     for (int64_t k = 0; k < n; ++k) g_m[k] += 0.5 * dt * gmv[k];
     for (size_t k = 0; k < sz; ++k) lam_vh[k] += dt * g_x0[k];
     oracle_force_vjp(n, x_old, m, lam_vh, G, eps, gx, gmv, nthreads);
+    if (g_params) {
+      oracle_param_vjp(n, x_old, m, lam_vh, G, eps, pg, nthreads);
+      g_params[0] += 0.5 * dt * pg[0], g_params[1] += 0.5 * dt * pg[1];
+    }
     for (size_t k = 0; k < sz; ++k) g_x0[k] += 0.5 * dt * gx[k];
     for (int64_t k = 0; k < n; ++k) g_m[k] += 0.5 * dt * gmv[k];
     memcpy(g_v0, lam_vh, sizeof(double) * sz);
   }
   free(traj), free(v), free(a), free(gx), free(gmv), free(lam_vh);
   return 0;
+}
+
+int oracle_adjoint(int64_t n, const double* x0, const double* v0, const double* m, double G, double eps, double dt,
+                   int n_steps, const double* lam_xT, const double* lam_vT, double* g_x0, double* g_v0, double* g_m,
+                   int nthreads) {
+  return adjoint_sweep(n, x0, v0, m, G, eps, dt, n_steps, lam_xT, lam_vT, g_x0, g_v0, g_m, NULL, nthreads);
+}
+
+/* oracle_adjoint plus g_params[0] = dL/dG and g_params[1] = dL/deps. */
+int oracle_adjoint_params(int64_t n, const double* x0, const double* v0, const double* m, double G, double eps,
+                          double dt, int n_steps, const double* lam_xT, const double* lam_vT, double* g_x0,
+                          double* g_v0, double* g_m, double* g_params, int nthreads) {
+  if (!g_params) return 1;
+  g_params[0] = g_params[1] = 0.0;
+  return adjoint_sweep(n, x0, v0, m, G, eps, dt, n_steps, lam_xT, lam_vT, g_x0, g_v0, g_m, g_params, nthreads);
 }
 
 /* ------------------------------------------------------------------------ */

@@ -320,6 +320,59 @@ def test_adjoint_matches_finite_differences():
         assert abs(fd - gm[k]) <= 1e-7 * max(abs(fd), np.abs(gm).max() * 1e-2), (k, fd, gm[k])
 
 
+def test_param_vjp_matches_finite_differences():
+    # w . da/dG and w . da/deps of the force map against central differences of w . a.
+    x, _, m = inputs.plummer(16, seed=7)
+    w = np.random.default_rng(5).standard_normal((16, 3))
+    G, eps = 1.7, 0.04
+    pG, pe = oracle.param_vjp(x, m, w, G=G, eps=eps)
+    f = lambda g, e: float((w * oracle.forces(x, m, G=g, eps=e)[0]).sum())
+    h = 1e-6
+    assert abs((f(G + h, eps) - f(G - h, eps)) / (2 * h) - pG) <= 1e-7 * abs(pG)
+    assert abs((f(G, eps + h) - f(G, eps - h)) / (2 * h) - pe) <= 1e-6 * abs(pe)
+    # a is linear in G: w . a = G (w . da/dG) exactly (up to rounding)
+    assert abs(f(G, eps) - G * pG) <= 1e-12 * abs(f(G, eps))
+
+
+def _param_case():
+    x0, v0, m = inputs.plummer(8, seed=14)
+    m = m * np.exp(0.3 * np.random.default_rng(6).standard_normal(8))
+    t = inputs.targets(8, seed=15)
+    G, eps, dt, n = 1.3, 0.05, 1e-2, 20
+    xT, vT, _, _ = oracle.kdk(x0, v0, m, G, eps, dt, n)
+    grads = oracle.adjoint_params(x0, v0, m, G, eps, dt, n, 2 * (xT - t), np.zeros_like(vT))
+    return x0, v0, m, t, G, eps, dt, n, xT, grads
+
+
+def test_adjoint_params_match_finite_differences():
+    # dL/dG and dL/deps of the 20-step loss against central differences (h = 1e-4 relative:
+    # truncation ~1e-8, rounding ~1e-16 L / h).
+    x0, v0, m, t, G, eps, dt, n, xT, (gx, gv, gm, (gG, ge)) = _param_case()
+    L = lambda g, e: oracle.trajectory_loss(x0, v0, m, g, e, dt, n, t, threads=1)
+    hG, he = 1e-4 * G, 1e-4 * eps
+    fdG = (L(G + hG, eps) - L(G - hG, eps)) / (2 * hG)
+    fde = (L(G, eps + he) - L(G, eps - he)) / (2 * he)
+    assert abs(fdG - gG) <= 1e-6 * abs(fdG), (fdG, gG)
+    assert abs(fde - ge) <= 1e-5 * abs(fde), (fde, ge)
+    # the parameter sweep leaves the other gradients unchanged
+    gx0, gv0, gm0 = oracle.adjoint(x0, v0, m, G, eps, dt, n, 2 * (xT - t), np.zeros_like(xT))
+    assert np.array_equal(gx, gx0) and np.array_equal(gv, gv0) and np.array_equal(gm, gm0)
+
+
+def test_adjoint_params_scaling_identities():
+    # Two exact symmetries of softened gravity under KDK pin dL/dG and dL/deps to the
+    # (separately pinned) gradients in x0, v0, m:
+    #  * G enters only as the product G m_j, so G dL/dG = sum_j m_j dL/dm_j;
+    #  * (x, v, m, eps, targets) -> (s x, s v, s^3 m, s eps, s t) maps every KDK step to
+    #    s times itself (a scales by s), so L scales by s^2 and, at s = 1,
+    #    2 L = x0.g_x0 + v0.g_v0 + 3 m.g_m + eps dL/deps - 2 (x_T - t).t .
+    x0, v0, m, t, G, eps, dt, n, xT, (gx, gv, gm, (gG, ge)) = _param_case()
+    assert abs(G * gG - (m * gm).sum()) <= 1e-12 * abs(G * gG)
+    L = float(((xT - t) ** 2).sum())
+    rhs = 2 * L - (gx * x0).sum() - (gv * v0).sum() - 3 * (m * gm).sum() + 2 * ((xT - t) * t).sum()
+    assert abs(eps * ge - rhs) <= 1e-9 * L, (eps * ge, rhs)
+
+
 # --------------------------------------------------------------------------------------
 # Lennard-Jones gas (the paper's pair law, Eq. 1)
 
