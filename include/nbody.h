@@ -160,6 +160,23 @@ nbody_status nbody_adjoint(nbody_ctx* ctx, const double* x0, const double* v0, c
                            double* g_v0, double* g_m);
 
 /*
+ * nbody_adjoint plus the gradients with respect to the two model parameters of
+ * softened gravity, per system: g_params [n_systems][2] (device, overwritten)
+ * = {dL/dG, dL/deps}. The acceleration depends on G linearly and on eps through
+ * s^2 = |d|^2 + eps^2, so every half-kick with weight w (= coef * lam_v) adds
+ *     dL/dG   += sum_k w_k . sum_{j != k} m_j d_kj / s_kj^3
+ *     dL/deps += sum_k w_k . (-3 G eps) sum_{j != k} m_j d_kj / s_kj^5
+ * (summed per system in a fixed order). G and eps are shared by all systems of
+ * the context, so the gradient of a loss summed over systems is the sum of the
+ * rows. Costs two more float32 (or float64) operations per pair of each VJP
+ * and 32 bytes more partial memory per body and slice. Same arguments, errors
+ * and restrictions as nbody_adjoint; g_params NULL is NBODY_EINVAL.
+ */
+nbody_status nbody_adjoint_params(nbody_ctx* ctx, const double* x0, const double* v0, const double* m,
+                                  int32_t n_steps, int32_t checkpoint_every, const double* lam_xT,
+                                  const double* lam_vT, double* g_x0, double* g_v0, double* g_m, double* g_params);
+
+/*
  * Host-memory variant of nbody_step: x, v, a (in/out), m (in) and energy_log
  * (out, nullable) are HOST pointers (pinned memory gives asynchronous copies).
  * The context copies them to its own device buffers, runs nbody_step, copies

@@ -7,7 +7,7 @@ device memory and streams. There is no CPU fallback: if the library is
 missing, ``load()`` raises.
 
 Functions carry the C names: ``nbody_init``, ``nbody_forces``, ``nbody_step``,
-``nbody_energy``, ``nbody_adjoint``, ``nbody_step_host``, ``nbody_sync``,
+``nbody_energy``, ``nbody_adjoint``, ``nbody_adjoint_params``, ``nbody_step_host``, ``nbody_sync``,
 ``nbody_get_tuning``, ``nbody_launch_count``, ``nbody_last_error``,
 ``nbody_destroy``, ``nbody_version``. ``NBodyAdjoint`` wraps the forward
 ``nbody_step`` and the reverse ``nbody_adjoint`` as a torch.autograd.Function.
@@ -21,7 +21,8 @@ import threading
 
 __all__ = [
     "FP64", "MIXED", "GRAVITY", "LENNARD_JONES", "FLAG_GRAPH", "FLAG_NOCHECK", "NBodyError", "Context", "load", "lib_path",
-    "nbody_init", "nbody_forces", "nbody_step", "nbody_energy", "nbody_adjoint", "nbody_step_host",
+    "nbody_init", "nbody_forces", "nbody_step", "nbody_energy", "nbody_adjoint", "nbody_adjoint_params",
+    "nbody_step_host",
     "nbody_sync", "nbody_get_tuning", "nbody_launch_count", "nbody_last_error", "nbody_destroy",
     "nbody_version", "nbody_profile", "nbody_kernel_time", "NBodyAdjoint", "ENERGY_FIELDS",
 ]
@@ -80,6 +81,7 @@ def load():
             "nbody_step": (i32, [p, p, p, p, p, i32, i32, p]),
             "nbody_energy": (i32, [p, p, p, p, p]),
             "nbody_adjoint": (i32, [p, p, p, p, i32, i32, p, p, p, p, p]),
+            "nbody_adjoint_params": (i32, [p, p, p, p, i32, i32, p, p, p, p, p, p]),
             "nbody_step_host": (i32, [p, p, p, p, p, i32, i32, p]),
             "nbody_sync": (i32, [p]),
             "nbody_get_tuning": (i32, [p] + [ctypes.POINTER(i32)] * 6),
@@ -260,6 +262,24 @@ def nbody_adjoint(ctx: Context, x0, v0, m, n_steps: int, checkpoint_every: int, 
     _bind_stream(ctx)
     _check(load().nbody_adjoint(ctx._h, *args), ctx)
     return g_x0, g_v0, g_m
+
+
+def nbody_adjoint_params(ctx: Context, x0, v0, m, n_steps: int, checkpoint_every: int, lam_xT, lam_vT):
+    """``nbody_adjoint`` plus g_params [n_systems, 2] = (dL/dG, dL/deps) per system."""
+    torch = _torch()
+    n = ctx.n_total
+    dev = x0.device
+    g_x0 = torch.empty((n, 3), dtype=torch.float64, device=dev)
+    g_v0 = torch.empty((n, 3), dtype=torch.float64, device=dev)
+    g_m = torch.empty((n,), dtype=torch.float64, device=dev)
+    g_p = torch.empty((ctx.n_systems, 2), dtype=torch.float64, device=dev)
+    args = (_dev(x0, "x0", (n, 3), ctx), _dev(v0, "v0", (n, 3), ctx), _dev(m, "m", (n,), ctx), int(n_steps),
+            int(checkpoint_every), _dev(lam_xT, "lam_xT", (n, 3), ctx), _dev(lam_vT, "lam_vT", (n, 3), ctx),
+            _dev(g_x0, "g_x0", (n, 3), ctx), _dev(g_v0, "g_v0", (n, 3), ctx), _dev(g_m, "g_m", (n,), ctx),
+            _dev(g_p, "g_params", (ctx.n_systems, 2), ctx))
+    _bind_stream(ctx)
+    _check(load().nbody_adjoint_params(ctx._h, *args), ctx)
+    return g_x0, g_v0, g_m, g_p
 
 
 def _host(t, name, shape):

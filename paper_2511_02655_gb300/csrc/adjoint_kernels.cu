@@ -9,8 +9,14 @@
 //   Gb = sum (m_k (d.w_j) - m_j (d.w_k)) d / s^5,  Gm = sum (d.w_j) / s^3,
 // so that g_x,k = G (m_k A1 - A2 w_k - 3 Gb) and g_m,k = -G Gm (formed by the
 // O(N) update kernel). The pair costs 26 float32 operations plus one MUFU.RSQ.
+// With P (the gradients with respect to G and eps requested) two more sums,
+//   Pg = sum m_j (d.w_k) / s^3   (w_k . da_k/dG),
+//   Pe = sum m_j (d.w_k) / s^5   (w_k . da_k/deps = -3 G eps Pe),
+// cost two float32 operations more per pair and a third double4 per body and slice.
 // Tiling, work distribution, self-pair masking and the compensated per-tile
 // fold are those of the force kernels.
+#include <algorithm>
+
 #include "nbody_internal.h"
 #include "pair_common.cuh"
 
@@ -18,10 +24,10 @@ namespace nbody {
 namespace {
 
 struct Acc8f {
-  float a1x, a1y, a1z, a2, gbx, gby, gbz, gm;
+  float a1x, a1y, a1z, a2, gbx, gby, gbz, gm, pg, pe;
 };
 
-template <bool MASK>
+template <bool MASK, bool P>
 __device__ __forceinline__ void vjp_pair_f32(const float4 q, const float4 wj, const float xk, const float yk,
                                              const float zk, const float mk, const float wkx, const float wky,
                                              const float wkz, const float eps2, Acc8f& s, const bool self) {
@@ -36,8 +42,14 @@ __device__ __forceinline__ void vjp_pair_f32(const float4 q, const float4 wj, co
   const float dwj = fmaf(dx, wj.x, fmaf(dy, wj.y, dz * wj.z));
   const float dwk = fmaf(dx, wkx, fmaf(dy, wky, dz * wkz));
   s.gm = fmaf(dwj, inv3, s.gm);
-  const float du = fmaf(mk, dwj, -(q.w * dwk));
-  const float t = du * (inv3 * inv2);
+  const float pk = q.w * dwk;
+  const float du = fmaf(mk, dwj, -pk);
+  const float inv5 = inv3 * inv2;
+  const float t = du * inv5;
+  if (P) {
+    s.pg = fmaf(pk, inv3, s.pg);
+    s.pe = fmaf(pk, inv5, s.pe);
+  }
   s.gbx = fmaf(t, dx, s.gbx);
   s.gby = fmaf(t, dy, s.gby);
   s.gbz = fmaf(t, dz, s.gbz);
@@ -48,10 +60,10 @@ __device__ __forceinline__ void vjp_pair_f32(const float4 q, const float4 wj, co
 }
 
 struct Acc8d {
-  double a1x, a1y, a1z, a2, gbx, gby, gbz, gm;
+  double a1x, a1y, a1z, a2, gbx, gby, gbz, gm, pg, pe;
 };
 
-template <bool MASK>
+template <bool MASK, bool P>
 __device__ __forceinline__ void vjp_pair_f64(const double4_32a q, const double4_32a wj, const double xk, const double yk,
                                              const double zk, const double mk, const double wkx, const double wky,
                                              const double wkz, const double eps2, Acc8d& s, const bool self) {
@@ -66,8 +78,14 @@ __device__ __forceinline__ void vjp_pair_f64(const double4_32a q, const double4_
   const double dwj = fma(dx, wj.x, fma(dy, wj.y, dz * wj.z));
   const double dwk = fma(dx, wkx, fma(dy, wky, dz * wkz));
   s.gm = fma(dwj, inv3, s.gm);
-  const double du = fma(mk, dwj, -(q.w * dwk));
-  const double t = du * (inv3 * inv2);
+  const double pk = q.w * dwk;
+  const double du = fma(mk, dwj, -pk);
+  const double inv5 = inv3 * inv2;
+  const double t = du * inv5;
+  if (P) {
+    s.pg = fma(pk, inv3, s.pg);
+    s.pe = fma(pk, inv5, s.pe);
+  }
   s.gbx = fma(t, dx, s.gbx);
   s.gby = fma(t, dy, s.gby);
   s.gbz = fma(t, dz, s.gbz);
@@ -77,7 +95,7 @@ __device__ __forceinline__ void vjp_pair_f64(const double4_32a q, const double4_
   s.a2 = fma(q.w, inv3, s.a2);
 }
 
-template <int BLOCK, int R, int J>
+template <int BLOCK, int R, int J, bool P>
 __global__ void __launch_bounds__(BLOCK) k_vjp_mixed(const PairLaunch L) {
   constexpr int LPT = (J + BLOCK - 1) / BLOCK;
   __shared__ __align__(16) float4 tx[J];
@@ -104,7 +122,7 @@ __global__ void __launch_bounds__(BLOCK) k_vjp_mixed(const PairLaunch L) {
       const float4 u = ok ? sw[ig[r]] : make_float4(0.f, 0.f, 0.f, 0.f);
       xk[r] = q.x, yk[r] = q.y, zk[r] = q.z, mk[r] = q.w;
       wkx[r] = u.x, wky[r] = u.y, wkz[r] = u.z;
-      hi[r] = Acc8f{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      hi[r] = Acc8f{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
       lo[r] = hi[r];
     }
 
@@ -133,14 +151,14 @@ __global__ void __launch_bounds__(BLOCK) k_vjp_mixed(const PairLaunch L) {
       }
       Acc8f s[R];
 #pragma unroll
-      for (int r = 0; r < R; ++r) s[r] = Acc8f{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      for (int r = 0; r < R; ++r) s[r] = Acc8f{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
       const bool diag = (jt < w.i_end) && (w.i_begin < jt + nj);
       if (diag) {
         for (int j = 0; j < nj; ++j) {
           const float4 q = tx[j], u = tw[j];
 #pragma unroll
           for (int r = 0; r < R; ++r)
-            vjp_pair_f32<true>(q, u, xk[r], yk[r], zk[r], mk[r], wkx[r], wky[r], wkz[r], eps2, s[r],
+            vjp_pair_f32<true, P>(q, u, xk[r], yk[r], zk[r], mk[r], wkx[r], wky[r], wkz[r], eps2, s[r],
                                jt + j == ig[r]);
         }
       } else {
@@ -149,7 +167,7 @@ __global__ void __launch_bounds__(BLOCK) k_vjp_mixed(const PairLaunch L) {
           const float4 q = tx[j], u = tw[j];
 #pragma unroll
           for (int r = 0; r < R; ++r)
-            vjp_pair_f32<false>(q, u, xk[r], yk[r], zk[r], mk[r], wkx[r], wky[r], wkz[r], eps2, s[r], false);
+            vjp_pair_f32<false, P>(q, u, xk[r], yk[r], zk[r], mk[r], wkx[r], wky[r], wkz[r], eps2, s[r], false);
         }
       }
 #pragma unroll
@@ -162,26 +180,34 @@ __global__ void __launch_bounds__(BLOCK) k_vjp_mixed(const PairLaunch L) {
         two_sum_acc(hi[r].gby, lo[r].gby, s[r].gby);
         two_sum_acc(hi[r].gbz, lo[r].gbz, s[r].gbz);
         two_sum_acc(hi[r].gm, lo[r].gm, s[r].gm);
+        if (P) {
+          two_sum_acc(hi[r].pg, lo[r].pg, s[r].pg);
+          two_sum_acc(hi[r].pe, lo[r].pe, s[r].pe);
+        }
       }
     }
 
-    double4_32a* out = part + 2 * ((int64_t)w.slice * L.n_total);
+    constexpr int kW = P ? 3 : 2;  // double4 per body and slice
+    double4_32a* out = part + kW * ((int64_t)w.slice * L.n_total);
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       if (ig[r] < w.i_end) {
-        out[2 * (int64_t)ig[r]] =
+        out[kW * (int64_t)ig[r]] =
             make_double4_32a((double)hi[r].a1x + lo[r].a1x, (double)hi[r].a1y + lo[r].a1y,
                          (double)hi[r].a1z + lo[r].a1z, (double)hi[r].a2 + lo[r].a2);
-        out[2 * (int64_t)ig[r] + 1] =
+        out[kW * (int64_t)ig[r] + 1] =
             make_double4_32a((double)hi[r].gbx + lo[r].gbx, (double)hi[r].gby + lo[r].gby,
                          (double)hi[r].gbz + lo[r].gbz, (double)hi[r].gm + lo[r].gm);
+        if (P)
+          out[kW * (int64_t)ig[r] + 2] =
+              make_double4_32a((double)hi[r].pg + lo[r].pg, (double)hi[r].pe + lo[r].pe, 0.0, 0.0);
       }
     }
   }
   retire_cta(L.counter);
 }
 
-template <int BLOCK, int R, int J>
+template <int BLOCK, int R, int J, bool P>
 __global__ void __launch_bounds__(BLOCK) k_vjp_fp64(const PairLaunch L) {
   constexpr int LPT = (J + BLOCK - 1) / BLOCK;
   __shared__ __align__(32) double4_32a tx[J];
@@ -208,7 +234,7 @@ __global__ void __launch_bounds__(BLOCK) k_vjp_fp64(const PairLaunch L) {
       const double4_32a u = ok ? sw[ig[r]] : make_double4_32a(0.0, 0.0, 0.0, 0.0);
       xk[r] = q.x, yk[r] = q.y, zk[r] = q.z, mk[r] = q.w;
       wkx[r] = u.x, wky[r] = u.y, wkz[r] = u.z;
-      s[r] = Acc8d{0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+      s[r] = Acc8d{0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     }
 
     double4_32a px[LPT], pw[LPT];
@@ -240,7 +266,7 @@ __global__ void __launch_bounds__(BLOCK) k_vjp_fp64(const PairLaunch L) {
           const double4_32a q = tx[j], u = tw[j];
 #pragma unroll
           for (int r = 0; r < R; ++r)
-            vjp_pair_f64<true>(q, u, xk[r], yk[r], zk[r], mk[r], wkx[r], wky[r], wkz[r], eps2, s[r],
+            vjp_pair_f64<true, P>(q, u, xk[r], yk[r], zk[r], mk[r], wkx[r], wky[r], wkz[r], eps2, s[r],
                                jt + j == ig[r]);
         }
       } else {
@@ -249,17 +275,19 @@ __global__ void __launch_bounds__(BLOCK) k_vjp_fp64(const PairLaunch L) {
           const double4_32a q = tx[j], u = tw[j];
 #pragma unroll
           for (int r = 0; r < R; ++r)
-            vjp_pair_f64<false>(q, u, xk[r], yk[r], zk[r], mk[r], wkx[r], wky[r], wkz[r], eps2, s[r], false);
+            vjp_pair_f64<false, P>(q, u, xk[r], yk[r], zk[r], mk[r], wkx[r], wky[r], wkz[r], eps2, s[r], false);
         }
       }
     }
 
-    double4_32a* out = part + 2 * ((int64_t)w.slice * L.n_total);
+    constexpr int kW = P ? 3 : 2;  // double4 per body and slice
+    double4_32a* out = part + kW * ((int64_t)w.slice * L.n_total);
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       if (ig[r] < w.i_end) {
-        out[2 * (int64_t)ig[r]] = make_double4_32a(s[r].a1x, s[r].a1y, s[r].a1z, s[r].a2);
-        out[2 * (int64_t)ig[r] + 1] = make_double4_32a(s[r].gbx, s[r].gby, s[r].gbz, s[r].gm);
+        out[kW * (int64_t)ig[r]] = make_double4_32a(s[r].a1x, s[r].a1y, s[r].a1z, s[r].a2);
+        out[kW * (int64_t)ig[r] + 1] = make_double4_32a(s[r].gbx, s[r].gby, s[r].gbz, s[r].gm);
+        if (P) out[kW * (int64_t)ig[r] + 2] = make_double4_32a(s[r].pg, s[r].pe, 0.0, 0.0);
       }
     }
   }
@@ -280,13 +308,17 @@ int occupancy_of(K kern, int block) {
 
 cudaError_t launch_vjp(int precision, const PairLaunch& L, cudaStream_t st) {
   if (L.n_ctas <= 0) return cudaErrorInvalidConfiguration;
-#define NBODY_X(B, R, J)                                   \
-  if (L.block == B && L.ipt == R && L.jtile == J) {        \
-    if (precision == 1)                                    \
-      k_vjp_mixed<B, R, J><<<L.n_ctas, B, 0, st>>>(L);     \
-    else                                                   \
-      k_vjp_fp64<B, R, J><<<L.n_ctas, B, 0, st>>>(L);      \
-    return cudaGetLastError();                             \
+#define NBODY_X(B, R, J)                                                 \
+  if (L.block == B && L.ipt == R && L.jtile == J) {                      \
+    if (precision == 1 && L.params)                                      \
+      k_vjp_mixed<B, R, J, true><<<L.n_ctas, B, 0, st>>>(L);             \
+    else if (precision == 1)                                             \
+      k_vjp_mixed<B, R, J, false><<<L.n_ctas, B, 0, st>>>(L);            \
+    else if (L.params)                                                   \
+      k_vjp_fp64<B, R, J, true><<<L.n_ctas, B, 0, st>>>(L);              \
+    else                                                                 \
+      k_vjp_fp64<B, R, J, false><<<L.n_ctas, B, 0, st>>>(L);             \
+    return cudaGetLastError();                                           \
   }
   NBODY_VJP_TILINGS(NBODY_X)
 #undef NBODY_X
@@ -294,9 +326,11 @@ cudaError_t launch_vjp(int precision, const PairLaunch& L, cudaStream_t st) {
 }
 
 int vjp_ctas_per_sm(int precision, int block, int ipt, int jtile) {
-#define NBODY_X(B, R, J)                                  \
-  if (block == B && ipt == R && jtile == J)               \
-    return precision == 1 ? occupancy_of(k_vjp_mixed<B, R, J>, B) : occupancy_of(k_vjp_fp64<B, R, J>, B);
+#define NBODY_X(B, R, J)                                                                              \
+  if (block == B && ipt == R && jtile == J)                                                           \
+    return precision == 1                                                                             \
+               ? std::min(occupancy_of(k_vjp_mixed<B, R, J, false>, B), occupancy_of(k_vjp_mixed<B, R, J, true>, B)) \
+               : std::min(occupancy_of(k_vjp_fp64<B, R, J, false>, B), occupancy_of(k_vjp_fp64<B, R, J, true>, B));
   NBODY_VJP_TILINGS(NBODY_X)
 #undef NBODY_X
   return 0;

@@ -104,6 +104,7 @@ struct nbody_ctx {
   int n_vitems = 0;
   int vmax_slices = 1;
   bool vjp_ready = false;
+  bool vjp_params = false;  // VJP launches also form the G and eps gradient sums
 
   // scratch
   DevBuf stage, stage_lo, stage_w, part, centre, epart, status_counter, a_scratch;
@@ -395,6 +396,7 @@ PairLaunch pair_launch(nbody_ctx* c, bool vjp, bool refine = false) {
   const Tiling& t = vjp ? c->vt : c->ft;
   L.block = t.block, L.ipt = t.ipt, L.jtile = t.jtile, L.n_ctas = t.n_ctas;
   L.variant = vjp ? 0 : t.variant;
+  L.params = vjp && c->vjp_params ? 1 : 0;
   return L;
 }
 
@@ -788,6 +790,147 @@ nbody_status check_state_args(nbody_ctx* c, const double* x, const double* v, co
   return NBODY_OK;
 }
 
+// RAII switch of the VJP launches to the parameter-gradient variant.
+struct ParamsScope {
+  nbody_ctx* c;
+  ParamsScope(nbody_ctx* ctx, bool on) : c(ctx) { c->vjp_params = on; }
+  ~ParamsScope() { c->vjp_params = false; }
+};
+
+nbody_status adjoint_sweep(nbody_ctx* c, const double* x0, const double* v0, const double* m, int32_t T, int32_t K,
+                           const double* lam_xT, const double* lam_vT, double* g_x0, double* g_v0, double* g_m,
+                           double* g_params) {
+  if (!c) return fail(nullptr, NBODY_EINVAL, "ctx is NULL");
+  if (T < 0 || K < 1) return fail(c, NBODY_EINVAL, "need n_steps >= 0 and checkpoint_every >= 1");
+  if (c->cfg.law != NBODY_LAW_GRAVITY || c->cfg.box > 0)
+    return fail(c, NBODY_EUNSUPPORTED, "nbody_adjoint supports softened gravity without walls only");
+  if (T > 0 && !(c->cfg.dt > 0)) return fail(c, NBODY_EINVAL, "dt must be > 0");
+  if (c->n_total == 0) return NBODY_OK;
+  const size_t n = (size_t)c->n_total, n3b = n * 3 * sizeof(double);
+  nbody_status s;
+  if ((s = check_state_args(c, x0, v0, m, nullptr, true, false))) return s;
+  if ((s = check_dev(c, lam_xT, n3b, "lam_xT"))) return s;
+  if ((s = check_dev(c, lam_vT, n3b, "lam_vT"))) return s;
+  if ((s = check_dev(c, g_x0, n3b, "g_x0"))) return s;
+  if ((s = check_dev(c, g_v0, n3b, "g_v0"))) return s;
+  if ((s = check_dev(c, g_m, n * sizeof(double), "g_m"))) return s;
+  if (g_params && (s = check_dev(c, g_params, (size_t)c->n_sys * 2 * sizeof(double), "g_params"))) return s;
+  cudaStream_t st = c->stream;
+
+  const size_t stage_bytes = n * (c->cfg.precision == NBODY_MIXED ? sizeof(float4) : sizeof(double4_32a));
+  if ((s = ensure(c, c->stage_w, stage_bytes))) return s;
+  if (!c->vjp_ready) {
+    // VJP tiling: tuned once per context (synchronises the stream)
+    NB_CUDA(c, cudaStreamSynchronize(st));
+    if ((s = autotune(c, true))) return s;
+  }
+  const int vjp_bytes = g_params ? 96 : 64;  // per body and slice: 2 or 3 double4
+  if ((s = ensure(c, c->part, (size_t)std::max(c->max_slices * 32, c->vmax_slices * vjp_bytes) * n))) return s;
+
+  NB_CUDA(c, cudaMemcpyAsync(g_x0, lam_xT, n3b, cudaMemcpyDeviceToDevice, st));
+  NB_CUDA(c, cudaMemcpyAsync(g_v0, lam_vT, n3b, cudaMemcpyDeviceToDevice, st));
+  NB_CUDA(c, cudaMemsetAsync(g_m, 0, n * sizeof(double), st));
+  if (g_params) NB_CUDA(c, cudaMemsetAsync(g_params, 0, (size_t)c->n_sys * 2 * sizeof(double), st));
+  if (T == 0) return NBODY_OK;
+  ParamsScope scope(c, g_params != nullptr);
+
+  const int nseg = (T + K - 1) / K;
+  if ((s = ensure(c, c->xw, n3b)) || (s = ensure(c, c->vw, n3b)) || (s = ensure(c, c->aw, n3b))) return s;
+  if ((s = ensure(c, c->ckpt, (size_t)nseg * 3 * n3b))) return s;
+  if ((s = ensure(c, c->traj, (size_t)(K + 1) * n3b))) return s;
+  double* xw = static_cast<double*>(c->xw.p);
+  double* vw = static_cast<double*>(c->vw.p);
+  double* aw = static_cast<double*>(c->aw.p);
+  double* ck = static_cast<double*>(c->ckpt.p);
+  double* X = static_cast<double*>(c->traj.p);
+  const size_t n3 = n * 3;
+
+  // staging origin for the whole call, from x0 (the same as nbody_step uses)
+  if ((s = run_centre(c, x0, m, st))) return s;
+  NB_CUDA(c, cudaMemcpyAsync(xw, x0, n3b, cudaMemcpyDeviceToDevice, st));
+  NB_CUDA(c, cudaMemcpyAsync(vw, v0, n3b, cudaMemcpyDeviceToDevice, st));
+  if ((s = run_post(c, post_launch(c, kStage, xw, vw, m, aw, nullptr), st))) return s;
+  if ((s = run_force(c, st))) return s;
+  if ((s = run_post(c, post_launch(c, kCombine, xw, vw, m, aw, nullptr), st))) return s;
+
+  // one KDK step on (xw, vw, aw), optionally copying x after the drift
+  auto step = [&](double* xcopy) -> nbody_status {
+    nbody_status r;
+    PostLaunch P = post_launch(c, kDrift | kStage, xw, vw, m, aw, nullptr);
+    P.x_copy = xcopy;
+    if ((r = run_post(c, P, st))) return r;
+    if ((r = run_force(c, st))) return r;
+    return run_post(c, post_launch(c, kCombine | kKickEnd, xw, vw, m, aw, nullptr), st);
+  };
+
+  // forward pass: checkpoints (x, v, a) at the start of every segment
+  for (int t = 0; t < T; ++t) {
+    if (t % K == 0) {
+      double* cp = ck + (size_t)(t / K) * 3 * n3;
+      NB_CUDA(c, cudaMemcpyAsync(cp, xw, n3b, cudaMemcpyDeviceToDevice, st));
+      NB_CUDA(c, cudaMemcpyAsync(cp + n3, vw, n3b, cudaMemcpyDeviceToDevice, st));
+      NB_CUDA(c, cudaMemcpyAsync(cp + 2 * n3, aw, n3b, cudaMemcpyDeviceToDevice, st));
+    }
+    if ((s = step(nullptr))) return s;
+  }
+
+  // reverse sweep. VJPs at x_T (coef dt/2), x_s for 0 < s < T (coef dt: the
+  // closing half-kick of step s-1 and the opening half-kick of step s share
+  // x_s and the same weights), x_0 (coef dt/2).
+  AdjLaunch A{};
+  A.chunks = c->d_vchunks;
+  A.n_chunks = (int32_t)c->chunks.size();
+  A.part = static_cast<const double*>(c->part.p);
+  A.n_total = c->n_total;
+  A.G = c->cfg.G;
+  A.dt = c->cfg.dt;
+  A.m = m;
+  A.lam_x = g_x0;
+  A.lam_v = g_v0;
+  A.g_m = g_m;
+  A.precision = c->cfg.precision;
+  A.stage_x = c->stage.p;
+  A.stage_w = c->stage_w.p;
+  A.centre = static_cast<const double*>(c->centre.p);
+  A.status = c->status;
+  A.g_params = g_params;
+  A.eps = c->cfg.eps;
+  A.cpart = static_cast<double*>(c->epart.p);
+  A.sys_chunk = c->d_sys_chunk;
+  A.n_sys = c->n_sys;
+  A.done = c->counter + 6;
+  const Chunk* vch = c->d_vchunks;
+  const int nch = (int)c->chunks.size();
+  for (int k = nseg - 1; k >= 0; --k) {
+    const int s0 = k * K, s1 = std::min(T, s0 + K), len = s1 - s0;
+    double* cp = ck + (size_t)k * 3 * n3;
+    NB_CUDA(c, cudaMemcpyAsync(xw, cp, n3b, cudaMemcpyDeviceToDevice, st));
+    NB_CUDA(c, cudaMemcpyAsync(vw, cp + n3, n3b, cudaMemcpyDeviceToDevice, st));
+    NB_CUDA(c, cudaMemcpyAsync(aw, cp + 2 * n3, n3b, cudaMemcpyDeviceToDevice, st));
+    NB_CUDA(c, cudaMemcpyAsync(X, xw, n3b, cudaMemcpyDeviceToDevice, st));
+    for (int t = 0; t < len; ++t)
+      if ((s = step(X + (size_t)(t + 1) * n3))) return s;
+    const int top = (k == nseg - 1) ? s1 : s1 - 1;
+    NB_CUDA(c, launch_stage_vec(vch, nch, c->cfg.precision, X + (size_t)(top - s0) * n3, m,
+                                static_cast<const double*>(c->centre.p), c->stage.p, 1, st));
+    ++c->launches;
+    if (k == nseg - 1) {
+      NB_CUDA(c, launch_stage_vec(vch, nch, c->cfg.precision, g_v0, m, static_cast<const double*>(c->centre.p),
+                                  c->stage_w.p, 0, st));
+      ++c->launches;
+    }
+    for (int t = top; t >= s0; --t) {
+      if ((s = run_vjp(c, st))) return s;
+      A.coef = (t == T || t == 0) ? 0.5 * c->cfg.dt : c->cfg.dt;
+      A.drift_rev = t > 0;
+      A.x_next = (t - 1 >= s0) ? X + (size_t)(t - 1 - s0) * n3 : nullptr;
+      NB_CUDA(c, launch_adj_update(A, st));
+      ++c->launches;
+    }
+  }
+  return NBODY_OK;
+}
+
 }  // namespace
 
 // ===========================================================================
@@ -993,126 +1136,18 @@ nbody_status nbody_energy(nbody_ctx* c, const double* x, const double* v, const 
 nbody_status nbody_adjoint(nbody_ctx* c, const double* x0, const double* v0, const double* m, int32_t T,
                            int32_t K, const double* lam_xT, const double* lam_vT, double* g_x0, double* g_v0,
                            double* g_m) {
-  if (!c) return fail(nullptr, NBODY_EINVAL, "ctx is NULL");
-  if (T < 0 || K < 1) return fail(c, NBODY_EINVAL, "need n_steps >= 0 and checkpoint_every >= 1");
-  if (c->cfg.law != NBODY_LAW_GRAVITY || c->cfg.box > 0)
-    return fail(c, NBODY_EUNSUPPORTED, "nbody_adjoint supports softened gravity without walls only");
-  if (T > 0 && !(c->cfg.dt > 0)) return fail(c, NBODY_EINVAL, "dt must be > 0");
-  if (c->n_total == 0) return NBODY_OK;
-  const size_t n = (size_t)c->n_total, n3b = n * 3 * sizeof(double);
-  nbody_status s;
-  if ((s = check_state_args(c, x0, v0, m, nullptr, true, false))) return s;
-  if ((s = check_dev(c, lam_xT, n3b, "lam_xT"))) return s;
-  if ((s = check_dev(c, lam_vT, n3b, "lam_vT"))) return s;
-  if ((s = check_dev(c, g_x0, n3b, "g_x0"))) return s;
-  if ((s = check_dev(c, g_v0, n3b, "g_v0"))) return s;
-  if ((s = check_dev(c, g_m, n * sizeof(double), "g_m"))) return s;
-  cudaStream_t st = c->stream;
-
-  const size_t stage_bytes = n * (c->cfg.precision == NBODY_MIXED ? sizeof(float4) : sizeof(double4_32a));
-  if ((s = ensure(c, c->stage_w, stage_bytes))) return s;
-  if (!c->vjp_ready) {
-    // VJP tiling: tuned once per context (synchronises the stream)
-    NB_CUDA(c, cudaStreamSynchronize(st));
-    if ((s = autotune(c, true))) return s;
-  }
-  if ((s = ensure(c, c->part, (size_t)std::max(c->max_slices * 32, c->vmax_slices * 64) * n))) return s;
-
-  NB_CUDA(c, cudaMemcpyAsync(g_x0, lam_xT, n3b, cudaMemcpyDeviceToDevice, st));
-  NB_CUDA(c, cudaMemcpyAsync(g_v0, lam_vT, n3b, cudaMemcpyDeviceToDevice, st));
-  NB_CUDA(c, cudaMemsetAsync(g_m, 0, n * sizeof(double), st));
-  if (T == 0) return NBODY_OK;
-
-  const int nseg = (T + K - 1) / K;
-  if ((s = ensure(c, c->xw, n3b)) || (s = ensure(c, c->vw, n3b)) || (s = ensure(c, c->aw, n3b))) return s;
-  if ((s = ensure(c, c->ckpt, (size_t)nseg * 3 * n3b))) return s;
-  if ((s = ensure(c, c->traj, (size_t)(K + 1) * n3b))) return s;
-  double* xw = static_cast<double*>(c->xw.p);
-  double* vw = static_cast<double*>(c->vw.p);
-  double* aw = static_cast<double*>(c->aw.p);
-  double* ck = static_cast<double*>(c->ckpt.p);
-  double* X = static_cast<double*>(c->traj.p);
-  const size_t n3 = n * 3;
-
-  // staging origin for the whole call, from x0 (the same as nbody_step uses)
-  if ((s = run_centre(c, x0, m, st))) return s;
-  NB_CUDA(c, cudaMemcpyAsync(xw, x0, n3b, cudaMemcpyDeviceToDevice, st));
-  NB_CUDA(c, cudaMemcpyAsync(vw, v0, n3b, cudaMemcpyDeviceToDevice, st));
-  if ((s = run_post(c, post_launch(c, kStage, xw, vw, m, aw, nullptr), st))) return s;
-  if ((s = run_force(c, st))) return s;
-  if ((s = run_post(c, post_launch(c, kCombine, xw, vw, m, aw, nullptr), st))) return s;
-
-  // one KDK step on (xw, vw, aw), optionally copying x after the drift
-  auto step = [&](double* xcopy) -> nbody_status {
-    nbody_status r;
-    PostLaunch P = post_launch(c, kDrift | kStage, xw, vw, m, aw, nullptr);
-    P.x_copy = xcopy;
-    if ((r = run_post(c, P, st))) return r;
-    if ((r = run_force(c, st))) return r;
-    return run_post(c, post_launch(c, kCombine | kKickEnd, xw, vw, m, aw, nullptr), st);
-  };
-
-  // forward pass: checkpoints (x, v, a) at the start of every segment
-  for (int t = 0; t < T; ++t) {
-    if (t % K == 0) {
-      double* cp = ck + (size_t)(t / K) * 3 * n3;
-      NB_CUDA(c, cudaMemcpyAsync(cp, xw, n3b, cudaMemcpyDeviceToDevice, st));
-      NB_CUDA(c, cudaMemcpyAsync(cp + n3, vw, n3b, cudaMemcpyDeviceToDevice, st));
-      NB_CUDA(c, cudaMemcpyAsync(cp + 2 * n3, aw, n3b, cudaMemcpyDeviceToDevice, st));
-    }
-    if ((s = step(nullptr))) return s;
-  }
-
-  // reverse sweep. VJPs at x_T (coef dt/2), x_s for 0 < s < T (coef dt: the
-  // closing half-kick of step s-1 and the opening half-kick of step s share
-  // x_s and the same weights), x_0 (coef dt/2).
-  AdjLaunch A{};
-  A.chunks = c->d_vchunks;
-  A.n_chunks = (int32_t)c->chunks.size();
-  A.part = static_cast<const double*>(c->part.p);
-  A.n_total = c->n_total;
-  A.G = c->cfg.G;
-  A.dt = c->cfg.dt;
-  A.m = m;
-  A.lam_x = g_x0;
-  A.lam_v = g_v0;
-  A.g_m = g_m;
-  A.precision = c->cfg.precision;
-  A.stage_x = c->stage.p;
-  A.stage_w = c->stage_w.p;
-  A.centre = static_cast<const double*>(c->centre.p);
-  A.status = c->status;
-  const Chunk* vch = c->d_vchunks;
-  const int nch = (int)c->chunks.size();
-  for (int k = nseg - 1; k >= 0; --k) {
-    const int s0 = k * K, s1 = std::min(T, s0 + K), len = s1 - s0;
-    double* cp = ck + (size_t)k * 3 * n3;
-    NB_CUDA(c, cudaMemcpyAsync(xw, cp, n3b, cudaMemcpyDeviceToDevice, st));
-    NB_CUDA(c, cudaMemcpyAsync(vw, cp + n3, n3b, cudaMemcpyDeviceToDevice, st));
-    NB_CUDA(c, cudaMemcpyAsync(aw, cp + 2 * n3, n3b, cudaMemcpyDeviceToDevice, st));
-    NB_CUDA(c, cudaMemcpyAsync(X, xw, n3b, cudaMemcpyDeviceToDevice, st));
-    for (int t = 0; t < len; ++t)
-      if ((s = step(X + (size_t)(t + 1) * n3))) return s;
-    const int top = (k == nseg - 1) ? s1 : s1 - 1;
-    NB_CUDA(c, launch_stage_vec(vch, nch, c->cfg.precision, X + (size_t)(top - s0) * n3, m,
-                                static_cast<const double*>(c->centre.p), c->stage.p, 1, st));
-    ++c->launches;
-    if (k == nseg - 1) {
-      NB_CUDA(c, launch_stage_vec(vch, nch, c->cfg.precision, g_v0, m, static_cast<const double*>(c->centre.p),
-                                  c->stage_w.p, 0, st));
-      ++c->launches;
-    }
-    for (int t = top; t >= s0; --t) {
-      if ((s = run_vjp(c, st))) return s;
-      A.coef = (t == T || t == 0) ? 0.5 * c->cfg.dt : c->cfg.dt;
-      A.drift_rev = t > 0;
-      A.x_next = (t - 1 >= s0) ? X + (size_t)(t - 1 - s0) * n3 : nullptr;
-      NB_CUDA(c, launch_adj_update(A, st));
-      ++c->launches;
-    }
-  }
-  return NBODY_OK;
+  return adjoint_sweep(c, x0, v0, m, T, K, lam_xT, lam_vT, g_x0, g_v0, g_m, nullptr);
 }
+
+nbody_status nbody_adjoint_params(nbody_ctx* c, const double* x0, const double* v0, const double* m, int32_t T,
+                                  int32_t K, const double* lam_xT, const double* lam_vT, double* g_x0,
+                                  double* g_v0, double* g_m, double* g_params) {
+  if (!c) return fail(nullptr, NBODY_EINVAL, "ctx is NULL");
+  if (!g_params) return fail(c, NBODY_EINVAL, "g_params must be a device pointer to n_systems x 2 doubles");
+  return adjoint_sweep(c, x0, v0, m, T, K, lam_xT, lam_vT, g_x0, g_v0, g_m, g_params);
+}
+
+
 
 nbody_status nbody_step_host(nbody_ctx* c, double* x, double* v, const double* m, double* a, int32_t a_valid,
                              int32_t n_steps, double* energy_log) {

@@ -43,7 +43,7 @@ struct PairLaunch {
   const WorkItem* items;
   int32_t n_items;
   unsigned* counter;     // [2]: next item, CTAs done (zero between launches)
-  double* part;          // force: double4_32a [slices][N]; VJP: 2 x double4_32a [slices][N]
+  double* part;          // force: double4_32a [slices][N]; VJP: (2 or 3 with params) x double4_32a [slices][N]
   int64_t n_total;
   double eps2;
   const float4* stage_lo;  // force (mixed): float32 remainders (x - c) - hi [N], near-pair refinement
@@ -53,6 +53,7 @@ struct PairLaunch {
   double sigma2;         // Lennard-Jones sigma^2
   int block, ipt, jtile; // tiling
   int n_ctas;            // persistent grid size
+  int params;            // VJP: also the sums for the G and eps gradients (third double4)
 };
 
 // Returns cudaErrorInvalidConfiguration for an unsupported tiling.
@@ -112,7 +113,7 @@ cudaError_t launch_centre(const Chunk* chunks, int n_chunks, const int32_t* sys_
 struct AdjLaunch {
   const Chunk* chunks;
   int32_t n_chunks;
-  const double* part;      // 2 x double4_32a [slices][N]
+  const double* part;      // 2 (3 with g_params) x double4_32a [slices][N]
   int64_t n_total;
   double G, coef, dt;      // lam_x += coef * gx ; g_m += coef * gm ; lam_v += dt lam_x
   const double* m;
@@ -126,6 +127,12 @@ struct AdjLaunch {
   void* stage_w;
   const double* centre;
   unsigned* status;
+  double* g_params;        // nullable [n_sys][2]: += coef (w.da/dG, w.da/deps), formed by the last CTA
+  double eps;
+  double* cpart;           // [n_chunks][kEnergyVals] chunk partials (g_params only)
+  const int32_t* sys_chunk;
+  int n_sys;
+  unsigned* done;          // last-CTA ticket (zero between launches)
 };
 cudaError_t launch_adj_update(const AdjLaunch& A, cudaStream_t st);
 

@@ -232,15 +232,21 @@ __global__ void __launch_bounds__(kPostThreads) k_adj_update(const AdjLaunch A) 
   const Chunk c = A.chunks[blockIdx.x];
   const double4_32a* part = reinterpret_cast<const double4_32a*>(A.part);
   const double* cen = A.centre + 3 * c.sys;
+  const int kw = A.g_params ? 3 : 2;  // double4 per body and slice
+  double pv[2] = {0.0, 0.0};          // this thread's w.da/dG and sum m (d.w) / s^5
   bool bad = false;
   for (int i = c.begin + (int)threadIdx.x; i < c.end; i += kPostThreads) {
     double a1x = 0, a1y = 0, a1z = 0, a2 = 0, gbx = 0, gby = 0, gbz = 0, gm = 0;
 #pragma unroll 4
     for (int s = 0; s < c.n_slices; ++s) {
-      const int64_t k = 2 * ((int64_t)s * A.n_total + i);
+      const int64_t k = kw * ((int64_t)s * A.n_total + i);
       const double4_32a p = part[k], q = part[k + 1];
       a1x += p.x, a1y += p.y, a1z += p.z, a2 += p.w;
       gbx += q.x, gby += q.y, gbz += q.z, gm += q.w;
+      if (A.g_params) {
+        const double4_32a r = part[k + 2];
+        pv[0] += r.x, pv[1] += r.y;
+      }
     }
     const double mi = A.m[i];
     double w0 = A.lam_v[3 * i + 0], w1 = A.lam_v[3 * i + 1], w2 = A.lam_v[3 * i + 2];
@@ -267,6 +273,20 @@ __global__ void __launch_bounds__(kPostThreads) k_adj_update(const AdjLaunch A) 
                   cen);
   }
   if (bad) atomicOr(A.status, kFlagNonFinite);
+  if (!A.g_params) return;
+  // dL/dG += coef sum_k w_k . da_k/dG; dL/deps += coef (-3 G eps) sum_k sum_j m_j (d.w_k) / s^5,
+  // per system in a fixed order (chunk partials, then the last CTA)
+  block_sum<2, kPostThreads>(pv);
+  if (threadIdx.x == 0) A.cpart[(int64_t)blockIdx.x * kEnergyVals + 0] = pv[0],
+                        A.cpart[(int64_t)blockIdx.x * kEnergyVals + 1] = pv[1];
+  if (!last_cta(A.done)) return;
+  __threadfence();
+  systems_final<2>(A.sys_chunk, A.n_sys, A.cpart, [&](int sy, const double (&v)[2]) {
+    const double dG = A.coef * v[0], de = A.coef * (-3.0 * A.G * A.eps) * v[1];
+    if (!(isfinite(dG) && isfinite(de))) atomicOr(A.status, kFlagNonFinite);
+    A.g_params[2 * sy + 0] += dG;
+    A.g_params[2 * sy + 1] += de;
+  });
 }
 
 __global__ void __launch_bounds__(kPostThreads) k_stage_vec(const Chunk* chunks, int precision, const double* vec,

@@ -84,6 +84,7 @@ def test_calls_with_null_context_are_rejected(lib):
     assert lib.nbody_step(None, None, None, None, None, 0, 1, None) == 1
     assert lib.nbody_energy(None, None, None, None, None) == 1
     assert lib.nbody_adjoint(None, None, None, None, 1, 1, None, None, None, None, None) == 1
+    assert lib.nbody_adjoint_params(None, None, None, None, 1, 1, None, None, None, None, None, None) == 1
     assert lib.nbody_sync(None) == 1
     assert lib.nbody_launch_count(None) == 0
     lib.nbody_destroy(None)

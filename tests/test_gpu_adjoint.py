@@ -154,3 +154,112 @@ def test_adjoint_n16384_200_steps_vs_finite_differences(nb):
         err = np.abs(ad - fd) / np.maximum(np.abs(fd), 1e-3 * np.abs(fd).max())
         assert err.max() <= 1e-4, (prec, err.max(), np.argmax(err))
         ctx.close()
+
+
+# --------------------------------------------------------------------------------------
+# gradients with respect to G and eps (nbody_adjoint_params)
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-11), (1, 2e-5)])
+@pytest.mark.parametrize("T,K", [(20, 5), (9, 1), (5, 8)])
+def test_adjoint_params_match_oracle(nb, prec, tol, T, K):
+    import torch
+    G, eps, dt = 1.3, 0.05, 5e-3
+    x, v, m, t = _small_case(n=200, seed=31)
+    xT, vT, _, _ = oracle.kdk(x, v, m, G, eps, dt, T)
+    lx, lv = 2 * (xT - t), 0.1 * np.random.default_rng(4).standard_normal(xT.shape)
+    gx_o, gv_o, gm_o, (gG_o, ge_o) = oracle.adjoint_params(x, v, m, G, eps, dt, T, lx, lv)
+    ctx = nb.nbody_init(G=G, eps=eps, dt=dt, precision=prec, n=len(m))
+    args = to_dev(x, v, m) + (T, K) + to_dev(lx, lv)
+    gx, gv, gm, gp = nb.nbody_adjoint_params(ctx, *args)
+    nb.nbody_sync(ctx)
+    assert gp.shape == (1, 2)
+    gG, ge = gp.cpu().numpy()[0]
+    assert abs(gG - gG_o) <= tol * abs(gG_o) and abs(ge - ge_o) <= tol * abs(ge_o), (gG, gG_o, ge, ge_o)
+    # the parameter sums leave the other gradients as nbody_adjoint computes them
+    hx, hv, hm = nb.nbody_adjoint(ctx, *args)
+    assert torch.equal(gx, hx) and torch.equal(gv, hv) and torch.equal(gm, hm)
+    assert rel(gx.cpu().numpy(), gx_o) <= tol and rel(gm.cpu().numpy(), gm_o) <= tol
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-11), (1, 1e-4)])
+def test_adjoint_params_several_systems_and_mass_identity(nb, prec, tol):
+    # per-system rows against the oracle, an empty system's row zero, and
+    # G dL/dG = sum_j m_j dL/dm_j (G enters softened gravity only as G m_j) per system
+    sizes = [7, 130, 0, 300]
+    ens = inputs.ensemble(len(sizes), seed=8, sizes=np.array(sizes))
+    off = [int(o) for o in ens.offsets]
+    G, eps, dt, T, K = 0.8, 0.04, 4e-3, 10, 3
+    t = inputs.targets(off[-1], seed=9)
+    lx_all = np.zeros((off[-1], 3))
+    for s in range(len(sizes)):
+        b, e = off[s], off[s + 1]
+        if e > b:
+            xT, _, _, _ = oracle.kdk(ens.x[b:e], ens.v[b:e], ens.m[b:e], G, eps, dt, T)
+            lx_all[b:e] = 2 * (xT - t[b:e])
+    ctx = nb.nbody_init(G=G, eps=eps, dt=dt, precision=prec, offsets=off)
+    gx, gv, gm, gp = nb.nbody_adjoint_params(ctx, *to_dev(ens.x, ens.v, ens.m), T, K,
+                                             *to_dev(lx_all, np.zeros_like(lx_all)))
+    nb.nbody_sync(ctx)
+    gm, gp = to_np(gm, gp)
+    for s in range(len(sizes)):
+        b, e = off[s], off[s + 1]
+        if e == b:
+            assert np.all(gp[s] == 0)
+            continue
+        _, _, _, (oG, oe) = oracle.adjoint_params(ens.x[b:e], ens.v[b:e], ens.m[b:e], G, eps, dt, T, lx_all[b:e],
+                                                  np.zeros((e - b, 3)))
+        assert abs(gp[s, 0] - oG) <= tol * abs(oG) and abs(gp[s, 1] - oe) <= tol * abs(oe), (s, gp[s], oG, oe)
+        assert abs(G * gp[s, 0] - (ens.m[b:e] * gm[b:e]).sum()) <= tol * abs(G * gp[s, 0])
+
+
+def test_adjoint_params_rejects_null_and_lj(nb):
+    x, v, m, t = _small_case(16)
+    ctx = nb.nbody_init(G=1.0, eps=0.05, dt=1e-3, precision=nb.FP64, n=16)
+    lib = nb.load()
+    xt, vt, mt, lx = to_dev(x, v, m, np.ones((16, 3)))
+    g = [lx.clone() for _ in range(2)] + [mt.clone()]
+    ptr = lambda a: a.data_ptr()
+    st = lib.nbody_adjoint_params(ctx._h, ptr(xt), ptr(vt), ptr(mt), 3, 1, ptr(lx), ptr(lx), ptr(g[0]), ptr(g[1]),
+                                  ptr(g[2]), None)
+    assert st == 1
+    ctx2 = nb.nbody_init(law=nb.LENNARD_JONES, precision=nb.FP64, n=16, dt=1e-3)
+    with pytest.raises(nb.NBodyError) as ei:
+        nb.nbody_adjoint_params(ctx2, xt, vt, mt, 3, 1, lx, lx)
+    assert ei.value.status == 6
+
+
+@pytest.mark.slow
+def test_adjoint_params_n16384_200_steps_vs_finite_differences(nb):
+    """dL/dG and dL/deps at N = 16384 Plummer, 200 KDK steps, dt = 1e-3, checkpoints every 20,
+    against FP64 central differences (relative step 1e-6) of the FP64 GPU trajectory; <= 1e-4."""
+    import torch
+    n, G, eps, dt, T, K = 16384, 1.0, 0.01, 1e-3, 200, 20
+    x, v, m = inputs.plummer(n, seed=5)
+    t = inputs.targets(n, seed=6)
+    tt = to_dev(t)[0]
+
+    def final_x(g, e):
+        ctx = nb.nbody_init(G=g, eps=e, dt=dt, precision=nb.FP64, n=n)
+        xs, vs, mt = to_dev(x, v, m)
+        nb.nbody_step(ctx, xs, vs, mt, torch.empty_like(xs), False, T)
+        nb.nbody_sync(ctx)
+        ctx.close()
+        return xs
+
+    fd = []
+    for gp, ep, gm_, em in ((G * (1 + 1e-6), eps, G * (1 - 1e-6), eps), (G, eps * (1 + 1e-6), G, eps * (1 - 1e-6))):
+        xp, xm = final_x(gp, ep), final_x(gm_, em)
+        dL = float(((xp - xm) * (xp + xm - 2 * tt)).sum())
+        fd.append(dL / (gp - gm_ + ep - em))
+    for prec in (nb.FP64, nb.MIXED):
+        ctx = nb.nbody_init(G=G, eps=eps, dt=dt, precision=prec, n=n)
+        xt, vt, mt = to_dev(x, v, m)
+        xs, vs, a = xt.clone(), vt.clone(), torch.empty_like(xt)
+        nb.nbody_step(ctx, xs, vs, mt, a, False, T)
+        _, _, _, gp = nb.nbody_adjoint_params(ctx, xt, vt, mt, T, K, 2 * (xs - tt), torch.zeros_like(vs))
+        nb.nbody_sync(ctx)
+        ad = gp.cpu().numpy()[0]
+        err = np.abs(ad - np.array(fd)) / np.abs(np.array(fd))
+        assert err.max() <= 1e-4, (prec, ad, fd, err)
+        ctx.close()
