@@ -15,6 +15,7 @@ Sec. II-A and Sec. V-B, Sec. VI):
 * ``kdk``         leapfrog kick-drift-kick steps, one force evaluation per step
 * ``force_vjp``   w -> (dL/dx, dL/dm) through a(x, m) for dL/da = w
 * ``adjoint``     gradients of a final-state loss w.r.t. x0, v0, m through KDK
+* ``virial``      (K, W, -2K/W) with the Clausius virial W = sum_{i<j} (x_i - x_j) . F_ij
 * ``param_vjp``   w -> (sum_k w_k . da_k/dG, sum_k w_k . da_k/deps)
 * ``adjoint_params``  ``adjoint`` plus dL/dG and dL/deps
 * ``lj_*``         the same for the paper's Lennard-Jones pair law (Eq. 1):
@@ -64,13 +65,14 @@ def _load():
             lib.oracle_force_vjp.argtypes = [i64, p, p, p, d, d, p, p, i32]
             lib.oracle_adjoint.argtypes = [i64, p, p, p, d, d, d, i32, p, p, p, p, p, i32]
             lib.oracle_param_vjp.argtypes = [i64, p, p, p, d, d, p, i32]
+            lib.oracle_virial.argtypes = [i64, p, p, p, i32, d, d, d, d, d, p, i32]
             lib.oracle_adjoint_params.argtypes = [i64, p, p, p, d, d, d, i32, p, p, p, p, p, p, i32]
             lib.oracle_lj_forces.argtypes = [i64, p, p, d, d, d, p, p, i32]
             lib.oracle_lj_forces_at.argtypes = [i64, p, p, d, d, d, p, i64, p, p, i32]
             lib.oracle_lj_energy.argtypes = [i64, p, p, p, d, d, d, p, i32]
             lib.oracle_lj_kdk.argtypes = [i64, p, p, p, d, d, d, d, d, i32, p, i32, i32, p, i32]
             for f in ("oracle_forces", "oracle_forces_at", "oracle_energy", "oracle_kdk",
-                      "oracle_force_vjp", "oracle_adjoint", "oracle_param_vjp", "oracle_adjoint_params",
+                      "oracle_force_vjp", "oracle_adjoint", "oracle_param_vjp", "oracle_adjoint_params", "oracle_virial",
                       "oracle_lj_forces", "oracle_lj_forces_at",
                       "oracle_lj_energy", "oracle_lj_kdk"):
                 getattr(lib, f).restype = i32
@@ -172,6 +174,19 @@ def adjoint(x0, v0, m, G, eps, dt, n_steps, lam_xT, lam_vT, threads=0):
     _check(_load().oracle_adjoint(n, _ptr(x0), _ptr(v0), _ptr(m), G, eps, dt, int(n_steps), _ptr(lx), _ptr(lv),
                                   _ptr(gx), _ptr(gv), _ptr(gm), threads), "oracle_adjoint")
     return gx, gv, gm
+
+
+def virial(x, v, m, G=1.0, eps=0.0, threads=0, law=0, eps_lj=1.0, sigma=1.0, soft=0.0):
+    """(K, W, Q): kinetic energy, Clausius virial (pair form), virial ratio -2K/W.
+
+    law 0: softened gravity (G, eps); law 1: Lennard-Jones (eps_lj, sigma, soft)."""
+    m = _f64(m)
+    n = m.shape[0]
+    x, v = _f64(x, (n, 3)), _f64(v, (n, 3))
+    out = np.zeros(3)
+    _check(_load().oracle_virial(n, _ptr(x), _ptr(v), _ptr(m), int(law), G, eps, eps_lj, sigma, soft, _ptr(out),
+                                 threads), "oracle_virial")
+    return out
 
 
 def param_vjp(x, m, w, G=1.0, eps=0.0, threads=0):

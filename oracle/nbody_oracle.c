@@ -551,6 +551,68 @@ int oracle_lj_energy(int64_t n, const double* x, const double* v, const double* 
   return 0;
 }
 
+/* ------------------------------------------------------------------------ */
+/* virial diagnostics                                                         */
+/*
+ * Clausius virial W = sum_i x_i . F_i (F_i = m_i a_i) in its pair form: the
+ * pair (i, j) contributes (x_i - x_j) . F_ij, F_ij the force of j on i, i.e.
+ *   gravity:        -G m_i m_j |d|^2 / s^3,                 s^2 = |d|^2 + eps^2
+ *   Lennard-Jones:  24 eps_lj (2 sigma^12 / s^14 - sigma^6 / s^8) |d|^2,  s^2 = |d|^2 + soft^2
+ * so that the sum over i < j is independent of the origin and of any per-body
+ * route. out[3] = {K, W, Q = -2K/W (0 if W = 0)}.
+ */
+typedef struct {
+  int64_t n;
+  const double *x, *m;
+  int law;
+  double G, eps, eps_lj, sigma, soft;
+  double* row_w;
+} vir_args;
+
+static void virial_rows(int64_t lo, int64_t hi, void* p) {
+  vir_args* f = (vir_args*)p;
+  for (int64_t i = lo; i < hi; ++i) {
+    csum w = {0.0, 0.0};
+    for (int64_t j = i + 1; j < f->n; ++j) {
+      double dx = f->x[3 * j + 0] - f->x[3 * i + 0];
+      double dy = f->x[3 * j + 1] - f->x[3 * i + 1];
+      double dz = f->x[3 * j + 2] - f->x[3 * i + 2];
+      double r2 = dx * dx + dy * dy + dz * dz;
+      if (f->law == 0) {
+        double s2 = r2 + f->eps * f->eps;
+        double s = sqrt(s2);
+        csum_add(&w, -f->G * f->m[i] * f->m[j] * r2 / (s2 * s));
+      } else {
+        double s2 = r2 + f->soft * f->soft;
+        double u = f->sigma * f->sigma / s2; /* sigma^2 / s^2 */
+        double u3 = u * u * u;
+        csum_add(&w, 24.0 * f->eps_lj * (2.0 * u3 * u3 - u3) * r2 / s2);
+      }
+    }
+    f->row_w[i] = csum_get(&w);
+  }
+}
+
+int oracle_virial(int64_t n, const double* x, const double* v, const double* m, int law, double G, double eps,
+                  double eps_lj, double sigma, double soft, double* out, int nthreads) {
+  if (n < 0 || !out || (law != 0 && law != 1) || (n > 0 && (!x || !v || !m))) return 1;
+  double* row_w = (double*)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+  if (!row_w) return 2;
+  vir_args f = {n, x, m, law, G, eps, eps_lj, sigma, soft, row_w};
+  parallel_rows(n, nthreads, virial_rows, &f);
+  csum K = {0, 0}, W = {0, 0};
+  for (int64_t i = 0; i < n; ++i) {
+    const double* vi = v + 3 * i;
+    csum_add(&K, 0.5 * m[i] * (vi[0] * vi[0] + vi[1] * vi[1] + vi[2] * vi[2]));
+    csum_add(&W, row_w[i]);
+  }
+  free(row_w);
+  out[0] = csum_get(&K);
+  out[1] = csum_get(&W);
+  out[2] = out[1] != 0.0 ? -2.0 * out[0] / out[1] : 0.0;
+  return 0;
+}
+
 /*
  * Reflecting walls of the box [0, box]^3 ("boundary checking", Fig. 3/4
  * captions): after the drift, a coordinate that left the box is mirrored back

@@ -266,6 +266,51 @@ def test_ensemble_sizes_log_uniform():
 
 
 # --------------------------------------------------------------------------------------
+# virial diagnostics
+
+
+def test_virial_equals_potential_when_unsoftened_and_matches_per_body_form():
+    x, v, m = inputs.plummer(300, seed=2)
+    m = m * np.exp(0.2 * np.random.default_rng(2).standard_normal(300))
+    K, W, Q = oracle.virial(x, v, m, G=1.7, eps=0.0)
+    E = oracle.energy(x, v, m, G=1.7, eps=0.0)
+    # eps = 0: each pair gives -G m m r^2 / r^3 = -G m m / r, so W = U (Euler's theorem, degree -1)
+    assert abs(W - E[2]) <= 1e-13 * abs(E[2]) and abs(K - E[1]) <= 1e-14 * E[1]
+    assert Q == -2 * K / W
+    # softened: the pair form equals sum_i m_i x_i . a_i of the force sum, for any origin
+    for shift in (0.0, 3.0):
+        xs = x + shift
+        a, _ = oracle.forces(xs, m, G=1.7, eps=0.03)
+        assert abs(oracle.virial(xs, v, m, G=1.7, eps=0.03)[1] - (m[:, None] * xs * a).sum()) <= 1e-12 * abs(W)
+
+
+def test_virial_lennard_jones_pair_and_body_forms():
+    # one pair: W = r F(r) = -r dV/dr, zero at the minimum r = 2^(1/6) sigma
+    sig, el = 0.9, 1.3
+    for r, expect_zero in ((2 ** (1 / 6) * sig, True), (0.95 * sig, False), (1.7 * sig, False)):
+        x = np.array([[0.0, 0.0, 0.0], [r, 0.0, 0.0]])
+        v, m = np.zeros((2, 3)), np.ones(2)
+        W = oracle.virial(x, v, m, law=1, eps_lj=el, sigma=sig)[1]
+        h = 1e-6 * r
+        U = lambda rr: oracle.lj_energy(np.array([[0.0, 0, 0], [rr, 0, 0]]), v, m, eps_lj=el, sigma=sig)[2]
+        dV = (U(r + h) - U(r - h)) / (2 * h)
+        assert abs(W - (-r * dV)) <= 1e-7 * max(1.0, abs(W))
+        if expect_zero:
+            assert abs(W) <= 1e-12
+    x, v, m, box = inputs.lj_gas(200, seed=3)
+    a, _ = oracle.lj_forces(x, m, eps_lj=el, sigma=sig)
+    W = oracle.virial(x, v, m, law=1, eps_lj=el, sigma=sig)[1]
+    assert abs(W - (m[:, None] * x * a).sum()) <= 1e-11 * abs(W)
+
+
+def test_plummer_is_in_virial_equilibrium():
+    # the Plummer model is a self-consistent equilibrium: -2K/W -> 1 (statistical, ~1/sqrt(N))
+    x, v, m = inputs.plummer(4096, seed=11)
+    K, W, Q = oracle.virial(x, v, m, G=1.0, eps=0.0)
+    assert abs(Q - 1.0) <= 0.05, Q
+
+
+# --------------------------------------------------------------------------------------
 # adjoint
 
 
