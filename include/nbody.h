@@ -142,6 +142,16 @@ nbody_status nbody_step(nbody_ctx* ctx, double* x, double* v, const double* m, d
 nbody_status nbody_energy(nbody_ctx* ctx, const double* x, const double* v, const double* m, double* out);
 
 /*
+ * Virial diagnostics at the state (x, v): out [n_systems][3] (device) =
+ * {K, W, Q} with K = 1/2 sum m|v|^2, the Clausius virial W = sum m x . a
+ * (a from a force evaluation in the context's precision, either pair law; for
+ * softened gravity W = -G sum_{i<j} m_i m_j r_ij^2 / s_ij^3, equal to U when
+ * eps = 0) and the virial ratio Q = -2K/W (0 if W = 0; Q = 1 in virial
+ * equilibrium). Sums run in float64 in a fixed order.
+ */
+nbody_status nbody_virial(nbody_ctx* ctx, const double* x, const double* v, const double* m, double* out);
+
+/*
  * Reverse-mode gradient through n_steps KDK steps from (x0, v0) with masses m:
  * given lam_xT = dL/dx_T and lam_vT = dL/dv_T [N,3] (device), writes
  * g_x0 = dL/dx0, g_v0 = dL/dv0 [N,3] and g_m = dL/dm [N]. The forward

@@ -21,7 +21,8 @@ import threading
 
 __all__ = [
     "FP64", "MIXED", "GRAVITY", "LENNARD_JONES", "FLAG_GRAPH", "FLAG_NOCHECK", "NBodyError", "Context", "load", "lib_path",
-    "nbody_init", "nbody_forces", "nbody_step", "nbody_energy", "nbody_adjoint", "nbody_adjoint_params",
+    "nbody_init", "nbody_forces", "nbody_step", "nbody_energy", "nbody_virial", "nbody_adjoint",
+    "nbody_adjoint_params",
     "nbody_step_host",
     "nbody_sync", "nbody_get_tuning", "nbody_launch_count", "nbody_last_error", "nbody_destroy",
     "nbody_version", "nbody_profile", "nbody_kernel_time", "NBodyAdjoint", "ENERGY_FIELDS",
@@ -80,6 +81,7 @@ def load():
             "nbody_forces": (i32, [p, p, p, p, p]),
             "nbody_step": (i32, [p, p, p, p, p, i32, i32, p]),
             "nbody_energy": (i32, [p, p, p, p, p]),
+            "nbody_virial": (i32, [p, p, p, p, p]),
             "nbody_adjoint": (i32, [p, p, p, p, i32, i32, p, p, p, p, p]),
             "nbody_adjoint_params": (i32, [p, p, p, p, i32, i32, p, p, p, p, p, p]),
             "nbody_step_host": (i32, [p, p, p, p, p, i32, i32, p]),
@@ -244,6 +246,19 @@ def nbody_energy(ctx: Context, x, v, m, out=None):
             _dev(out, "out", (ctx.n_systems, 9), ctx))
     _bind_stream(ctx)
     _check(load().nbody_energy(ctx._h, *args), ctx)
+    return out
+
+
+def nbody_virial(ctx: Context, x, v, m, out=None):
+    """[n_systems, 3] = (K, W, Q): kinetic energy, Clausius virial sum m x.a, ratio -2K/W."""
+    torch = _torch()
+    n = ctx.n_total
+    if out is None:
+        out = torch.empty((ctx.n_systems, 3), dtype=torch.float64, device=x.device)
+    args = (_dev(x, "x", (n, 3), ctx), _dev(v, "v", (n, 3), ctx), _dev(m, "m", (n,), ctx),
+            _dev(out, "out", (ctx.n_systems, 3), ctx))
+    _bind_stream(ctx)
+    _check(load().nbody_virial(ctx._h, *args), ctx)
     return out
 
 

@@ -1133,6 +1133,27 @@ nbody_status nbody_energy(nbody_ctx* c, const double* x, const double* v, const 
   return run_post(c, P, c->stream);
 }
 
+nbody_status nbody_virial(nbody_ctx* c, const double* x, const double* v, const double* m, double* out) {
+  if (!c) return fail(nullptr, NBODY_EINVAL, "ctx is NULL");
+  nbody_status s;
+  if ((s = check_dev(c, out, (size_t)c->n_sys * 3 * sizeof(double), "out"))) return s;
+  if (c->n_total == 0) {
+    NB_CUDA(c, cudaMemsetAsync(out, 0, (size_t)c->n_sys * 3 * sizeof(double), c->stream));
+    return NBODY_OK;
+  }
+  if ((s = check_state_args(c, x, v, m, nullptr, true, false))) return s;
+  if ((s = ensure(c, c->a_scratch, (size_t)c->n_total * 3 * sizeof(double)))) return s;
+  double* xm = const_cast<double*>(x);
+  double* vm = const_cast<double*>(v);
+  double* as = static_cast<double*>(c->a_scratch.p);
+  if ((s = run_centre(c, x, m, c->stream))) return s;
+  if ((s = run_post(c, post_launch(c, kStage, xm, vm, m, as, nullptr), c->stream))) return s;
+  if ((s = run_force(c, c->stream))) return s;
+  PostLaunch P = post_launch(c, kCombine | kVirial, xm, vm, m, as, nullptr);
+  P.vout = out;
+  return run_post(c, P, c->stream);
+}
+
 nbody_status nbody_adjoint(nbody_ctx* c, const double* x0, const double* v0, const double* m, int32_t T,
                            int32_t K, const double* lam_xT, const double* lam_vT, double* g_x0, double* g_v0,
                            double* g_m) {
@@ -1146,8 +1167,6 @@ nbody_status nbody_adjoint_params(nbody_ctx* c, const double* x0, const double* 
   if (!g_params) return fail(c, NBODY_EINVAL, "g_params must be a device pointer to n_systems x 2 doubles");
   return adjoint_sweep(c, x0, v0, m, T, K, lam_xT, lam_vT, g_x0, g_v0, g_m, g_params);
 }
-
-
 
 nbody_status nbody_step_host(nbody_ctx* c, double* x, double* v, const double* m, double* a, int32_t a_valid,
                              int32_t n_steps, double* energy_log) {

@@ -72,6 +72,7 @@ enum PostMode : unsigned {
   kEnergy = 4u,    // per-chunk partial energies / momenta at (x, v)
   kDrift = 8u,     // v += dt/2 a; x += dt v (opening half-kick + drift of the next step)
   kStage = 16u,    // staging tile entry from x (after the drift, if any)
+  kVirial = 32u,   // per-chunk partial K and Clausius virial W = sum m x.a (not with kEnergy)
 };
 
 struct PostLaunch {
@@ -97,6 +98,7 @@ struct PostLaunch {
   double* epart;           // [n_chunks][kEnergyVals]
   unsigned* status;        // device status word
   double* eout;            // kEnergy: nullable [n_sys][9] record formed by the last CTA
+  double* vout;            // kVirial: [n_sys][3] record {K, W, -2K/W} formed by the last CTA
   const int32_t* sys_chunk;  // [n_sys + 1] chunk range of each system
   int n_sys;
   unsigned* done;          // last-CTA ticket (zero between launches)

@@ -146,6 +146,12 @@ __global__ void __launch_bounds__(kPostThreads) k_post(const PostLaunch P) {
     } else if (mode & (kKickEnd | kDrift)) {
       ax = P.a[3 * i + 0], ay = P.a[3 * i + 1], az = P.a[3 * i + 2];
     }
+    if (mode & kVirial) {
+      const double mi = P.m[i];
+      const double v0 = P.v[3 * i + 0], v1 = P.v[3 * i + 1], v2 = P.v[3 * i + 2];
+      e[0] += 0.5 * mi * (v0 * v0 + v1 * v1 + v2 * v2);
+      e[1] += mi * (P.x[3 * i + 0] * ax + P.x[3 * i + 1] * ay + P.x[3 * i + 2] * az);
+    }
     if (!(mode & (kKickEnd | kEnergy | kDrift | kStage))) continue;
     double x0 = P.x[3 * i + 0], x1 = P.x[3 * i + 1], x2 = P.x[3 * i + 2];
     const double m = P.m[i];
@@ -178,6 +184,22 @@ __global__ void __launch_bounds__(kPostThreads) k_post(const PostLaunch P) {
     if (mode & kStage) stage_store(P.precision, P.stage, i, x0, x1, x2, m, cen, P.stage_lo);
   }
   if (bad) atomicOr(P.status, kFlagNonFinite);
+  if (mode & kVirial) {
+    double kw[2] = {e[0], e[1]};
+    block_sum<2, kPostThreads>(kw);
+    if (threadIdx.x == 0) P.epart[(int64_t)blockIdx.x * kEnergyVals + 0] = kw[0],
+                          P.epart[(int64_t)blockIdx.x * kEnergyVals + 1] = kw[1];
+    if (last_cta(P.done)) {
+      __threadfence();
+      systems_final<2>(P.sys_chunk, P.n_sys, P.epart, [&](int sy, const double (&v)[2]) {
+        double* o = P.vout + 3 * (int64_t)sy;
+        o[0] = v[0];
+        o[1] = v[1];
+        o[2] = v[1] != 0.0 ? -2.0 * v[0] / v[1] : 0.0;
+      });
+    }
+    return;
+  }
   if (mode & kEnergy) {
     block_sum<kEnergyVals, kPostThreads>(e);
     if (threadIdx.x == 0) {

@@ -291,3 +291,35 @@ def test_near_pairs_far_from_origin(nb, variant):
     a_ref, phi_ref = oracle.forces(x, m, G=1.0, eps=eps)
     e = force_rel_err(a, a_ref)
     assert np.median(e) <= MIX_MED and e.max() <= MIX_MAX, (np.median(e), e.max())
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-12), (1, 1e-6)])
+def test_virial_matches_oracle(nb, prec, tol):
+    sizes = [300, 0, 1200, 37]
+    ens = inputs.ensemble(len(sizes), seed=17, sizes=np.array(sizes))
+    off = [int(o) for o in ens.offsets]
+    G, eps = 1.2, 0.02
+    ctx = nb.nbody_init(G=G, eps=eps, dt=1e-3, precision=prec, offsets=off)
+    out = nb.nbody_virial(ctx, *to_dev(ens.x, ens.v, ens.m))
+    nb.nbody_sync(ctx)
+    out = out.cpu().numpy()
+    for s in range(len(sizes)):
+        b, e = off[s], off[s + 1]
+        if e == b:
+            assert np.all(out[s] == 0)
+            continue
+        K, W, Q = oracle.virial(ens.x[b:e], ens.v[b:e], ens.m[b:e], G=G, eps=eps)
+        assert abs(out[s, 0] - K) <= 1e-13 * K
+        assert abs(out[s, 1] - W) <= tol * abs(W), (s, out[s], W)
+        assert abs(out[s, 2] - Q) <= 2 * tol * abs(Q)
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-12), (1, 1e-6)])
+def test_virial_lennard_jones_matches_oracle(nb, prec, tol):
+    x, v, m, box = inputs.lj_gas(2000, seed=19, density=0.2)
+    ctx = nb.nbody_init(law=nb.LENNARD_JONES, precision=prec, n=2000, dt=1e-3, lj_epsilon=1.1, lj_sigma=0.95)
+    out = nb.nbody_virial(ctx, *to_dev(x, v, m))
+    nb.nbody_sync(ctx)
+    K, W, Q = oracle.virial(x, v, m, law=1, eps_lj=1.1, sigma=0.95)
+    got = out.cpu().numpy()[0]
+    assert abs(got[1] - W) <= tol * abs(W) and abs(got[0] - K) <= 1e-13 * K, (got, W)
