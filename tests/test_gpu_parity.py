@@ -323,3 +323,27 @@ def test_virial_lennard_jones_matches_oracle(nb, prec, tol):
     K, W, Q = oracle.virial(x, v, m, law=1, eps_lj=1.1, sigma=0.95)
     got = out.cpu().numpy()[0]
     assert abs(got[1] - W) <= tol * abs(W) and abs(got[0] - K) <= 1e-13 * K, (got, W)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_ring_schedule_passes_agree(nb, prec):
+    """The paper's ring exchange (Sec. V-B, Fig. 1) as a blocked schedule on one GPU: P j-slices
+    play the P ranks' blocks, each an (i-tile, j-block) pass with its own float64 partial folded
+    in a fixed order. Every P gives the oracle's forces; FP64 results agree across P to rounding."""
+    n = 4096
+    x, v, m = inputs.plummer(n, seed=23)
+    a_ref, _ = oracle.forces(x, m, G=1.0, eps=0.01)
+    res = []
+    for P in (1, 2, 3, 4, 8):
+        sl = -(-n // P)
+        sl = -(-sl // 128) * 128
+        ctx, a, _ = _forces(nb, prec, x, m, 1.0, 0.01, block=128, i_per_thread=1, j_tile=128, slice=sl)
+        assert nb.nbody_get_tuning(ctx)["slice"] == sl
+        res.append(a)
+        e = force_rel_err(a, a_ref)
+        if prec == nb.FP64:
+            assert e.max() <= FP64_TOL
+        else:
+            assert np.median(e) <= MIX_MED and e.max() <= MIX_MAX
+    for a in res[1:]:
+        assert force_rel_err(a, res[0]).max() <= (1e-13 if prec == nb.FP64 else 1e-5)
