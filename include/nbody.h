@@ -82,8 +82,9 @@ typedef struct {
                            NBODY_MIXED) (0 = autotune) */
   int32_t slice;        /* force kernel: j-bodies per work item, multiple of j_tile (0 = autotune) */
   uint32_t flags;       /* NBODY_FLAG_* */
-  int32_t variant;      /* mixed force kernel: 1 = scalar float32, 2 = packed float32x2, 0 = autotune;
-                           must be 0 or 1 for NBODY_FP64; NBODY_LAW_LJ with NBODY_MIXED uses 2 */
+  int32_t variant;      /* mixed force and adjoint-VJP kernels: 1 = scalar float32, 2 = packed
+                           float32x2, 0 = autotune (each kernel separately); must be 0 or 1 for
+                           NBODY_FP64; NBODY_LAW_LJ with NBODY_MIXED uses 2 */
   int32_t law;          /* nbody_law */
   int32_t reserved;     /* must be 0 */
   double lj_epsilon;    /* Lennard-Jones well depth (finite; law = NBODY_LAW_LJ) */

@@ -16,6 +16,7 @@
 // Tiling, work distribution, self-pair masking and the compensated per-tile
 // fold are those of the force kernels.
 #include <algorithm>
+#include <type_traits>
 
 #include "nbody_internal.h"
 #include "pair_common.cuh"
@@ -294,6 +295,201 @@ __global__ void __launch_bounds__(BLOCK) k_vjp_fp64(const PairLaunch L) {
   retire_cta(L.counter);
 }
 
+// ---- packed float32x2 form: two j-bodies per instruction (j-pairs from a
+// structure-of-arrays tile, the i-body duplicated in both lanes), 13 packed
+// FMA-pipe operations and two MUFU.RSQ per pair of interactions. The tile holds
+// -m_j, so that the one subtraction of the pair (m_k (d.w_j) - m_j (d.w_k))
+// needs no negation: A2, Pg and Pe are accumulated negated and flipped at the end.
+
+struct Acc2 {
+  float2 a1x, a1y, a1z, a2n, gbx, gby, gbz, gm, pgn, pen;
+};
+
+template <bool MASK, bool P>
+__device__ __forceinline__ void vjp_pair2(const float2 xj, const float2 yj, const float2 zj, const float2 mjn,
+                                          const float2 wxj, const float2 wyj, const float2 wzj, const int jg0,
+                                          const int ig, const float2 nx, const float2 ny, const float2 nz,
+                                          const float2 mk, const float2 wkx, const float2 wky, const float2 wkz,
+                                          const float2 e2, Acc2& s) {
+  const float2 dx = __fadd2_rn(xj, nx);
+  const float2 dy = __fadd2_rn(yj, ny);
+  const float2 dz = __fadd2_rn(zj, nz);
+  const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __ffma2_rn(dz, dz, e2)));
+  float2 inv = make_float2(rsq_approx(r2.x), rsq_approx(r2.y));
+  if (MASK) {
+    inv.x = (jg0 == ig) ? 0.f : inv.x;
+    inv.y = (jg0 + 1 == ig) ? 0.f : inv.y;
+  }
+  const float2 inv2 = __fmul2_rn(inv, inv);
+  const float2 inv3 = __fmul2_rn(inv2, inv);
+  const float2 dwj = __ffma2_rn(dx, wxj, __ffma2_rn(dy, wyj, __fmul2_rn(dz, wzj)));
+  const float2 dwk = __ffma2_rn(dx, wkx, __ffma2_rn(dy, wky, __fmul2_rn(dz, wkz)));
+  s.gm = __ffma2_rn(dwj, inv3, s.gm);
+  const float2 pkn = __fmul2_rn(mjn, dwk);      // -m_j (d.w_k)
+  const float2 du = __ffma2_rn(mk, dwj, pkn);   // m_k (d.w_j) - m_j (d.w_k)
+  const float2 inv5 = __fmul2_rn(inv3, inv2);
+  const float2 t = __fmul2_rn(du, inv5);
+  s.gbx = __ffma2_rn(t, dx, s.gbx);
+  s.gby = __ffma2_rn(t, dy, s.gby);
+  s.gbz = __ffma2_rn(t, dz, s.gbz);
+  s.a1x = __ffma2_rn(inv3, wxj, s.a1x);
+  s.a1y = __ffma2_rn(inv3, wyj, s.a1y);
+  s.a1z = __ffma2_rn(inv3, wzj, s.a1z);
+  s.a2n = __ffma2_rn(mjn, inv3, s.a2n);
+  if (P) {
+    s.pgn = __ffma2_rn(pkn, inv3, s.pgn);
+    s.pen = __ffma2_rn(pkn, inv5, s.pen);
+  }
+}
+
+// far, massless, weightless padding of a tile to whole quads
+constexpr float kFarAwayV = 1.0e18f;
+
+template <int BLOCK, int R, int J, bool P>
+__global__ void __launch_bounds__(BLOCK) k_vjp_mixed2(const PairLaunch L) {
+  static_assert(J % 4 == 0, "tiles hold whole quads of j-bodies");
+  constexpr int LPT = (J + BLOCK - 1) / BLOCK;
+  constexpr int NC = P ? 10 : 8;  // compensated components per i-body
+  __shared__ __align__(16) float tx[2][J], ty[2][J], tz[2][J], tmn[2][J];
+  __shared__ __align__(16) float twx[2][J], twy[2][J], twz[2][J];
+  __shared__ int s_item;
+  const float4* __restrict__ sx = static_cast<const float4*>(L.stage_x);
+  const float4* __restrict__ sw = static_cast<const float4*>(L.stage_w);
+  double4_32a* __restrict__ part = reinterpret_cast<double4_32a*>(L.part);
+  const float eps2 = (float)L.eps2;
+  const float2 e2 = make_float2(eps2, eps2);
+
+  auto put = [&](const int b, const int t, const float4 q, const float4 u) {
+    tx[b][t] = q.x, ty[b][t] = q.y, tz[b][t] = q.z, tmn[b][t] = -q.w;
+    twx[b][t] = u.x, twy[b][t] = u.y, twz[b][t] = u.z;
+  };
+  auto pad = [&](const int b, const int t) {
+    tx[b][t] = kFarAwayV, ty[b][t] = kFarAwayV, tz[b][t] = kFarAwayV, tmn[b][t] = 0.f;
+    twx[b][t] = 0.f, twy[b][t] = 0.f, twz[b][t] = 0.f;
+  };
+
+  for (;;) {
+    const int it = next_item(L.counter, &s_item);
+    if (it >= L.n_items) break;
+    const WorkItem w = L.items[it];
+
+    float2 nx[R], ny[R], nz[R], mk[R], wkx[R], wky[R], wkz[R];
+    float hi[R][NC], lo[R][NC];
+    int ig[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      ig[r] = w.i_begin + (int)threadIdx.x + r * BLOCK;
+      const bool ok = ig[r] < w.i_end;
+      const float4 q = ok ? sx[ig[r]] : make_float4(0.f, 0.f, 0.f, 0.f);
+      const float4 u = ok ? sw[ig[r]] : make_float4(0.f, 0.f, 0.f, 0.f);
+      nx[r] = make_float2(-q.x, -q.x), ny[r] = make_float2(-q.y, -q.y), nz[r] = make_float2(-q.z, -q.z);
+      mk[r] = make_float2(q.w, q.w);
+      wkx[r] = make_float2(u.x, u.x), wky[r] = make_float2(u.y, u.y), wkz[r] = make_float2(u.z, u.z);
+#pragma unroll
+      for (int c = 0; c < NC; ++c) hi[r][c] = lo[r][c] = 0.f;
+    }
+
+    {
+      const int nj = min(J, w.j_end - w.j_begin), nj4 = (nj + 3) & ~3;
+#pragma unroll
+      for (int k = 0; k < LPT; ++k) {
+        const int t = (int)threadIdx.x + k * BLOCK;
+        if (t < nj)
+          put(0, t, sx[w.j_begin + t], sw[w.j_begin + t]);
+        else if (t < nj4)
+          pad(0, t);
+      }
+    }
+    __syncthreads();
+
+    int buf = 0;
+    for (int jt = w.j_begin; jt < w.j_end; jt += J, buf ^= 1) {
+      const int nj = min(J, w.j_end - jt), nj4 = (nj + 3) & ~3;
+      const bool more = jt + J < w.j_end;
+      float4 px[LPT], pw[LPT];
+      if (more) {
+#pragma unroll
+        for (int k = 0; k < LPT; ++k) {
+          const int jj = jt + J + (int)threadIdx.x + k * BLOCK;
+          if ((int)threadIdx.x + k * BLOCK < J && jj < w.j_end) px[k] = sx[jj], pw[k] = sw[jj];
+        }
+      }
+      Acc2 s[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const float2 z = make_float2(0.f, 0.f);
+        s[r] = Acc2{z, z, z, z, z, z, z, z, z, z};
+      }
+      const bool diag = (jt < w.i_end) && (w.i_begin < jt + nj);
+      const float *cx = tx[buf], *cy = ty[buf], *cz = tz[buf], *cm = tmn[buf];
+      const float *cwx = twx[buf], *cwy = twy[buf], *cwz = twz[buf];
+      auto quad = [&](const int j, auto mask) {
+        constexpr bool M = decltype(mask)::value;
+        const float4 X = *reinterpret_cast<const float4*>(cx + j);
+        const float4 Y = *reinterpret_cast<const float4*>(cy + j);
+        const float4 Z = *reinterpret_cast<const float4*>(cz + j);
+        const float4 Mn = *reinterpret_cast<const float4*>(cm + j);
+        const float4 WX = *reinterpret_cast<const float4*>(cwx + j);
+        const float4 WY = *reinterpret_cast<const float4*>(cwy + j);
+        const float4 WZ = *reinterpret_cast<const float4*>(cwz + j);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          vjp_pair2<M, P>(make_float2(X.x, X.y), make_float2(Y.x, Y.y), make_float2(Z.x, Z.y),
+                          make_float2(Mn.x, Mn.y), make_float2(WX.x, WX.y), make_float2(WY.x, WY.y),
+                          make_float2(WZ.x, WZ.y), jt + j, ig[r], nx[r], ny[r], nz[r], mk[r], wkx[r], wky[r],
+                          wkz[r], e2, s[r]);
+          vjp_pair2<M, P>(make_float2(X.z, X.w), make_float2(Y.z, Y.w), make_float2(Z.z, Z.w),
+                          make_float2(Mn.z, Mn.w), make_float2(WX.z, WX.w), make_float2(WY.z, WY.w),
+                          make_float2(WZ.z, WZ.w), jt + j + 2, ig[r], nx[r], ny[r], nz[r], mk[r], wkx[r], wky[r],
+                          wkz[r], e2, s[r]);
+        }
+      };
+      if (diag) {
+        for (int j = 0; j < nj4; j += 4) quad(j, std::true_type{});
+      } else {
+#pragma unroll 2
+        for (int j = 0; j < nj4; j += 4) quad(j, std::false_type{});
+      }
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const float v[10] = {s[r].a1x.x + s[r].a1x.y, s[r].a1y.x + s[r].a1y.y, s[r].a1z.x + s[r].a1z.y,
+                             -(s[r].a2n.x + s[r].a2n.y), s[r].gbx.x + s[r].gbx.y, s[r].gby.x + s[r].gby.y,
+                             s[r].gbz.x + s[r].gbz.y, s[r].gm.x + s[r].gm.y, -(s[r].pgn.x + s[r].pgn.y),
+                             -(s[r].pen.x + s[r].pen.y)};
+#pragma unroll
+        for (int c = 0; c < NC; ++c) two_sum_acc(hi[r][c], lo[r][c], v[c]);
+      }
+      if (more) {
+        const int nn = min(J, w.j_end - jt - J), nn4 = (nn + 3) & ~3;
+#pragma unroll
+        for (int k = 0; k < LPT; ++k) {
+          const int t = (int)threadIdx.x + k * BLOCK;
+          if (t < nn)
+            put(buf ^ 1, t, px[k], pw[k]);
+          else if (t < nn4)
+            pad(buf ^ 1, t);
+        }
+      }
+      __syncthreads();
+    }
+
+    constexpr int kW = P ? 3 : 2;  // double4 per body and slice
+    double4_32a* out = part + kW * ((int64_t)w.slice * L.n_total);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      if (ig[r] < w.i_end) {
+        double d[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) d[c] = (double)hi[r][c] + (double)lo[r][c];
+        out[kW * (int64_t)ig[r]] = make_double4_32a(d[0], d[1], d[2], d[3]);
+        out[kW * (int64_t)ig[r] + 1] = make_double4_32a(d[4], d[5], d[6], d[7]);
+        if constexpr (P) out[kW * (int64_t)ig[r] + 2] = make_double4_32a(d[8], d[9], 0.0, 0.0);
+      }
+    }
+  }
+  retire_cta(L.counter);
+}
+
 template <typename K>
 int occupancy_of(K kern, int block) {
   int n = 0;
@@ -301,8 +497,9 @@ int occupancy_of(K kern, int block) {
   return n;
 }
 
-// Tilings compiled for the VJP: BLOCK in {128, 256}, R in {1, 2}, J = 128.
-#define NBODY_VJP_TILINGS(X) X(128, 1, 128) X(128, 2, 128) X(256, 1, 128) X(256, 2, 128)
+// Tilings compiled for the VJP: BLOCK in {128, 256}, R in {1, 2}, J in {128, 256}.
+#define NBODY_VJP_TILINGS(X) \
+  X(128, 1, 128) X(128, 2, 128) X(256, 1, 128) X(256, 2, 128) X(128, 1, 256) X(128, 2, 256) X(256, 1, 256) X(256, 2, 256)
 
 }  // namespace
 
@@ -310,7 +507,11 @@ cudaError_t launch_vjp(int precision, const PairLaunch& L, cudaStream_t st) {
   if (L.n_ctas <= 0) return cudaErrorInvalidConfiguration;
 #define NBODY_X(B, R, J)                                                 \
   if (L.block == B && L.ipt == R && L.jtile == J) {                      \
-    if (precision == 1 && L.params)                                      \
+    if (precision == 1 && L.variant == 1 && L.params)                    \
+      k_vjp_mixed2<B, R, J, true><<<L.n_ctas, B, 0, st>>>(L);            \
+    else if (precision == 1 && L.variant == 1)                           \
+      k_vjp_mixed2<B, R, J, false><<<L.n_ctas, B, 0, st>>>(L);           \
+    else if (precision == 1 && L.params)                                 \
       k_vjp_mixed<B, R, J, true><<<L.n_ctas, B, 0, st>>>(L);             \
     else if (precision == 1)                                             \
       k_vjp_mixed<B, R, J, false><<<L.n_ctas, B, 0, st>>>(L);            \
@@ -325,12 +526,16 @@ cudaError_t launch_vjp(int precision, const PairLaunch& L, cudaStream_t st) {
   return cudaErrorInvalidConfiguration;
 }
 
-int vjp_ctas_per_sm(int precision, int block, int ipt, int jtile) {
-#define NBODY_X(B, R, J)                                                                              \
-  if (block == B && ipt == R && jtile == J)                                                           \
-    return precision == 1                                                                             \
+int vjp_ctas_per_sm(int precision, int variant, int block, int ipt, int jtile) {
+  if (variant != 0 && (variant != 1 || precision != 1)) return 0;
+#define NBODY_X(B, R, J)                                                                                     \
+  if (block == B && ipt == R && jtile == J) {                                                                \
+    if (precision == 1 && variant == 1)                                                                      \
+      return std::min(occupancy_of(k_vjp_mixed2<B, R, J, false>, B), occupancy_of(k_vjp_mixed2<B, R, J, true>, B)); \
+    return precision == 1                                                                                    \
                ? std::min(occupancy_of(k_vjp_mixed<B, R, J, false>, B), occupancy_of(k_vjp_mixed<B, R, J, true>, B)) \
-               : std::min(occupancy_of(k_vjp_fp64<B, R, J, false>, B), occupancy_of(k_vjp_fp64<B, R, J, true>, B));
+               : std::min(occupancy_of(k_vjp_fp64<B, R, J, false>, B), occupancy_of(k_vjp_fp64<B, R, J, true>, B)); \
+  }
   NBODY_VJP_TILINGS(NBODY_X)
 #undef NBODY_X
   return 0;

@@ -229,9 +229,8 @@ nbody_status check_dev(nbody_ctx* c, const void* p, size_t bytes, const char* na
 // work lists
 
 int ctas_per_sm(int prec, const Tiling& t, bool vjp, int law) {
-  if (!vjp) return force_ctas_per_sm(prec, t.variant, t.block, t.ipt, t.jtile, law);
-  return vjp ? vjp_ctas_per_sm(prec, t.block, t.ipt, t.jtile)
-             : force_ctas_per_sm(prec, t.variant, t.block, t.ipt, t.jtile, 0);
+  return vjp ? vjp_ctas_per_sm(prec, t.variant, t.block, t.ipt, t.jtile)
+             : force_ctas_per_sm(prec, t.variant, t.block, t.ipt, t.jtile, law);
 }
 
 // Slice length for tiling t: the largest power-of-two multiple of jtile that
@@ -395,7 +394,7 @@ PairLaunch pair_launch(nbody_ctx* c, bool vjp, bool refine = false) {
   L.eps2 = c->cfg.eps * c->cfg.eps;
   const Tiling& t = vjp ? c->vt : c->ft;
   L.block = t.block, L.ipt = t.ipt, L.jtile = t.jtile, L.n_ctas = t.n_ctas;
-  L.variant = vjp ? 0 : t.variant;
+  L.variant = t.variant;
   L.params = vjp && c->vjp_params ? 1 : 0;
   return L;
 }
@@ -650,20 +649,21 @@ nbody_status autotune(nbody_ctx* c, bool vjp) {
   std::vector<Tiling> cands;
   const int blocks[] = {128, 256};
   const int ipts_f[] = {1, 2, 4}, ipts_v[] = {1, 2};
-  const int jts_v[] = {128};
+  const int jts_v[] = {128, 256};
   // j-tiles: 128 and 256 for every kernel, 512 for the mixed kernels
   const std::vector<int> jts_f = g.precision == NBODY_MIXED ? std::vector<int>{128, 256, 512} : std::vector<int>{128, 256};
   std::vector<int> variants = {0};
-  if (!vjp && g.precision == NBODY_MIXED) {
+  if (g.precision == NBODY_MIXED) {
+    // a variant fixed by the caller applies to the force and the VJP kernels
     variants = g.variant ? std::vector<int>{g.variant - 1} : std::vector<int>{0, 1};
-    if (g.law == NBODY_LAW_LJ) variants = {1};  // Lennard-Jones: packed kernel only
+    if (!vjp && g.law == NBODY_LAW_LJ) variants = {1};  // Lennard-Jones: packed kernel only
   }
   for (int var : variants)
     for (int b : blocks) {
       if (!vjp && g.block && g.block != b) continue;
       for (int r : (vjp ? std::vector<int>(ipts_v, ipts_v + 2) : std::vector<int>(ipts_f, ipts_f + 3))) {
         if (!vjp && g.i_per_thread && g.i_per_thread != r) continue;
-        for (int j : (vjp ? std::vector<int>(jts_v, jts_v + 1) : jts_f)) {
+        for (int j : (vjp ? std::vector<int>(jts_v, jts_v + 2) : jts_f)) {
           if (!vjp && g.j_tile && g.j_tile != j) continue;
           Tiling t;
           t.block = b, t.ipt = r, t.jtile = j, t.slice = vjp ? 0 : g.slice, t.variant = var;

@@ -48,7 +48,7 @@ struct PairLaunch {
   double eps2;
   const float4* stage_lo;  // force (mixed): float32 remainders (x - c) - hi [N], near-pair refinement
   float r2_near;         // force (mixed): refine pairs with s^2 below this (0 = never)
-  int variant;           // force (mixed): 0 scalar float32, 1 packed float32x2
+  int variant;           // mixed kernels: 0 scalar float32, 1 packed float32x2
   int law;               // 0 softened gravity, 1 Lennard-Jones
   double sigma2;         // Lennard-Jones sigma^2
   int block, ipt, jtile; // tiling
@@ -61,7 +61,7 @@ cudaError_t launch_force(int precision, const PairLaunch& L, cudaStream_t st);
 cudaError_t launch_vjp(int precision, const PairLaunch& L, cudaStream_t st);
 // CTAs of the force kernel that fit on one SM for the tiling (0 if unsupported).
 int force_ctas_per_sm(int precision, int variant, int block, int ipt, int jtile, int law);
-int vjp_ctas_per_sm(int precision, int block, int ipt, int jtile);
+int vjp_ctas_per_sm(int precision, int variant, int block, int ipt, int jtile);
 
 // ---------------------------------------------------------------------------
 // O(N) kernels (post_kernels.cu)

@@ -263,3 +263,26 @@ def test_adjoint_params_n16384_200_steps_vs_finite_differences(nb):
         err = np.abs(ad - np.array(fd)) / np.abs(np.array(fd))
         assert err.max() <= 1e-4, (prec, ad, fd, err)
         ctx.close()
+
+
+@pytest.mark.parametrize("variant", [1, 2])
+@pytest.mark.parametrize("n,T,K", [(203, 12, 5), (64, 7, 7), (1, 3, 2), (517, 4, 1)])
+def test_scalar_and_packed_vjp_match_oracle(nb, variant, n, T, K):
+    """Both mixed VJP kernels (scalar float32, packed float32x2 over j-pairs with a padded,
+    ragged last tile) against the oracle's reverse sweep, gradients and parameter gradients."""
+    G, eps, dt = 1.1, 0.05, 5e-3
+    x, v, m, t = _small_case(n, seed=50 + n)
+    xT, vT, _, _ = oracle.kdk(x, v, m, G, eps, dt, T)
+    lx, lv = 2 * (xT - t), 0.1 * np.random.default_rng(9).standard_normal(xT.shape)
+    gx_o, gv_o, gm_o, (gG_o, ge_o) = oracle.adjoint_params(x, v, m, G, eps, dt, T, lx, lv)
+    ctx = nb.nbody_init(G=G, eps=eps, dt=dt, precision=nb.MIXED, n=n, variant=variant)
+    gx, gv, gm, gp = nb.nbody_adjoint_params(ctx, *to_dev(x, v, m), T, K, *to_dev(lx, lv))
+    nb.nbody_sync(ctx)
+    gx, gv, gm, gp = to_np(gx, gv, gm, gp)
+    tol = 2e-5
+    assert rel(gx, gx_o) <= tol and rel(gv, gv_o) <= tol, (rel(gx, gx_o), rel(gv, gv_o))
+    if n > 1:
+        assert rel(gm, gm_o) <= tol and abs(gp[0, 0] - gG_o) <= tol * abs(gG_o)
+        assert abs(gp[0, 1] - ge_o) <= tol * abs(ge_o), (gp, gG_o, ge_o)
+    else:
+        assert np.all(gm == 0) and np.all(gp == 0)
