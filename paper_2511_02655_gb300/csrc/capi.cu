@@ -609,7 +609,9 @@ nbody_status time_tiling(nbody_ctx* c, bool vjp, double* cost) {
     cudaError_t err = launch(P);  // warm-up; also writes every partial the combine reads
     if (err == cudaSuccess && combine) err = launch_post(C, c->stream);
     *best_ms = 1e30f;
-    for (int rep = 0; rep < 3 && err == cudaSuccess; ++rep) {
+    // best of 3 launches, or of as many as fill ~2 ms (at most 20) for short ones
+    int reps = 3;
+    for (int rep = 0; rep < reps && err == cudaSuccess; ++rep) {
       err = cudaEventRecord(ev[0], c->stream);
       if (err == cudaSuccess) err = launch(P);
       if (err == cudaSuccess && combine) err = launch_post(C, c->stream);
@@ -618,8 +620,9 @@ nbody_status time_tiling(nbody_ctx* c, bool vjp, double* cost) {
       float ms = 0.f;
       if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, ev[0], ev[1]);
       if (err == cudaSuccess) *best_ms = std::min(*best_ms, ms);
+      if (rep == 0 && err == cudaSuccess) reps = std::max(3, std::min(20, (int)std::ceil(2.0 / std::max(ms, 1e-3f))));
     }
-    c->launches += 4 * (combine ? 2 : 1);
+    c->launches += (reps + 1) * (combine ? 2 : 1);
     return err;
   };
   PairLaunch P = L;

@@ -292,17 +292,21 @@ __device__ __forceinline__ void pair2_f32x2(const float2 xj, const float2 yj, co
 //   sum (u^3 - 2 u^6) / r^2 d  (a_i = 24 eps / m_i times this)
 //   sum (u^6 - u^3)            (phi_i = 4 eps / m_i times this),
 // 17 float32 operations (8.5 packed) and one MUFU.RCP per interaction.
+// Near pairs are common in a gas (a dozen neighbours inside the 4 sigma
+// refinement radius per particle), so instead of a running minimum each pair
+// sets its bit in the sub-block's near mask (bit0 for the first j-body, the
+// next bit for the second) and the second look visits exactly those pairs.
 template <bool MASK>
 __device__ __forceinline__ void pair2_lj_f32x2(const float2 xj, const float2 yj, const float2 zj, const int jg0,
                                                const int ig, const float2 nx, const float2 ny, const float2 nz,
                                                const float2 e2, const float2 s2, float2& ax, float2& ay, float2& az,
-                                               float2& pp, float& mn0, float& mn1) {
+                                               float2& pp, unsigned& near, const unsigned bit0, const float r2c) {
   const float2 dx = __fadd2_rn(xj, nx);
   const float2 dy = __fadd2_rn(yj, ny);
   const float2 dz = __fadd2_rn(zj, nz);
   const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __ffma2_rn(dz, dz, e2)));
-  mn0 = fminf(mn0, r2.x);
-  mn1 = fminf(mn1, r2.y);
+  if (r2.x < r2c) near |= bit0;
+  if (r2.y < r2c) near |= bit0 << 1;
   float2 inv2 = make_float2(rcp_approx(r2.x), rcp_approx(r2.y));
   if (MASK) {
     inv2.x = (jg0 == ig) ? 0.f : inv2.x;
@@ -324,7 +328,8 @@ __device__ __forceinline__ void quad_f32x2(const float* tx, const float* ty, con
                                            const int j, const int jg, const int (&ig)[R], const float2 (&nx)[R],
                                            const float2 (&ny)[R], const float2 (&nz)[R], const float2 e2,
                                            const float2 s2, float2 (&ax)[R], float2 (&ay)[R], float2 (&az)[R],
-                                           float2 (&pp)[R], float& mn0, float& mn1) {
+                                           float2 (&pp)[R], float& mn0, float& mn1, unsigned (&near)[R],
+                                           const unsigned qbit, const float r2c) {
   const float4 X = *reinterpret_cast<const float4*>(tx + j);
   const float4 Y = *reinterpret_cast<const float4*>(ty + j);
   const float4 Z = *reinterpret_cast<const float4*>(tz + j);
@@ -343,9 +348,9 @@ __device__ __forceinline__ void quad_f32x2(const float* tx, const float* ty, con
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       pair2_lj_f32x2<MASK>(make_float2(X.x, X.y), make_float2(Y.x, Y.y), make_float2(Z.x, Z.y), jg, ig[r], nx[r],
-                           ny[r], nz[r], e2, s2, ax[r], ay[r], az[r], pp[r], mn0, mn1);
+                           ny[r], nz[r], e2, s2, ax[r], ay[r], az[r], pp[r], near[r], qbit, r2c);
       pair2_lj_f32x2<MASK>(make_float2(X.z, X.w), make_float2(Y.z, Y.w), make_float2(Z.z, Z.w), jg + 2, ig[r],
-                           nx[r], ny[r], nz[r], e2, s2, ax[r], ay[r], az[r], pp[r], mn0, mn1);
+                           nx[r], ny[r], nz[r], e2, s2, ax[r], ay[r], az[r], pp[r], near[r], qbit << 2, r2c);
     }
   }
 }
@@ -357,19 +362,38 @@ __device__ __forceinline__ void tile_pass_f32x2(const float* tx, const float* ty
                                                 const float2 e2, const float2 s2, const float r2c,
                                                 const float4* __restrict__ lo, float2 (&ax)[R], float2 (&ay)[R],
                                                 float2 (&az)[R], float2 (&pp)[R]) {
+  static_assert(kSub <= 32, "one near-mask bit per j-body of a sub-block");
   const int nj4 = (nj + 3) & ~3;  // the tile is padded to a multiple of four
   for (int jb = 0; jb < nj4; jb += kSub) {
     const int nb = min(kSub, nj4 - jb);
     float mn0 = 3.0e38f, mn1 = 3.0e38f;
+    unsigned near[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) near[r] = 0u;
     if (nb == kSub) {
 #pragma unroll(kQuadUnroll)
       for (int j = jb; j < jb + kSub; j += 4)
-        quad_f32x2<LAW, R, MASK>(tx, ty, tz, tm, j, jt + j, ig, nx, ny, nz, e2, s2, ax, ay, az, pp, mn0, mn1);
+        quad_f32x2<LAW, R, MASK>(tx, ty, tz, tm, j, jt + j, ig, nx, ny, nz, e2, s2, ax, ay, az, pp, mn0, mn1, near,
+                                 1u << (j - jb), r2c);
     } else {
       for (int j = jb; j < jb + nb; j += 4)
-        quad_f32x2<LAW, R, MASK>(tx, ty, tz, tm, j, jt + j, ig, nx, ny, nz, e2, s2, ax, ay, az, pp, mn0, mn1);
+        quad_f32x2<LAW, R, MASK>(tx, ty, tz, tm, j, jt + j, ig, nx, ny, nz, e2, s2, ax, ay, az, pp, mn0, mn1, near,
+                                 1u << (j - jb), r2c);
     }
-    if (fminf(mn0, mn1) < r2c) {
+    if (LAW == 1) {
+      // Lennard-Jones: correct exactly the flagged pairs (any lane of the partial will do)
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        unsigned b = near[r];
+        while (b) {
+          const int j = jb + __ffs(b) - 1;
+          b &= b - 1u;
+          if (j < nj)
+            correct_pair<LAW>(make_float4(tx[j], ty[j], tz[j], tm[j]), jt + j, ig[r], i_end, -nx[r].x, -ny[r].x,
+                              -nz[r].x, e2.x, r2c, lo, ax[r].x, ay[r].x, az[r].x, pp[r].x, s2.x);
+        }
+      }
+    } else if (fminf(mn0, mn1) < r2c) {
       // rescan two j-bodies at a time: packed s^2, scalar correction of the near ones
       for (int j = jb; j < jb + nb; j += 2) {
         const float2 xj = *reinterpret_cast<const float2*>(tx + j);
