@@ -156,10 +156,10 @@ nbody_status nbody_virial(nbody_ctx* ctx, const double* x, const double* v, cons
  * Reverse-mode gradient through n_steps KDK steps from (x0, v0) with masses m:
  * given lam_xT = dL/dx_T and lam_vT = dL/dv_T [N,3] (device), writes
  * g_x0 = dL/dx0, g_v0 = dL/dv0 [N,3] and g_m = dL/dm [N]. The forward
- * trajectory is recomputed from checkpoints of (x, v) taken every
- * checkpoint_every steps (1 <= checkpoint_every; device memory
- * ~ (n_steps / checkpoint_every + checkpoint_every) * N * 48 bytes, allocated
- * by the context on first use and kept). Each reverse step applies the
+ * trajectory is recomputed from checkpoints of (x, v, a) taken every
+ * checkpoint_every steps (1 <= checkpoint_every; device memory about
+ * (72 * ceil(n_steps / checkpoint_every) + 24 * (checkpoint_every + 1)) * N
+ * bytes, allocated by the context on first use and kept). Each reverse step applies the
  * vector-Jacobian product of a(x, m),
  *     g_x,k = G sum_{j != k} J(d_kj) (m_k w_j - m_j w_k),  J(d) = I/s^3 - 3 d d^T / s^5
  *     g_m,j = G sum_{i != j} w_i . d_ij / s_ij^3
