@@ -23,6 +23,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -41,7 +42,7 @@ OPS_PER_INTERACTION = 13
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
 L2_FLUSH_BYTES = 256 << 20
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "force_mixed_traffic.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "force_mixed_n65536_full.md")
 FORCE_SRC = os.path.join(ROOT, "paper_2511_02655_gb300", "csrc", "force_kernels.cu")
 
 
@@ -131,11 +132,13 @@ class ClockSampler:
 def traffic_per_launch():
     """DRAM bytes per force launch from the committed ncu summary, if it still matches the source."""
     try:
-        rec = json.load(open(TRAFFIC_FILE))
+        text = open(TRAFFIC_FILE).read()
+        nbytes = re.search(r"DRAM bytes per launch \(.*?\): (\d+)", text)
+        src_sha = re.search(r"Kernel source SHA-256 \(.*?\): ([0-9a-f]{64})", text)
         sha = hashlib.sha256(open(FORCE_SRC, "rb").read()).hexdigest()
-        if rec.get("source_sha256") != sha:
+        if not nbytes or not src_sha or src_sha.group(1) != sha:
             return None
-        return float(rec["dram_bytes_per_launch"])
+        return float(nbytes.group(1))
     except Exception:
         return None
 
