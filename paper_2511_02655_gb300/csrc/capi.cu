@@ -30,7 +30,7 @@ constexpr int kTuneSlice = 8192;
 
 struct Tiling {
   int block = 0, ipt = 0, jtile = 0, slice = 0, n_ctas = 0;
-  int variant = 0;  // force (mixed): 0 scalar, 1 packed float32x2
+  int variant = 0;  // mixed force and VJP kernels: 0 scalar, 1 packed float32x2
 };
 
 // Near-pair refinement radius of the mixed force kernels: 4 softening lengths
