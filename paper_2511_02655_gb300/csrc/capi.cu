@@ -116,6 +116,7 @@ struct nbody_ctx {
 
   // host-memory entry point scratch
   DevBuf hx, hv, hm, ha, hlog;
+  unsigned* h_status = nullptr;  // pinned host word the status is copied into by nbody_sync
 
   // kernel timing (nbody_profile)
   bool profiling = false;
@@ -773,6 +774,7 @@ void free_ctx(nbody_ctx* c) {
   for (DevBuf* b : {&c->stage, &c->stage_lo, &c->stage_w, &c->part, &c->centre, &c->epart, &c->status_counter, &c->a_scratch,
                     &c->xw, &c->vw, &c->aw, &c->ckpt, &c->traj, &c->hx, &c->hv, &c->hm, &c->ha, &c->hlog})
     release(*b);
+  if (c->h_status) cudaFreeHost(c->h_status);
   if (c->d_chunks) cudaFree(c->d_chunks);
   if (c->d_vchunks) cudaFree(c->d_vchunks);
   if (c->d_sys_chunk) cudaFree(c->d_sys_chunk);
@@ -934,6 +936,24 @@ nbody_status adjoint_sweep(nbody_ctx* c, const double* x0, const double* v0, con
   return NBODY_OK;
 }
 
+// Device address of a mapped, page-locked host buffer (cudaHostAlloc /
+// cudaHostRegister under unified addressing), or NULL for any other pointer.
+double* mapped_host(const void* p) {
+  if (!p) return nullptr;
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (at.type != cudaMemoryTypeHost || !at.devicePointer) return nullptr;
+  void* d = nullptr;
+  if (cudaHostGetDevicePointer(&d, const_cast<void*>(p), 0) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return static_cast<double*>(d);
+}
+
 }  // namespace
 
 // ===========================================================================
@@ -1010,11 +1030,17 @@ nbody_status nbody_init(nbody_ctx** out, const nbody_config* cfg, int64_t n_syst
   if (cfg->precision == NBODY_MIXED && (s = ensure(c, c->stage_lo, n * sizeof(float4)))) return bail(s);
   if ((s = ensure(c, c->centre, (size_t)c->n_sys * 3 * sizeof(double)))) return bail(s);
   if ((s = ensure(c, c->epart, std::max<size_t>(1, c->chunks.size()) * kEnergyVals * sizeof(double)))) return bail(s);
-  // [0..1] work counter, [2] status word, [3] unused, [4] energy ticket, [5] centre ticket
+  // [0..1] work counter, [2] status word, [4] energy ticket, [5] centre ticket, [6] adjoint-parameter ticket
   if ((s = ensure(c, c->status_counter, 8 * sizeof(unsigned)))) return bail(s);
   c->counter = static_cast<unsigned*>(c->status_counter.p);
   c->status = c->counter + 2;
   if (cudaMemset(c->status_counter.p, 0, 8 * sizeof(unsigned)) != cudaSuccess) return bail(fail(c, NBODY_ECUDA, "memset failed"));
+  if (cudaHostAlloc(reinterpret_cast<void**>(&c->h_status), sizeof(unsigned), cudaHostAllocDefault) != cudaSuccess) {
+    cudaGetLastError();
+    c->h_status = nullptr;
+    return bail(fail(c, NBODY_ENOMEM, "cudaHostAlloc of the status word failed"));
+  }
+  *c->h_status = 0u;
   if (cudaMemset(c->centre.p, 0, (size_t)c->n_sys * 3 * sizeof(double)) != cudaSuccess)
     return bail(fail(c, NBODY_ECUDA, "memset failed"));
   if (cudaMalloc(&c->d_off, (n_systems + 1) * sizeof(int64_t)) != cudaSuccess ||
@@ -1186,26 +1212,51 @@ nbody_status nbody_step_host(nbody_ctx* c, double* x, double* v, const double* m
     return s;
   if (energy_log && logb && (s = ensure(c, c->hlog, logb))) return s;
   cudaStream_t st = c->stream;
-  NB_CUDA(c, cudaMemcpyAsync(c->hx.p, x, n3b, cudaMemcpyHostToDevice, st));
-  NB_CUDA(c, cudaMemcpyAsync(c->hv.p, v, n3b, cudaMemcpyHostToDevice, st));
-  NB_CUDA(c, cudaMemcpyAsync(c->hm.p, m, n * sizeof(double), cudaMemcpyHostToDevice, st));
-  if (a_valid) NB_CUDA(c, cudaMemcpyAsync(c->ha.p, a, n3b, cudaMemcpyHostToDevice, st));
-  s = nbody_step(c, static_cast<double*>(c->hx.p), static_cast<double*>(c->hv.p),
-                 static_cast<const double*>(c->hm.p), static_cast<double*>(c->ha.p), a_valid, n_steps,
-                 (energy_log && logb) ? static_cast<double*>(c->hlog.p) : nullptr);
+  double* hx = static_cast<double*>(c->hx.p);
+  double* hv = static_cast<double*>(c->hv.p);
+  double* hm = static_cast<double*>(c->hm.p);
+  double* ha = static_cast<double*>(c->ha.p);
+  double* hlog = (energy_log && logb) ? static_cast<double*>(c->hlog.p) : nullptr;
+  // Mapped pinned buffers move in one copy kernel each way, read and written by
+  // the GPU across the host link; any other host memory takes cudaMemcpyAsync.
+  double* mx = mapped_host(x);
+  double* mv = mapped_host(v);
+  double* mm = mapped_host(m);
+  double* ma = mapped_host(a);
+  double* mlog = hlog ? mapped_host(energy_log) : nullptr;
+  const bool zero_copy = mx && mv && mm && ma && (!hlog || mlog);
+  const int64_t n3 = (int64_t)n * 3;
+  if (zero_copy) {
+    const Copy4 in{{mx, mv, mm, a_valid ? ma : nullptr}, {hx, hv, hm, ha}, {n3, n3, (int64_t)n, a_valid ? n3 : 0}};
+    NB_CUDA(c, launch_copy4(in, c->sm_count, st));
+    ++c->launches;
+  } else {
+    NB_CUDA(c, cudaMemcpyAsync(hx, x, n3b, cudaMemcpyHostToDevice, st));
+    NB_CUDA(c, cudaMemcpyAsync(hv, v, n3b, cudaMemcpyHostToDevice, st));
+    NB_CUDA(c, cudaMemcpyAsync(hm, m, n * sizeof(double), cudaMemcpyHostToDevice, st));
+    if (a_valid) NB_CUDA(c, cudaMemcpyAsync(ha, a, n3b, cudaMemcpyHostToDevice, st));
+  }
+  s = nbody_step(c, hx, hv, hm, ha, a_valid, n_steps, hlog);
   if (s) return s;
-  NB_CUDA(c, cudaMemcpyAsync(x, c->hx.p, n3b, cudaMemcpyDeviceToHost, st));
-  NB_CUDA(c, cudaMemcpyAsync(v, c->hv.p, n3b, cudaMemcpyDeviceToHost, st));
-  NB_CUDA(c, cudaMemcpyAsync(a, c->ha.p, n3b, cudaMemcpyDeviceToHost, st));
-  if (energy_log && logb) NB_CUDA(c, cudaMemcpyAsync(energy_log, c->hlog.p, logb, cudaMemcpyDeviceToHost, st));
+  if (zero_copy) {
+    const Copy4 out{{hx, hv, ha, hlog}, {mx, mv, ma, mlog}, {n3, n3, n3, hlog ? (int64_t)(logb / sizeof(double)) : 0}};
+    NB_CUDA(c, launch_copy4(out, c->sm_count, st));
+    ++c->launches;
+  } else {
+    NB_CUDA(c, cudaMemcpyAsync(x, hx, n3b, cudaMemcpyDeviceToHost, st));
+    NB_CUDA(c, cudaMemcpyAsync(v, hv, n3b, cudaMemcpyDeviceToHost, st));
+    NB_CUDA(c, cudaMemcpyAsync(a, ha, n3b, cudaMemcpyDeviceToHost, st));
+    if (hlog) NB_CUDA(c, cudaMemcpyAsync(energy_log, hlog, logb, cudaMemcpyDeviceToHost, st));
+  }
   return nbody_sync(c);
 }
 
 nbody_status nbody_sync(nbody_ctx* c) {
   if (!c) return fail(nullptr, NBODY_EINVAL, "ctx is NULL");
+  // the status word rides on the stream into pinned memory: one wait, no second round trip
+  NB_CUDA(c, cudaMemcpyAsync(c->h_status, c->status, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
   NB_CUDA(c, cudaStreamSynchronize(c->stream));
-  unsigned st = 0;
-  NB_CUDA(c, cudaMemcpy(&st, c->status, sizeof(unsigned), cudaMemcpyDeviceToHost));
+  const unsigned st = *c->h_status;
   if (st) NB_CUDA(c, cudaMemset(c->status, 0, sizeof(unsigned)));
   if (st & kFlagTimeout) return fail(c, NBODY_ETIMEOUT, "a bounded device-side wait gave up");
   if ((st & kFlagNonFinite) && !(c->cfg.flags & NBODY_FLAG_NOCHECK))

@@ -138,6 +138,15 @@ struct AdjLaunch {
 };
 cudaError_t launch_adj_update(const AdjLaunch& A, cudaStream_t st);
 
+// dst[k][0 .. n[k]) = src[k][...] for k = 0..3 in one launch (entries with a
+// null pointer or n = 0 are skipped); grid at most 8 CTAs per SM.
+struct Copy4 {
+  const double* src[4];
+  double* dst[4];
+  int64_t n[4];
+};
+cudaError_t launch_copy4(const Copy4& C, int n_sms, cudaStream_t st);
+
 // stage w = lam (float4 / double4_32a) and/or x for a VJP without an update
 cudaError_t launch_stage_vec(const Chunk* chunks, int n_chunks, int precision, const double* vec, const double* m,
                              const double* centre, void* stage, int as_position, cudaStream_t st);

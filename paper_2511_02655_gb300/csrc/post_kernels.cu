@@ -5,6 +5,8 @@
 // partials never mix systems and every sum has a fixed order.
 #include <math.h>
 
+#include <algorithm>
+
 #include "nbody_internal.h"
 
 namespace nbody {
@@ -328,7 +330,30 @@ __global__ void __launch_bounds__(kPostThreads) k_stage_vec(const Chunk* chunks,
   }
 }
 
+// Up to four plain copies of float64 arrays in one launch (the host-buffer
+// step's transfers through mapped pinned host memory).
+__global__ void __launch_bounds__(256) k_copy4(const Copy4 C) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const double* __restrict__ src = C.src[k];
+    double* __restrict__ dst = C.dst[k];
+    const int64_t n = (src && dst) ? C.n[k] : 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) dst[i] = src[i];
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_copy4(const Copy4& C, int n_sms, cudaStream_t st) {
+  int64_t most = 0;
+  for (int k = 0; k < 4; ++k) most = std::max<int64_t>(most, C.src[k] && C.dst[k] ? C.n[k] : 0);
+  if (most == 0) return cudaSuccess;
+  const int64_t want = (most + 255) / 256;
+  const int grid = (int)std::min<int64_t>(want, (int64_t)std::max(1, n_sms) * 8);
+  k_copy4<<<grid, 256, 0, st>>>(C);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_post(const PostLaunch& P, cudaStream_t st) {
   if (P.n_chunks <= 0) return cudaSuccess;

@@ -207,20 +207,30 @@ def test_host_pointers_rejected_without_launch(nb):
     nb.nbody_sync(ctx)
 
 
-def test_step_host_matches_device_path(nb):
+@pytest.mark.parametrize("memory", ["pinned", "pinned_state_pageable_log", "pageable"])
+def test_step_host_matches_device_path(nb, memory):
+    """nbody_step_host moves mapped pinned buffers with one copy kernel each way and any
+    other host memory with cudaMemcpyAsync; both give the device path's results bit for bit."""
     import torch
-    x, v, m = inputs.plummer(2048, seed=12)
-    ctx = nb.nbody_init(G=1.0, eps=0.01, dt=1e-3, precision=nb.MIXED, n=2048, energy_every=2)
+    n = 2049  # odd: the copy kernel's ragged end
+    x, v, m = inputs.plummer(n, seed=12)
+    ctx = nb.nbody_init(G=1.0, eps=0.01, dt=1e-3, precision=nb.MIXED, n=n, energy_every=2)
     xt, vt, mt = to_dev(x, v, m)
     at = torch.empty_like(xt)
     log = nb.nbody_step(ctx, xt, vt, mt, at, False, 4)
+    log2 = nb.nbody_step(ctx, xt, vt, mt, at, True, 4)
     nb.nbody_sync(ctx)
-    xh, vh = torch.from_numpy(x.copy()).pin_memory(), torch.from_numpy(v.copy()).pin_memory()
-    mh, ah = torch.from_numpy(m.copy()).pin_memory(), torch.zeros((2048, 3), dtype=torch.float64).pin_memory()
+    pin = (lambda t: t.pin_memory()) if memory != "pageable" else (lambda t: t)
+    xh, vh = pin(torch.from_numpy(x.copy())), pin(torch.from_numpy(v.copy()))
+    mh, ah = pin(torch.from_numpy(m.copy())), pin(torch.zeros((n, 3), dtype=torch.float64))
     logh = torch.zeros((2, 1, 9), dtype=torch.float64)
+    if memory == "pinned":
+        logh = logh.pin_memory()
     nb.nbody_step_host(ctx, xh, vh, mh, ah, False, 4, logh)
-    assert torch.equal(xh, xt.cpu()) and torch.equal(vh, vt.cpu()) and torch.equal(ah, at.cpu())
     assert torch.equal(logh, log.cpu())
+    nb.nbody_step_host(ctx, xh, vh, mh, ah, True, 4, logh)  # a passed in from the host
+    assert torch.equal(xh, xt.cpu()) and torch.equal(vh, vt.cpu()) and torch.equal(ah, at.cpu())
+    assert torch.equal(logh, log2.cpu())
 
 
 def test_graph_replay_matches_eager(nb):
