@@ -189,10 +189,12 @@ nbody_status nbody_adjoint_params(nbody_ctx* ctx, const double* x0, const double
 
 /*
  * Host-memory variant of nbody_step: x, v, a (in/out), m (in) and energy_log
- * (out, nullable) are HOST pointers (pinned memory gives asynchronous copies).
- * The context copies them to its own device buffers, runs nbody_step, copies
- * x, v, a and the energy records back, and synchronises the stream before
- * returning.
+ * (out, nullable) are HOST pointers. The context copies them to its own device
+ * buffers, runs nbody_step, copies x, v, a and the energy records back, and
+ * synchronises the stream before returning. When every buffer is mapped
+ * page-locked memory (cudaHostAlloc / cudaHostRegister, e.g. torch pinned
+ * tensors) one copy kernel moves the inputs and one the results across the
+ * host link; otherwise cudaMemcpyAsync is used.
  */
 nbody_status nbody_step_host(nbody_ctx* ctx, double* x, double* v, const double* m, double* a, int32_t a_valid,
                              int32_t n_steps, double* energy_log);
