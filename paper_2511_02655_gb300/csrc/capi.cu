@@ -374,7 +374,7 @@ nbody_status install_tiling(nbody_ctx* c, Tiling t, bool vjp) {
 }
 
 // refine: the mixed force kernel may use the staged remainders (near pairs).
-PairLaunch pair_launch(nbody_ctx* c, bool vjp, bool refine = false) {
+PairLaunch pair_launch(nbody_ctx* c, bool vjp, bool refine = false, bool phi = true) {
   PairLaunch L{};
   const bool lo = refine && !vjp && c->cfg.precision == NBODY_MIXED && c->stage_lo.p;
   L.stage_lo = lo ? static_cast<const float4*>(c->stage_lo.p) : nullptr;
@@ -397,6 +397,7 @@ PairLaunch pair_launch(nbody_ctx* c, bool vjp, bool refine = false) {
   L.block = t.block, L.ipt = t.ipt, L.jtile = t.jtile, L.n_ctas = t.n_ctas;
   L.variant = t.variant;
   L.params = vjp && c->vjp_params ? 1 : 0;
+  L.phi = phi ? 1 : 0;
   return L;
 }
 
@@ -416,9 +417,9 @@ cudaEvent_t pooled_event(nbody_ctx* c) {
 
 // Launches an all-pairs kernel, bracketed by an event pair when profiling an
 // eager (non-capturing) stream.
-nbody_status run_pair(nbody_ctx* c, cudaStream_t st, bool vjp) {
+nbody_status run_pair(nbody_ctx* c, cudaStream_t st, bool vjp, bool phi = true) {
   if (c->n_total == 0) return NBODY_OK;
-  PairLaunch L = pair_launch(c, vjp, !vjp);
+  PairLaunch L = pair_launch(c, vjp, !vjp, phi);
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (c->profiling && !c->capturing) {
     e0 = pooled_event(c);
@@ -434,7 +435,9 @@ nbody_status run_pair(nbody_ctx* c, cudaStream_t st, bool vjp) {
   return NBODY_OK;
 }
 
-nbody_status run_force(nbody_ctx* c, cudaStream_t st) { return run_pair(c, st, false); }
+// phi: whether the potential is needed (an energy record, a phi output); only
+// the packed mixed kernel can skip it, the others always form it.
+nbody_status run_force(nbody_ctx* c, cudaStream_t st, bool phi) { return run_pair(c, st, false, phi); }
 nbody_status run_vjp(nbody_ctx* c, cudaStream_t st) { return run_pair(c, st, true); }
 
 PostLaunch post_launch(nbody_ctx* c, unsigned mode, double* x, double* v, const double* m, double* a, double* phi) {
@@ -488,7 +491,7 @@ nbody_status enqueue_step(nbody_ctx* c, double* x, double* v, const double* m, d
   if ((s = run_centre(c, x, m, st))) return s;
   if (!a_valid) {
     if ((s = run_post(c, post_launch(c, kStage, x, v, m, a, nullptr), st))) return s;
-    if ((s = run_force(c, st))) return s;
+    if ((s = run_force(c, st, false))) return s;
     if ((s = run_post(c, post_launch(c, kCombine, x, v, m, a, nullptr), st))) return s;
   }
   if (n_steps == 0) return NBODY_OK;
@@ -496,8 +499,8 @@ nbody_status enqueue_step(nbody_ctx* c, double* x, double* v, const double* m, d
   const int every = c->cfg.energy_every;
   int rec = 0;
   for (int k = 0; k < n_steps; ++k) {
-    if ((s = run_force(c, st))) return s;
     const bool rec_now = elog && every > 0 && (k + 1) % every == 0;
+    if ((s = run_force(c, st, rec_now))) return s;
     unsigned mode = kCombine | kKickEnd;
     if (rec_now) mode |= kEnergy;
     if (k + 1 < n_steps) mode |= kDrift | kStage;
@@ -855,7 +858,7 @@ nbody_status adjoint_sweep(nbody_ctx* c, const double* x0, const double* v0, con
   NB_CUDA(c, cudaMemcpyAsync(xw, x0, n3b, cudaMemcpyDeviceToDevice, st));
   NB_CUDA(c, cudaMemcpyAsync(vw, v0, n3b, cudaMemcpyDeviceToDevice, st));
   if ((s = run_post(c, post_launch(c, kStage, xw, vw, m, aw, nullptr), st))) return s;
-  if ((s = run_force(c, st))) return s;
+  if ((s = run_force(c, st, false))) return s;
   if ((s = run_post(c, post_launch(c, kCombine, xw, vw, m, aw, nullptr), st))) return s;
 
   // one KDK step on (xw, vw, aw), optionally copying x after the drift
@@ -864,7 +867,7 @@ nbody_status adjoint_sweep(nbody_ctx* c, const double* x0, const double* v0, con
     PostLaunch P = post_launch(c, kDrift | kStage, xw, vw, m, aw, nullptr);
     P.x_copy = xcopy;
     if ((r = run_post(c, P, st))) return r;
-    if ((r = run_force(c, st))) return r;
+    if ((r = run_force(c, st, false))) return r;
     return run_post(c, post_launch(c, kCombine | kKickEnd, xw, vw, m, aw, nullptr), st);
   };
 
@@ -1085,7 +1088,7 @@ nbody_status nbody_forces(nbody_ctx* c, const double* x, const double* m, double
   double* xm = const_cast<double*>(x);
   if ((s = run_centre(c, x, m, c->stream))) return s;
   if ((s = run_post(c, post_launch(c, kStage, xm, nullptr, m, a, nullptr), c->stream))) return s;
-  if ((s = run_force(c, c->stream))) return s;
+  if ((s = run_force(c, c->stream, phi != nullptr))) return s;
   return run_post(c, post_launch(c, kCombine, xm, nullptr, m, a, phi), c->stream);
 }
 
@@ -1155,7 +1158,7 @@ nbody_status nbody_energy(nbody_ctx* c, const double* x, const double* v, const 
   double* as = static_cast<double*>(c->a_scratch.p);
   if ((s = run_centre(c, x, m, c->stream))) return s;
   if ((s = run_post(c, post_launch(c, kStage, xm, vm, m, as, nullptr), c->stream))) return s;
-  if ((s = run_force(c, c->stream))) return s;
+  if ((s = run_force(c, c->stream, true))) return s;
   // the last CTA writes every system's record (systems without bodies get zeros)
   PostLaunch P = post_launch(c, kCombine | kEnergy, xm, vm, m, as, nullptr);
   P.eout = out;
@@ -1177,7 +1180,7 @@ nbody_status nbody_virial(nbody_ctx* c, const double* x, const double* v, const 
   double* as = static_cast<double*>(c->a_scratch.p);
   if ((s = run_centre(c, x, m, c->stream))) return s;
   if ((s = run_post(c, post_launch(c, kStage, xm, vm, m, as, nullptr), c->stream))) return s;
-  if ((s = run_force(c, c->stream))) return s;
+  if ((s = run_force(c, c->stream, false))) return s;
   PostLaunch P = post_launch(c, kCombine | kVirial, xm, vm, m, as, nullptr);
   P.vout = out;
   return run_post(c, P, c->stream);

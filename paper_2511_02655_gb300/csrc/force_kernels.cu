@@ -19,6 +19,8 @@
 // partial (sum m d / s^3, sum m / s) per i-body to its slice; the O(N) post
 // kernel adds the slices in a fixed order, so results are deterministic.
 // Self pairs are masked in the tiles that overlap the item's own i-range.
+#include <algorithm>
+
 #include "nbody_internal.h"
 #include "pair_common.cuh"
 
@@ -264,7 +266,7 @@ __global__ void __launch_bounds__(BLOCK) k_force_mixed(const PairLaunch L) {
 
 constexpr float kFarAway = 1.0e18f;
 
-template <bool MASK>
+template <bool MASK, bool PHI>
 __device__ __forceinline__ void pair2_f32x2(const float2 xj, const float2 yj, const float2 zj, const float2 mj,
                                             const int jg0, const int ig, const float2 nx, const float2 ny,
                                             const float2 nz, const float2 e2, float2& ax, float2& ay, float2& az,
@@ -285,7 +287,7 @@ __device__ __forceinline__ void pair2_f32x2(const float2 xj, const float2 yj, co
   ax = __ffma2_rn(dx, w, ax);
   ay = __ffma2_rn(dy, w, ay);
   az = __ffma2_rn(dz, w, az);
-  pp = __fadd2_rn(pp, ms);
+  if (PHI) pp = __fadd2_rn(pp, ms);
 }
 
 // Lennard-Jones pair (Eq. 1) on two j-bodies: with u = sigma^2 / r^2,
@@ -296,7 +298,7 @@ __device__ __forceinline__ void pair2_f32x2(const float2 xj, const float2 yj, co
 // refinement radius per particle), so instead of a running minimum each pair
 // sets its bit in the sub-block's near mask (bit0 for the first j-body, the
 // next bit for the second) and the second look visits exactly those pairs.
-template <bool MASK>
+template <bool MASK, bool PHI>
 __device__ __forceinline__ void pair2_lj_f32x2(const float2 xj, const float2 yj, const float2 zj, const int jg0,
                                                const int ig, const float2 nx, const float2 ny, const float2 nz,
                                                const float2 e2, const float2 s2, float2& ax, float2& ay, float2& az,
@@ -319,11 +321,11 @@ __device__ __forceinline__ void pair2_lj_f32x2(const float2 xj, const float2 yj,
   ax = __ffma2_rn(dx, w, ax);
   ay = __ffma2_rn(dy, w, ay);
   az = __ffma2_rn(dz, w, az);
-  pp = __fadd2_rn(pp, __ffma2_rn(u3, make_float2(-1.f, -1.f), u6));
+  if (PHI) pp = __fadd2_rn(pp, __ffma2_rn(u3, make_float2(-1.f, -1.f), u6));
 }
 
 // Four j-bodies (tile entries j..j+3) against the thread's R i-bodies.
-template <int LAW, int R, bool MASK>
+template <int LAW, int R, bool MASK, bool PHI>
 __device__ __forceinline__ void quad_f32x2(const float* tx, const float* ty, const float* tz, const float* tm,
                                            const int j, const int jg, const int (&ig)[R], const float2 (&nx)[R],
                                            const float2 (&ny)[R], const float2 (&nz)[R], const float2 e2,
@@ -337,25 +339,25 @@ __device__ __forceinline__ void quad_f32x2(const float* tx, const float* ty, con
     const float4 M = *reinterpret_cast<const float4*>(tm + j);
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-      pair2_f32x2<MASK>(make_float2(X.x, X.y), make_float2(Y.x, Y.y), make_float2(Z.x, Z.y),
+      pair2_f32x2<MASK, PHI>(make_float2(X.x, X.y), make_float2(Y.x, Y.y), make_float2(Z.x, Z.y),
                         make_float2(M.x, M.y), jg, ig[r], nx[r], ny[r], nz[r], e2, ax[r], ay[r], az[r], pp[r], mn0,
                         mn1);
-      pair2_f32x2<MASK>(make_float2(X.z, X.w), make_float2(Y.z, Y.w), make_float2(Z.z, Z.w),
+      pair2_f32x2<MASK, PHI>(make_float2(X.z, X.w), make_float2(Y.z, Y.w), make_float2(Z.z, Z.w),
                         make_float2(M.z, M.w), jg + 2, ig[r], nx[r], ny[r], nz[r], e2, ax[r], ay[r], az[r], pp[r],
                         mn0, mn1);
     }
   } else {
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-      pair2_lj_f32x2<MASK>(make_float2(X.x, X.y), make_float2(Y.x, Y.y), make_float2(Z.x, Z.y), jg, ig[r], nx[r],
+      pair2_lj_f32x2<MASK, PHI>(make_float2(X.x, X.y), make_float2(Y.x, Y.y), make_float2(Z.x, Z.y), jg, ig[r], nx[r],
                            ny[r], nz[r], e2, s2, ax[r], ay[r], az[r], pp[r], near[r], qbit, r2c);
-      pair2_lj_f32x2<MASK>(make_float2(X.z, X.w), make_float2(Y.z, Y.w), make_float2(Z.z, Z.w), jg + 2, ig[r],
+      pair2_lj_f32x2<MASK, PHI>(make_float2(X.z, X.w), make_float2(Y.z, Y.w), make_float2(Z.z, Z.w), jg + 2, ig[r],
                            nx[r], ny[r], nz[r], e2, s2, ax[r], ay[r], az[r], pp[r], near[r], qbit << 2, r2c);
     }
   }
 }
 
-template <int LAW, int R, bool MASK>
+template <int LAW, int R, bool MASK, bool PHI>
 __device__ __forceinline__ void tile_pass_f32x2(const float* tx, const float* ty, const float* tz, const float* tm,
                                                 const int jt, const int nj, const int (&ig)[R], const float2 (&nx)[R],
                                                 const float2 (&ny)[R], const float2 (&nz)[R], const int i_end,
@@ -373,11 +375,11 @@ __device__ __forceinline__ void tile_pass_f32x2(const float* tx, const float* ty
     if (nb == kSub) {
 #pragma unroll(kQuadUnroll)
       for (int j = jb; j < jb + kSub; j += 4)
-        quad_f32x2<LAW, R, MASK>(tx, ty, tz, tm, j, jt + j, ig, nx, ny, nz, e2, s2, ax, ay, az, pp, mn0, mn1, near,
+        quad_f32x2<LAW, R, MASK, PHI>(tx, ty, tz, tm, j, jt + j, ig, nx, ny, nz, e2, s2, ax, ay, az, pp, mn0, mn1, near,
                                  1u << (j - jb), r2c);
     } else {
       for (int j = jb; j < jb + nb; j += 4)
-        quad_f32x2<LAW, R, MASK>(tx, ty, tz, tm, j, jt + j, ig, nx, ny, nz, e2, s2, ax, ay, az, pp, mn0, mn1, near,
+        quad_f32x2<LAW, R, MASK, PHI>(tx, ty, tz, tm, j, jt + j, ig, nx, ny, nz, e2, s2, ax, ay, az, pp, mn0, mn1, near,
                                  1u << (j - jb), r2c);
     }
     if (LAW == 1) {
@@ -418,7 +420,10 @@ __device__ __forceinline__ void tile_pass_f32x2(const float* tx, const float* ty
   }
 }
 
-template <int LAW, int BLOCK, int R, int J>
+// PHI = false skips the potential (one packed operation per pair of interactions
+// for gravity, two for Lennard-Jones) when no caller needs it; the partials'
+// fourth component is then 0.
+template <int LAW, int BLOCK, int R, int J, bool PHI>
 __global__ void __launch_bounds__(BLOCK, (NBODY_MIN_CTAS > 0 ? NBODY_MIN_CTAS : 1)) k_force_mixed2(const PairLaunch L) {
   static_assert(J % 4 == 0, "tiles hold whole quads of j-bodies");
   constexpr int LPT = (J + BLOCK - 1) / BLOCK;
@@ -488,10 +493,10 @@ __global__ void __launch_bounds__(BLOCK, (NBODY_MIN_CTAS > 0 ? NBODY_MIN_CTAS : 
       for (int r = 0; r < R; ++r) ax[r] = ay[r] = az[r] = pp[r] = make_float2(0.f, 0.f);
       const bool diag = (jt < w.i_end) && (w.i_begin < jt + nj);
       if (diag)
-        tile_pass_f32x2<LAW, R, true>(tx[buf], ty[buf], tz[buf], tm[buf], jt, nj, ig, nx, ny, nz, w.i_end, e2, s2,
+        tile_pass_f32x2<LAW, R, true, PHI>(tx[buf], ty[buf], tz[buf], tm[buf], jt, nj, ig, nx, ny, nz, w.i_end, e2, s2,
                                       r2c, lo, ax, ay, az, pp);
       else
-        tile_pass_f32x2<LAW, R, false>(tx[buf], ty[buf], tz[buf], tm[buf], jt, nj, ig, nx, ny, nz, w.i_end, e2, s2,
+        tile_pass_f32x2<LAW, R, false, PHI>(tx[buf], ty[buf], tz[buf], tm[buf], jt, nj, ig, nx, ny, nz, w.i_end, e2, s2,
                                        r2c, lo, ax, ay, az, pp);
 #pragma unroll
       for (int r = 0; r < R; ++r) {
@@ -521,7 +526,7 @@ __global__ void __launch_bounds__(BLOCK, (NBODY_MIN_CTAS > 0 ? NBODY_MIN_CTAS : 
     for (int r = 0; r < R; ++r) {
       if (ig[r] < w.i_end)
         out[ig[r]] = make_double4_32a((double)hx[r] + (double)lx[r], (double)hy[r] + (double)ly[r],
-                                      (double)hz[r] + (double)lz[r], (double)hp[r] + (double)lp[r]);
+                                      (double)hz[r] + (double)lz[r], PHI ? (double)hp[r] + (double)lp[r] : 0.0);
     }
   }
   retire_cta(L.counter);
@@ -657,7 +662,10 @@ cudaError_t launch_force(int precision, const PairLaunch& L, cudaStream_t st) {
   if (L.law == 1) {
 #define NBODY_X(B, R, J)                                               \
   if (L.block == B && L.ipt == R && L.jtile == J) {                    \
-    k_force_mixed2<1, B, R, J><<<L.n_ctas, B, 0, st>>>(L);             \
+    if (L.phi)                                                         \
+      k_force_mixed2<1, B, R, J, true><<<L.n_ctas, B, 0, st>>>(L);     \
+    else                                                               \
+      k_force_mixed2<1, B, R, J, false><<<L.n_ctas, B, 0, st>>>(L);    \
     return cudaGetLastError();                                         \
   }
     if (precision == 1) {
@@ -680,8 +688,10 @@ cudaError_t launch_force(int precision, const PairLaunch& L, cudaStream_t st) {
   if (precision == 1) {
 #define NBODY_X(B, R, J)                                               \
   if (L.block == B && L.ipt == R && L.jtile == J) {                    \
-    if (L.variant == 1)                                                \
-      k_force_mixed2<0, B, R, J><<<L.n_ctas, B, 0, st>>>(L);           \
+    if (L.variant == 1 && L.phi)                                       \
+      k_force_mixed2<0, B, R, J, true><<<L.n_ctas, B, 0, st>>>(L);     \
+    else if (L.variant == 1)                                           \
+      k_force_mixed2<0, B, R, J, false><<<L.n_ctas, B, 0, st>>>(L);    \
     else                                                               \
       k_force_mixed<B, R, J><<<L.n_ctas, B, 0, st>>>(L);               \
     return cudaGetLastError();                                         \
@@ -707,7 +717,8 @@ int force_ctas_per_sm(int precision, int variant, int block, int ipt, int jtile,
     if (precision == 1) {
       if (variant != 1) return 0;
 #define NBODY_X(B, R, J) \
-  if (block == B && ipt == R && jtile == J) return occupancy_of(k_force_mixed2<1, B, R, J>, B);
+  if (block == B && ipt == R && jtile == J)                                                          \
+    return std::min(occupancy_of(k_force_mixed2<1, B, R, J, true>, B), occupancy_of(k_force_mixed2<1, B, R, J, false>, B));
       NBODY_LJ_MIXED_TILINGS(NBODY_X)
 #undef NBODY_X
       return 0;
@@ -724,7 +735,9 @@ int force_ctas_per_sm(int precision, int variant, int block, int ipt, int jtile,
     if (variant != 0 && variant != 1) return 0;
 #define NBODY_X(B, R, J)                                                                             \
   if (block == B && ipt == R && jtile == J)                                                          \
-    return variant == 1 ? occupancy_of(k_force_mixed2<0, B, R, J>, B) : occupancy_of(k_force_mixed<B, R, J>, B);
+    return variant == 1 ? std::min(occupancy_of(k_force_mixed2<0, B, R, J, true>, B),                  \
+                                   occupancy_of(k_force_mixed2<0, B, R, J, false>, B))                 \
+                        : occupancy_of(k_force_mixed<B, R, J>, B);
     NBODY_MIXED_TILINGS(NBODY_X)
 #undef NBODY_X
     return 0;

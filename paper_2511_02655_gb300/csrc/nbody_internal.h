@@ -54,6 +54,7 @@ struct PairLaunch {
   int block, ipt, jtile; // tiling
   int n_ctas;            // persistent grid size
   int params;            // VJP: also the sums for the G and eps gradients (third double4)
+  int phi;               // force (mixed packed): accumulate the potential (0: skip it, partial .w = 0)
 };
 
 // Returns cudaErrorInvalidConfiguration for an unsupported tiling.

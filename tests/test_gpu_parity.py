@@ -357,3 +357,31 @@ def test_ring_schedule_passes_agree(nb, prec):
             assert np.median(e) <= MIX_MED and e.max() <= MIX_MAX
     for a in res[1:]:
         assert force_rel_err(a, res[0]).max() <= (1e-13 if prec == nb.FP64 else 1e-5)
+
+
+@pytest.mark.parametrize("law", ["gravity", "lj"])
+def test_potential_free_pass_matches(nb, law):
+    """Without a phi output or an energy record the packed kernel skips the potential; the
+    accelerations and trajectories are bit-identical to the passes that form it."""
+    import torch
+    if law == "gravity":
+        x, v, m = inputs.plummer(3001, seed=31)
+        kw = dict(G=1.0, eps=0.01, dt=1e-3)
+    else:
+        x, v, m, box = inputs.lj_gas(3001, seed=32, density=0.1)
+        kw = dict(law=nb.LENNARD_JONES, dt=5e-3, box=box)
+    til = dict(variant=2, block=128, i_per_thread=2, j_tile=256, slice=1024)
+    xt, vt, mt = to_dev(x, v, m)
+    runs = []
+    for every in (1, 0):  # energy record every step (potential formed) / none (skipped)
+        ctx = nb.nbody_init(precision=nb.MIXED, n=len(m), energy_every=every, **til, **kw)
+        a1, phi = nb.nbody_forces(ctx, xt, mt)
+        a0, none = nb.nbody_forces(ctx, xt, mt, with_phi=False)
+        assert none is None and torch.equal(a0, a1)
+        xs, vs, at = xt.clone(), vt.clone(), torch.empty_like(xt)
+        nb.nbody_step(ctx, xs, vs, mt, at, False, 6)
+        nb.nbody_sync(ctx)
+        runs.append((a1, xs, vs, at))
+        ctx.close()
+    for p, q in zip(*runs):
+        assert torch.equal(p, q)
