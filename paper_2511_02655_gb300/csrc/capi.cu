@@ -104,6 +104,7 @@ struct nbody_ctx {
   int n_vitems = 0;
   int vmax_slices = 1;
   bool vjp_ready = false;
+  int64_t fault_alloc = 0;  // > 0: the fault_alloc-th scratch allocation fails (NBODY_FAULT_ALLOC, tests)
   bool vjp_params = false;  // VJP launches also form the G and eps gradient sums
 
   // scratch
@@ -174,6 +175,8 @@ nbody_status ensure(nbody_ctx* c, DevBuf& b, size_t bytes) {
     b.bytes = 0;
   }
   if (bytes == 0) bytes = 16;
+  if (c->fault_alloc > 0 && --c->fault_alloc == 0)
+    return fail(c, NBODY_ENOMEM, "injected allocation failure (NBODY_FAULT_ALLOC) for %zu bytes", bytes);
   cudaError_t e = cudaMalloc(&b.p, bytes);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -1007,6 +1010,9 @@ nbody_status nbody_init(nbody_ctx** out, const nbody_config* cfg, int64_t n_syst
   c->cfg = *cfg;
   c->device = dev;
   c->sm_count = prop.multiProcessorCount;
+  // host-side fault injection for tests: NBODY_FAULT_ALLOC=k makes the k-th scratch
+  // allocation of this context report NBODY_ENOMEM (no device fault is involved)
+  if (const char* fa = getenv("NBODY_FAULT_ALLOC")) c->fault_alloc = std::max<int64_t>(0, atoll(fa));
   c->stream = static_cast<cudaStream_t>(cuda_stream);
   c->n_sys = (int)n_systems;
   c->offsets.assign(offsets, offsets + n_systems + 1);
