@@ -103,6 +103,12 @@ typedef struct {
  * times candidate tilings of the force kernel on synthetic positions of this
  * layout during init (this synchronises the device). The context keeps a copy
  * of *cfg. On failure *ctx is NULL.
+ *
+ * Environment: NBODY_TUNE_CACHE=<file> keeps the tuner's choices (force and
+ * VJP) across runs, keyed by device, configuration and layout;
+ * NBODY_TUNE_VERBOSE=1 prints the candidates' costs on stderr;
+ * NBODY_FAULT_ALLOC=k makes the k-th scratch allocation of the context report
+ * NBODY_ENOMEM (for testing failure paths).
  */
 nbody_status nbody_init(nbody_ctx** ctx, const nbody_config* cfg, int64_t n_systems, const int64_t* offsets,
                         void* cuda_stream);

@@ -77,6 +77,8 @@ struct nbody_ctx {
   nbody_config cfg{};
   int device = 0;
   int sm_count = 0;
+  std::string dev_name;  // cudaDeviceProp::name, part of the tuning-cache key
+  int dev_cc = 0;
   cudaStream_t stream = nullptr;
   cudaStream_t cap_stream = nullptr;  // private stream used only to capture graphs
   int64_t n_total = 0;
@@ -654,7 +656,69 @@ nbody_status time_tiling(nbody_ctx* c, bool vjp, double* cost) {
   return NBODY_OK;
 }
 
+// ---------------------------------------------------------------------------
+// tuning cache: NBODY_TUNE_CACHE=<file> keeps the tuner's choices across runs.
+// One line per choice, "<key>\t<block> <ipt> <jtile> <slice> <variant>"; the key
+// holds the device, the kernel (force or VJP), every configuration field the
+// choice depends on and a hash of the system layout, so an entry is reused only
+// for the same setup. A cached tiling that no longer installs is re-tuned.
+
+std::string tune_key(const nbody_ctx* c, bool vjp) {
+  const nbody_config& g = c->cfg;
+  uint64_t h = 1469598103934665603ull;  // FNV-1a over the offsets
+  for (int s = 0; s <= c->n_sys; ++s) {
+    uint64_t v = (uint64_t)c->offsets[s];
+    for (int k = 0; k < 8; ++k, v >>= 8) h = (h ^ (v & 0xff)) * 1099511628211ull;
+  }
+  char buf[512];
+  snprintf(buf, sizeof(buf),
+           "v1|%s|cc%d|sm%d|%s|prec%d|law%d|var%d|b%d|r%d|j%d|s%d|nsys%d|n%lld|lay%016llx|eps%.17g|sig%.17g|box%.17g",
+           c->dev_name.c_str(), c->dev_cc, c->sm_count, vjp ? "vjp" : "force", g.precision, g.law, g.variant,
+           vjp ? 0 : g.block, vjp ? 0 : g.i_per_thread, vjp ? 0 : g.j_tile, vjp ? 0 : g.slice, c->n_sys,
+           (long long)c->n_total, (unsigned long long)h, g.eps, g.lj_sigma, g.box);
+  for (char* p = buf; *p; ++p)
+    if (*p == '\t' || *p == '\n') *p = ' ';
+  return buf;
+}
+
+bool tune_cache_lookup(const nbody_ctx* c, bool vjp, Tiling* t) {
+  const char* path = getenv("NBODY_TUNE_CACHE");
+  if (!path || !*path) return false;
+  FILE* f = fopen(path, "r");
+  if (!f) return false;
+  const std::string key = tune_key(c, vjp);
+  bool found = false;
+  char line[1024];
+  while (fgets(line, sizeof(line), f)) {
+    char* tab = strchr(line, '\t');
+    if (!tab) continue;
+    *tab = '\0';
+    if (key != line) continue;
+    Tiling u;
+    if (sscanf(tab + 1, "%d %d %d %d %d", &u.block, &u.ipt, &u.jtile, &u.slice, &u.variant) == 5) *t = u, found = true;
+  }
+  fclose(f);
+  return found;
+}
+
+void tune_cache_store(const nbody_ctx* c, bool vjp, const Tiling& t) {
+  const char* path = getenv("NBODY_TUNE_CACHE");
+  if (!path || !*path) return;
+  FILE* f = fopen(path, "a");
+  if (!f) return;
+  fprintf(f, "%s\t%d %d %d %d %d\n", tune_key(c, vjp).c_str(), t.block, t.ipt, t.jtile, t.slice, t.variant);
+  fclose(f);
+}
+
 nbody_status autotune(nbody_ctx* c, bool vjp) {
+  {
+    Tiling t;
+    if (tune_cache_lookup(c, vjp, &t)) {
+      t.n_ctas = 0;
+      if (install_tiling(c, t, vjp) == NBODY_OK) return NBODY_OK;
+      cudaGetLastError();
+    }
+  }
   const nbody_config& g = c->cfg;
   std::vector<Tiling> cands;
   const int blocks[] = {128, 256};
@@ -745,6 +809,8 @@ nbody_status autotune(nbody_ctx* c, bool vjp) {
   // synthetic data must not leave a latched device condition behind
   NB_CUDA(c, cudaStreamSynchronize(c->stream));
   NB_CUDA(c, cudaMemset(c->status, 0, sizeof(unsigned)));
+  Tiling chosen = vjp ? c->vt : c->ft;
+  tune_cache_store(c, vjp, chosen);
   return NBODY_OK;
 }
 
@@ -1010,6 +1076,8 @@ nbody_status nbody_init(nbody_ctx** out, const nbody_config* cfg, int64_t n_syst
   c->cfg = *cfg;
   c->device = dev;
   c->sm_count = prop.multiProcessorCount;
+  c->dev_name = prop.name;
+  c->dev_cc = prop.major * 10 + prop.minor;
   // host-side fault injection for tests: NBODY_FAULT_ALLOC=k makes the k-th scratch
   // allocation of this context report NBODY_ENOMEM (no device fault is involved)
   if (const char* fa = getenv("NBODY_FAULT_ALLOC")) c->fault_alloc = std::max<int64_t>(0, atoll(fa));

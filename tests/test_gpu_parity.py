@@ -385,3 +385,42 @@ def test_potential_free_pass_matches(nb, law):
         ctx.close()
     for p, q in zip(*runs):
         assert torch.equal(p, q)
+
+
+def test_tuning_cache(nb, tmp_path, monkeypatch):
+    """NBODY_TUNE_CACHE keeps the tuner's choices: a second context of the same setup reuses
+    the force and VJP tilings without tuning, another setup gets its own entry, and an entry
+    that no longer installs is re-tuned."""
+    import torch
+    path = tmp_path / "tune.txt"
+    monkeypatch.setenv("NBODY_TUNE_CACHE", str(path))
+    n = 5000
+    x, v, m = inputs.plummer(n, seed=61)
+    xt, vt, mt = to_dev(x, v, m)
+    lam = torch.ones_like(xt)
+
+    def make(eps=0.01):
+        ctx = nb.nbody_init(G=1.0, eps=eps, dt=1e-3, precision=nb.MIXED, n=n)
+        nb.nbody_adjoint(ctx, xt, vt, mt, 2, 1, lam, lam)  # tunes the VJP
+        a, _ = nb.nbody_forces(ctx, xt, mt)
+        nb.nbody_sync(ctx)
+        return ctx, a
+
+    c1, a1 = make()
+    lines = path.read_text().splitlines()
+    assert len(lines) == 2 and "|force|" in lines[0] and "|vjp|" in lines[1]
+    c2, a2 = make()
+    assert path.read_text().splitlines() == lines  # reused, nothing tuned
+    assert nb.nbody_get_tuning(c2) == nb.nbody_get_tuning(c1) and torch.equal(a1, a2)
+    c3, _ = make(eps=0.02)
+    assert len(path.read_text().splitlines()) == 4  # another setup, its own entries
+    # an entry that no longer installs (an uncompiled block size) is ignored and re-tuned
+    key = lines[0].split("\t")[0]
+    with open(path, "a") as f:
+        f.write(f"{key}\t96 2 256 4096 1\n")
+    c4, a4 = make()
+    assert nb.nbody_get_tuning(c4)["block"] in (128, 256)
+    assert torch.equal(a4, a1) or force_rel_err(a4.cpu().numpy(), a1.cpu().numpy()).max() <= 1e-5
+    assert path.read_text().splitlines()[-1].startswith(key)
+    for c in (c1, c2, c3, c4):
+        c.close()
