@@ -1,6 +1,7 @@
 // C ABI of libnbody (include/nbody.h): context, argument validation, work
-// lists, autotuner, the KDK step sequence (with optional CUDA-graph replay),
-// the energy reduction and the checkpointed adjoint driver.
+// lists, autotuner (with its optional cache), the KDK step sequence (with
+// optional CUDA-graph replay), the host-buffer step, the energy and virial
+// reductions and the checkpointed adjoint driver.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>

@@ -1,6 +1,7 @@
-// All-pairs softened-gravity force kernels (the paper's force calculation over
-// "N_p^2 operations", Sec. V-B, with the energy term fused into the same loop,
-// Sec. VI). Two precisions:
+// All-pairs force kernels (the paper's force calculation over "N_p^2
+// operations", Sec. V-B, with the energy term fused into the same loop,
+// Sec. VI) for softened gravity and for the paper's Lennard-Jones law (Eq. 1).
+// Two precisions:
 //
 //   mixed : staged j-bodies are float4 (x - c, y - c, z - c, m) with c the
 //           system's staging origin; each interaction is 3 FADD + 3 FFMA +
@@ -10,7 +11,8 @@
 //   fp64  : staged double4_32a (x, y, z, m), every operation in float64.
 //
 // The mixed path has a scalar kernel and a packed one (two j-bodies per
-// float32x2 instruction); the autotuner picks.
+// float32x2 instruction); the autotuner picks. The packed kernel also comes
+// without the potential term, for passes that need no energy.
 // Both precisions are persistent kernels over a work list of (i-tile, j-slice) items.
 // i-bodies live in registers (R per thread, strided by the CTA size so loads
 // and stores coalesce), j-bodies stream through a shared-memory tile that
@@ -30,11 +32,14 @@ namespace {
 // Near-pair refinement. The float32 staging coordinates carry an absolute
 // rounding error of about |x - c| 2^-24, harmless for distant pairs but
 // dominant for pairs closer than a few softening lengths. Pairs with s^2 below
-// the refinement radius get d recomputed with the staged remainders (below). Such pairs are rare, so they are found without a branch per
+// the refinement radius get d recomputed with the staged remainders (below).
+// For gravity such pairs are rare, so they are found without a branch per
 // pair: every pair folds its s^2 into a running minimum (one FMNMX), and after
 // each sub-block of kSub j-bodies a thread whose minimum fell below the radius
 // rescans that sub-block (s^2 only) and, for each near pair, adds the refined
-// contribution minus the unrefined one it accumulated in the first pass.
+// contribution minus the unrefined one it accumulated in the first pass. The
+// Lennard-Jones kernel marks near pairs in a bit mask instead (see there).
+//
 // Compile-time tuning of the mixed kernels. The defaults won a sweep on GB300
 // (Plummer N = 65 536 and two spheres N = 1 048 576): 32-body sub-blocks were
 // 2-5% faster than 16 or 8; unroll depth 2 vs 4 within 1%; requesting a minimum

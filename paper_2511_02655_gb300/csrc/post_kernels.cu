@@ -1,7 +1,8 @@
 // O(N) kernels around the all-pairs passes: staging, slice combination, the
 // leapfrog kicks and drift (Verlet half-stepping, Sec. II-A), the fixed-order
-// float64 reductions of energy and momenta (Sec. VI), and the reverse-sweep
-// update of the adjoint. One CTA handles one chunk of one system, so chunk
+// float64 reductions of energy and momenta (Sec. VI) and of the virial, the
+// reverse-sweep update of the adjoint (with its G and eps sums), and the copy
+// kernel of the host-buffer step. One CTA handles one chunk of one system, so chunk
 // partials never mix systems and every sum has a fixed order.
 #include <math.h>
 
