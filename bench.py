@@ -428,22 +428,33 @@ def run_ours(args):
     fp64_value = interactions * k64 / (e0.elapsed_time(e1) * 1e-3)
     ctx64.close()
 
-    # ---- end to end through the host-memory entry point (pinned buffers, copies inside the timing)
+    # ---- end to end through the host-memory entry point (pinned buffers, copies inside the timing):
+    # a context with the same tiling that replays its step as a CUDA graph; L2 flushed between
+    # steps outside the timing, each call timed on the host clock (it returns after its sync)
     ke = max(3, min(K, 50))
+    ctx_h = nb.nbody_init(G=G, eps=eps, dt=dt, precision=nb.MIXED, n=n, energy_every=1, flags=nb.FLAG_GRAPH,
+                          block=tuning["block"], i_per_thread=tuning["i_per_thread"], j_tile=tuning["j_tile"],
+                          slice=tuning["slice"], variant=tuning["variant"])
     xh = xt.cpu().pin_memory()
     vh = vt.cpu().pin_memory()
     mh = mt.cpu().pin_memory()
     ah = at.cpu().pin_memory()
     lh = torch.empty((1, 1, 9), dtype=torch.float64).pin_memory()
-    nb.nbody_step_host(ctx, xh, vh, mh, ah, True, 1, lh)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
+    for _ in range(W):
+        nb.nbody_step_host(ctx_h, xh, vh, mh, ah, True, 1, lh)
+    e2e_s = 0.0
     for _ in range(ke):
-        nb.nbody_step_host(ctx, xh, vh, mh, ah, True, 1, lh)
-    e2e_s = reduce_max(time.perf_counter() - t0, pg, dev)
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        nb.nbody_step_host(ctx_h, xh, vh, mh, ah, True, 1, lh)
+        e2e_s += time.perf_counter() - t0
+    e2e_s = reduce_max(e2e_s, pg, dev)
+    ctx_h.close()
     e2e = {"value": whole_job_rate(interactions * ke, world, e2e_s), "unit": UNIT,
            "h2d_bytes_per_step": n * 10 * 8, "d2h_bytes_per_step": n * 9 * 8 + 9 * 8,
-           "call": "nbody_step_host (1 KDK step per call, pinned host x, v, m, a in; x, v, a, energy out)"}
+           "call": "nbody_step_host (1 KDK step per call, pinned host x, v, m, a in; x, v, a, energy out; "
+                   "step replayed as a CUDA graph; L2 flushed between calls, outside the timing)"}
 
     # ---- CPU oracle on this host (rank 0, N = 1 only), which also gives the force error
     base, ferr = None, None

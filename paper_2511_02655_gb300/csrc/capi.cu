@@ -1167,6 +1167,11 @@ nbody_status nbody_forces(nbody_ctx* c, const double* x, const double* m, double
   return run_post(c, post_launch(c, kCombine, xm, nullptr, m, a, phi), c->stream);
 }
 
+namespace {
+nbody_status step_validated(nbody_ctx* c, double* x, double* v, const double* m, double* a, int32_t a_valid,
+                            int32_t n_steps, double* energy_log);
+}  // namespace
+
 nbody_status nbody_step(nbody_ctx* c, double* x, double* v, const double* m, double* a, int32_t a_valid,
                         int32_t n_steps, double* energy_log) {
   if (!c) return fail(nullptr, NBODY_EINVAL, "ctx is NULL");
@@ -1179,7 +1184,16 @@ nbody_status nbody_step(nbody_ctx* c, double* x, double* v, const double* m, dou
   const int nrec = every > 0 ? n_steps / every : 0;
   if (energy_log && (s = check_dev(c, energy_log, (size_t)nrec * c->n_sys * 9 * sizeof(double), "energy_log")))
     return s;
+  return step_validated(c, x, v, m, a, a_valid, n_steps, energy_log);
+}
 
+namespace {
+
+// nbody_step after its argument checks (also the host-buffer step's path, whose
+// device buffers are the context's own).
+nbody_status step_validated(nbody_ctx* c, double* x, double* v, const double* m, double* a, int32_t a_valid,
+                            int32_t n_steps, double* energy_log) {
+  nbody_status s;
   if (!(c->cfg.flags & NBODY_FLAG_GRAPH)) return enqueue_step(c, x, v, m, a, a_valid, n_steps, energy_log, c->stream);
 
   // CUDA-graph replay: capture the whole call once per argument set, replay afterwards.
@@ -1217,6 +1231,8 @@ nbody_status nbody_step(nbody_ctx* c, double* x, double* v, const double* m, dou
   c->launches += c->glaunches;
   return NBODY_OK;
 }
+
+}  // namespace
 
 nbody_status nbody_energy(nbody_ctx* c, const double* x, const double* v, const double* m, double* out) {
   if (!c) return fail(nullptr, NBODY_EINVAL, "ctx is NULL");
@@ -1280,6 +1296,8 @@ nbody_status nbody_step_host(nbody_ctx* c, double* x, double* v, const double* m
   if (!c) return fail(nullptr, NBODY_EINVAL, "ctx is NULL");
   if (c->n_total == 0) return NBODY_OK;
   if (!x || !v || !m || !a) return fail(c, NBODY_EINVAL, "x, v, m and a must be non-NULL host pointers");
+  if (n_steps < 0) return fail(c, NBODY_EINVAL, "n_steps < 0");
+  if (n_steps > 0 && !(c->cfg.dt > 0)) return fail(c, NBODY_EINVAL, "dt must be > 0");
   const size_t n = (size_t)c->n_total, n3b = n * 3 * sizeof(double);
   const int every = c->cfg.energy_every;
   const int nrec = (every > 0 && n_steps > 0) ? n_steps / every : 0;
@@ -1314,7 +1332,7 @@ nbody_status nbody_step_host(nbody_ctx* c, double* x, double* v, const double* m
     NB_CUDA(c, cudaMemcpyAsync(hm, m, n * sizeof(double), cudaMemcpyHostToDevice, st));
     if (a_valid) NB_CUDA(c, cudaMemcpyAsync(ha, a, n3b, cudaMemcpyHostToDevice, st));
   }
-  s = nbody_step(c, hx, hv, hm, ha, a_valid, n_steps, hlog);
+  s = step_validated(c, hx, hv, hm, ha, a_valid, n_steps, hlog);  // the context's own buffers
   if (s) return s;
   if (zero_copy) {
     const Copy4 out{{hx, hv, ha, hlog}, {mx, mv, ma, mlog}, {n3, n3, n3, hlog ? (int64_t)(logb / sizeof(double)) : 0}};

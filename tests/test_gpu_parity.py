@@ -207,14 +207,16 @@ def test_host_pointers_rejected_without_launch(nb):
     nb.nbody_sync(ctx)
 
 
+@pytest.mark.parametrize("graph", [False, True])
 @pytest.mark.parametrize("memory", ["pinned", "pinned_state_pageable_log", "pageable"])
-def test_step_host_matches_device_path(nb, memory):
+def test_step_host_matches_device_path(nb, memory, graph):
     """nbody_step_host moves mapped pinned buffers with one copy kernel each way and any
     other host memory with cudaMemcpyAsync; both give the device path's results bit for bit."""
     import torch
     n = 2049  # odd: the copy kernel's ragged end
     x, v, m = inputs.plummer(n, seed=12)
-    ctx = nb.nbody_init(G=1.0, eps=0.01, dt=1e-3, precision=nb.MIXED, n=n, energy_every=2)
+    ctx = nb.nbody_init(G=1.0, eps=0.01, dt=1e-3, precision=nb.MIXED, n=n, energy_every=2,
+                        flags=nb.FLAG_GRAPH if graph else 0)
     xt, vt, mt = to_dev(x, v, m)
     at = torch.empty_like(xt)
     log = nb.nbody_step(ctx, xt, vt, mt, at, False, 4)
