@@ -83,8 +83,10 @@ typedef struct {
   int32_t slice;        /* force kernel: j-bodies per work item, multiple of j_tile (0 = autotune) */
   uint32_t flags;       /* NBODY_FLAG_* */
   int32_t variant;      /* mixed force and adjoint-VJP kernels: 1 = scalar float32, 2 = packed
-                           float32x2, 0 = autotune (each kernel separately); must be 0 or 1 for
-                           NBODY_FP64; NBODY_LAW_LJ with NBODY_MIXED uses 2 */
+                           float32x2, 3 = packed force kernel compiled for 4 CTAs per SM (a
+                           register cap; softened gravity, tiling 128 x 2 x 256; the VJP
+                           then uses 2), 0 = autotune (each kernel separately); must be 0 or 1
+                           for NBODY_FP64; NBODY_LAW_LJ with NBODY_MIXED uses 2 */
   int32_t law;          /* nbody_law */
   int32_t reserved;     /* must be 0 */
   double lj_epsilon;    /* Lennard-Jones well depth (finite; law = NBODY_LAW_LJ) */
@@ -217,7 +219,7 @@ nbody_status nbody_sync(nbody_ctx* ctx);
 /*
  * Tiling in use (after init / autotune): block, i_per_thread, j_tile, slice,
  * the number of persistent CTAs the force kernel launches, and the force
- * kernel variant (as in nbody_config.variant: 1 scalar, 2 packed). Any pointer
+ * kernel variant (as in nbody_config.variant: 1 scalar, 2 packed, 3 packed capped). Any pointer
  * may be NULL.
  */
 nbody_status nbody_get_tuning(const nbody_ctx* ctx, int32_t* block, int32_t* i_per_thread, int32_t* j_tile,

@@ -428,8 +428,14 @@ __device__ __forceinline__ void tile_pass_f32x2(const float* tx, const float* ty
 // PHI = false skips the potential (one packed operation per pair of interactions
 // for gravity, two for Lennard-Jones) when no caller needs it; the partials'
 // fourth component is then 0.
-template <int LAW, int BLOCK, int R, int J, bool PHI>
-__global__ void __launch_bounds__(BLOCK, (NBODY_MIN_CTAS > 0 ? NBODY_MIN_CTAS : 1)) k_force_mixed2(const PairLaunch L) {
+// MINB > 0 asks the compiler for MINB resident CTAs per SM (a register cap): the
+// 128 x 2 x 256 tiling compiles to 146 registers (3 CTAs per SM) without it, and
+// the 4-CTA build is ~1% faster at N = 65 536 but ~4% slower at N = 262 144, so
+// the tuner gets both (variant 3 of nbody_config). (The same cap on the 512-body
+// tile timed well on the tuner's synthetic sphere but 3% slower on real inputs.)
+template <int LAW, int BLOCK, int R, int J, bool PHI, int MINB = 0>
+__global__ void __launch_bounds__(BLOCK, (MINB > 0 ? MINB : (NBODY_MIN_CTAS > 0 ? NBODY_MIN_CTAS : 1)))
+    k_force_mixed2(const PairLaunch L) {
   static_assert(J % 4 == 0, "tiles hold whole quads of j-bodies");
   constexpr int LPT = (J + BLOCK - 1) / BLOCK;
   __shared__ __align__(16) float tx[2][J];  // double buffer: one barrier per tile
@@ -656,6 +662,8 @@ int occupancy_of(K kern, int block) {
   X(256, 1, 128) X(256, 2, 128) X(256, 4, 128) X(256, 1, 256) X(256, 2, 256) X(256, 4, 256)
 #define NBODY_MIXED_TILINGS(X) \
   NBODY_FORCE_TILINGS(X) X(128, 1, 512) X(128, 2, 512) X(128, 4, 512) X(256, 1, 512) X(256, 2, 512) X(256, 4, 512)
+// The register-capped packed variant (4 CTAs per SM): softened gravity only.
+#define NBODY_CAPPED_TILINGS(X) X(128, 2, 256)
 #define NBODY_LJ_MIXED_TILINGS(X) \
   X(128, 1, 256) X(256, 1, 256) X(128, 2, 256) X(128, 1, 512) X(256, 1, 512) X(256, 2, 512)
 #define NBODY_LJ_FP64_TILINGS(X) X(128, 1, 128) X(256, 1, 128) X(128, 2, 128) X(256, 2, 128)
@@ -691,6 +699,20 @@ cudaError_t launch_force(int precision, const PairLaunch& L, cudaStream_t st) {
   }
   if (L.law != 0) return cudaErrorInvalidConfiguration;
   if (precision == 1) {
+    if (L.variant == 2) {
+#define NBODY_X(B, R, J)                                                \
+  if (L.block == B && L.ipt == R && L.jtile == J) {                     \
+    if (L.phi)                                                          \
+      k_force_mixed2<0, B, R, J, true, 4><<<L.n_ctas, B, 0, st>>>(L);   \
+    else                                                                \
+      k_force_mixed2<0, B, R, J, false, 4><<<L.n_ctas, B, 0, st>>>(L);  \
+    return cudaGetLastError();                                          \
+  }
+      NBODY_CAPPED_TILINGS(NBODY_X)
+#undef NBODY_X
+      return cudaErrorInvalidConfiguration;
+    }
+    if (L.variant != 0 && L.variant != 1) return cudaErrorInvalidConfiguration;
 #define NBODY_X(B, R, J)                                               \
   if (L.block == B && L.ipt == R && L.jtile == J) {                    \
     if (L.variant == 1 && L.phi)                                       \
@@ -701,7 +723,6 @@ cudaError_t launch_force(int precision, const PairLaunch& L, cudaStream_t st) {
       k_force_mixed<B, R, J><<<L.n_ctas, B, 0, st>>>(L);               \
     return cudaGetLastError();                                         \
   }
-    if (L.variant != 0 && L.variant != 1) return cudaErrorInvalidConfiguration;
     NBODY_MIXED_TILINGS(NBODY_X)
 #undef NBODY_X
     return cudaErrorInvalidConfiguration;
@@ -736,6 +757,14 @@ int force_ctas_per_sm(int precision, int variant, int block, int ipt, int jtile,
     return 0;
   }
   if (law != 0) return 0;
+  if (precision == 1 && variant == 2) {
+#define NBODY_X(B, R, J)                                                                                    \
+  if (block == B && ipt == R && jtile == J)                                                                 \
+    return std::min(occupancy_of(k_force_mixed2<0, B, R, J, true, 4>, B), occupancy_of(k_force_mixed2<0, B, R, J, false, 4>, B));
+    NBODY_CAPPED_TILINGS(NBODY_X)
+#undef NBODY_X
+    return 0;
+  }
   if (precision == 1) {
     if (variant != 0 && variant != 1) return 0;
 #define NBODY_X(B, R, J)                                                                             \

@@ -426,3 +426,30 @@ def test_tuning_cache(nb, tmp_path, monkeypatch):
     assert path.read_text().splitlines()[-1].startswith(key)
     for c in (c1, c2, c3, c4):
         c.close()
+
+
+def test_register_capped_packed_variant(nb):
+    """Variant 3 (the packed kernel compiled for 4 CTAs per SM) computes exactly what variant 2
+    computes, in forces and in steps, and the tuner may choose it."""
+    import torch
+    x, v, m = inputs.plummer(4099, seed=71)
+    xt, vt, mt = to_dev(x, v, m)
+    outs = []
+    for variant in (2, 3):
+        ctx = nb.nbody_init(G=1.0, eps=0.01, dt=1e-3, precision=nb.MIXED, n=4099, variant=variant, block=128,
+                            i_per_thread=2, j_tile=256, slice=1024)
+        assert nb.nbody_get_tuning(ctx)["variant"] == variant
+        a, phi = nb.nbody_forces(ctx, xt, mt)
+        xs, vs, at = xt.clone(), vt.clone(), torch.empty_like(xt)
+        nb.nbody_step(ctx, xs, vs, mt, at, False, 3)
+        nb.nbody_sync(ctx)
+        outs.append((a, phi, xs, vs, at))
+        ctx.close()
+    for p, q in zip(*outs):
+        assert torch.equal(p, q)
+    a_ref, _ = oracle.forces(x, m, G=1.0, eps=0.01)
+    e = force_rel_err(outs[1][0].cpu().numpy(), a_ref)
+    assert np.median(e) <= MIX_MED and e.max() <= MIX_MAX
+    with pytest.raises(nb.NBodyError):  # capped build exists for the 128 x 2 tilings only
+        nb.nbody_init(G=1.0, eps=0.01, dt=1e-3, precision=nb.MIXED, n=4099, variant=3, block=256,
+                      i_per_thread=1, j_tile=256)
