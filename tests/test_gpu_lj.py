@@ -112,3 +112,60 @@ def test_lj_unsoftened_coincident_bodies_flag_nonfinite(nb):
     with pytest.raises(nb.NBodyError) as ei:
         nb.nbody_sync(ctx)
     assert ei.value.status == 5
+
+
+@pytest.mark.parametrize("graph", [False, True])
+def test_lj_paper_configuration_mixed(nb, graph):
+    """The paper's system (10 000 particles, density 0.05, walls) on the mixed path as the bench
+    runs it (tuned tiling, energy every step, optionally replayed as a CUDA graph): forces of 1024
+    sampled particles against the oracle at the start and after 40 steps, and the energy record
+    against the oracle's pair sum."""
+    import torch
+    n = 10000
+    x, v, m, box = inputs.lj_gas(n, seed=9)
+    ctx = nb.nbody_init(law=nb.LENNARD_JONES, precision=nb.MIXED, n=n, dt=5e-3, box=box, energy_every=1,
+                        flags=nb.FLAG_GRAPH if graph else 0)
+    xt, vt, mt = to_dev(x, v, m)
+    at = torch.empty_like(xt)
+    nb.nbody_forces(ctx, xt, mt, at)
+    idx = inputs.sample_indices(n, 1024, seed=5)
+    a_ref, _ = oracle.lj_forces_at(x, m, idx)
+    e = force_rel_err(at.cpu().numpy()[idx], a_ref)
+    assert np.median(e) <= MIX_MED and e.max() <= MIX_MAX, (np.median(e), e.max())
+    log = nb.nbody_step(ctx, xt, vt, mt, at, True, 40)
+    nb.nbody_sync(ctx)
+    xf, vf, af = to_np(xt, vt, at)
+    assert xf.min() >= 0 and xf.max() <= box
+    a_ref, _ = oracle.lj_forces_at(xf, m, idx)
+    e = force_rel_err(af[idx], a_ref)
+    assert np.median(e) <= MIX_MED and e.max() <= MIX_MAX, (np.median(e), e.max())
+    E = oracle.lj_energy(xf, vf, m)
+    assert abs(log.cpu().numpy()[-1, 0, 0] - E[0]) <= 1e-6 * abs(E[0])
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_lj_several_systems(nb, prec):
+    """Independent Lennard-Jones systems in one context (one of them empty): each system's forces
+    match the oracle on that system alone, so no pair crosses a system boundary."""
+    sizes = [500, 0, 1201, 37]
+    parts = [inputs.lj_gas(s, seed=20 + k, density=0.1) for k, s in enumerate(sizes) if s > 0]
+    x = np.concatenate([p[0] for p in parts])
+    m = np.concatenate([p[2] for p in parts])
+    off = [0]
+    for s_ in sizes:
+        off.append(off[-1] + s_)
+    ctx = nb.nbody_init(law=nb.LENNARD_JONES, precision=prec, offsets=off, dt=5e-3)
+    xt, mt = to_dev(x, m)
+    a, phi = nb.nbody_forces(ctx, xt, mt)
+    nb.nbody_sync(ctx)
+    a, phi = to_np(a, phi)
+    for s in range(len(sizes)):
+        b, e = off[s], off[s + 1]
+        if e == b:
+            continue
+        a_ref, phi_ref = oracle.lj_forces(x[b:e], m[b:e])
+        err = force_rel_err(a[b:e], a_ref)
+        if prec == nb.FP64:
+            assert err.max() <= FP64_TOL
+        else:
+            assert np.median(err) <= MIX_MED and err.max() <= MIX_MAX, (s, np.median(err), err.max())
