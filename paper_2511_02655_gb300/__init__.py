@@ -1,4 +1,5 @@
-"""GB300-native softened-gravity N-body hot path: Python binding of libnbody.
+"""GB300-native N-body hot path (softened gravity and the Lennard-Jones law):
+Python binding of libnbody.
 
 Argument marshalling only: every step of the path (staging, all-pairs forces,
 KDK leapfrog, reductions, adjoint) runs in the sm_103a kernels of
@@ -7,8 +8,9 @@ device memory and streams. There is no CPU fallback: if the library is
 missing, ``load()`` raises.
 
 Functions carry the C names: ``nbody_init``, ``nbody_forces``, ``nbody_step``,
-``nbody_energy``, ``nbody_adjoint``, ``nbody_adjoint_params``, ``nbody_step_host``, ``nbody_sync``,
-``nbody_get_tuning``, ``nbody_launch_count``, ``nbody_last_error``,
+``nbody_energy``, ``nbody_virial``, ``nbody_adjoint``, ``nbody_adjoint_params``,
+``nbody_step_host``, ``nbody_forces_noalloc``, ``nbody_sync``, ``nbody_get_tuning``,
+``nbody_profile``, ``nbody_kernel_time``, ``nbody_launch_count``, ``nbody_last_error``,
 ``nbody_destroy``, ``nbody_version``. ``NBodyAdjoint`` wraps the forward
 ``nbody_step`` and the reverse ``nbody_adjoint`` as a torch.autograd.Function.
 """
@@ -25,7 +27,8 @@ __all__ = [
     "nbody_adjoint_params",
     "nbody_step_host",
     "nbody_sync", "nbody_get_tuning", "nbody_launch_count", "nbody_last_error", "nbody_destroy",
-    "nbody_version", "nbody_profile", "nbody_kernel_time", "NBodyAdjoint", "ENERGY_FIELDS",
+    "nbody_version", "nbody_profile", "nbody_kernel_time", "nbody_forces_noalloc", "NOALLOC_MAX_BODIES",
+    "NBodyAdjoint", "ENERGY_FIELDS",
 ]
 
 FP64, MIXED = 0, 1
