@@ -110,7 +110,8 @@ typedef struct {
  * VJP) across runs, keyed by device, configuration and layout;
  * NBODY_TUNE_VERBOSE=1 prints the candidates' costs on stderr;
  * NBODY_FAULT_ALLOC=k makes the k-th scratch allocation of the context report
- * NBODY_ENOMEM (for testing failure paths).
+ * NBODY_ENOMEM (for testing failure paths); NBODY_NVTX=1 wraps the context's
+ * API calls (and the adjoint's forward and reverse phases) in NVTX ranges.
  */
 nbody_status nbody_init(nbody_ctx** ctx, const nbody_config* cfg, int64_t n_systems, const int64_t* offsets,
                         void* cuda_stream);

@@ -12,9 +12,12 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <memory>
 #include <mutex>
 #include <string>
 #include <vector>
+
+#include <nvtx3/nvToolsExt.h>
 
 #include "../../include/nbody.h"
 #include "nbody_internal.h"
@@ -43,6 +46,17 @@ constexpr double kNearRadiusSigma = 4.0;
 struct DevBuf {
   void* p = nullptr;
   size_t bytes = 0;
+};
+
+// NVTX range for profilers (nsys, ncu --nvtx), pushed only when the context asks for it.
+struct NvtxRange {
+  bool on;
+  NvtxRange(bool enable, const char* name) : on(enable) {
+    if (on) nvtxRangePushA(name);
+  }
+  ~NvtxRange() {
+    if (on) nvtxRangePop();
+  }
 };
 
 std::mutex g_err_mu;
@@ -108,6 +122,7 @@ struct nbody_ctx {
   int vmax_slices = 1;
   bool vjp_ready = false;
   int64_t fault_alloc = 0;  // > 0: the fault_alloc-th scratch allocation fails (NBODY_FAULT_ALLOC, tests)
+  bool nvtx = false;        // NBODY_NVTX=1: NVTX ranges around the API calls and the adjoint's phases
   bool vjp_params = false;  // VJP launches also form the G and eps gradient sums
 
   // scratch
@@ -712,6 +727,7 @@ void tune_cache_store(const nbody_ctx* c, bool vjp, const Tiling& t) {
 }
 
 nbody_status autotune(nbody_ctx* c, bool vjp) {
+  NvtxRange range(c->nvtx, vjp ? "nbody_autotune_vjp" : "nbody_autotune");
   {
     Tiling t;
     if (tune_cache_lookup(c, vjp, &t)) {
@@ -909,6 +925,7 @@ nbody_status adjoint_sweep(nbody_ctx* c, const double* x0, const double* v0, con
                            const double* lam_xT, const double* lam_vT, double* g_x0, double* g_v0, double* g_m,
                            double* g_params) {
   if (!c) return fail(nullptr, NBODY_EINVAL, "ctx is NULL");
+  NvtxRange range(c->nvtx, "nbody_adjoint");
   if (T < 0 || K < 1) return fail(c, NBODY_EINVAL, "need n_steps >= 0 and checkpoint_every >= 1");
   if (c->cfg.law != NBODY_LAW_GRAVITY || c->cfg.box > 0)
     return fail(c, NBODY_EUNSUPPORTED, "nbody_adjoint supports softened gravity without walls only");
@@ -972,6 +989,7 @@ nbody_status adjoint_sweep(nbody_ctx* c, const double* x0, const double* v0, con
   };
 
   // forward pass: checkpoints (x, v, a) at the start of every segment
+  std::unique_ptr<NvtxRange> fwd(new NvtxRange(c->nvtx, "forward"));
   for (int t = 0; t < T; ++t) {
     if (t % K == 0) {
       double* cp = ck + (size_t)(t / K) * 3 * n3;
@@ -982,6 +1000,8 @@ nbody_status adjoint_sweep(nbody_ctx* c, const double* x0, const double* v0, con
     if ((s = step(nullptr))) return s;
   }
 
+  fwd.reset();
+  NvtxRange rev(c->nvtx, "reverse");
   // reverse sweep. VJPs at x_T (coef dt/2), x_s for 0 < s < T (coef dt: the
   // closing half-kick of step s-1 and the opening half-kick of step s share
   // x_s and the same weights), x_0 (coef dt/2).
@@ -1112,6 +1132,8 @@ nbody_status nbody_init(nbody_ctx** out, const nbody_config* cfg, int64_t n_syst
   // host-side fault injection for tests: NBODY_FAULT_ALLOC=k makes the k-th scratch
   // allocation of this context report NBODY_ENOMEM (no device fault is involved)
   if (const char* fa = getenv("NBODY_FAULT_ALLOC")) c->fault_alloc = std::max<int64_t>(0, atoll(fa));
+  if (const char* nv = getenv("NBODY_NVTX")) c->nvtx = nv[0] == '1';
+  NvtxRange range_init(c->nvtx, "nbody_init");
   c->stream = static_cast<cudaStream_t>(cuda_stream);
   c->n_sys = (int)n_systems;
   c->offsets.assign(offsets, offsets + n_systems + 1);
@@ -1186,6 +1208,7 @@ nbody_status nbody_set_stream(nbody_ctx* c, void* stream) {
 
 nbody_status nbody_forces(nbody_ctx* c, const double* x, const double* m, double* a, double* phi) {
   if (!c) return fail(nullptr, NBODY_EINVAL, "ctx is NULL");
+  NvtxRange range(c->nvtx, "nbody_forces");
   if (c->n_total == 0) return NBODY_OK;
   nbody_status s;
   if ((s = check_state_args(c, x, nullptr, m, a, false, true))) return s;
@@ -1205,6 +1228,7 @@ nbody_status step_validated(nbody_ctx* c, double* x, double* v, const double* m,
 nbody_status nbody_step(nbody_ctx* c, double* x, double* v, const double* m, double* a, int32_t a_valid,
                         int32_t n_steps, double* energy_log) {
   if (!c) return fail(nullptr, NBODY_EINVAL, "ctx is NULL");
+  NvtxRange range(c->nvtx, "nbody_step");
   if (n_steps < 0) return fail(c, NBODY_EINVAL, "n_steps < 0");
   if (n_steps > 0 && !(c->cfg.dt > 0)) return fail(c, NBODY_EINVAL, "dt must be > 0");
   if (c->n_total == 0) return NBODY_OK;
@@ -1266,6 +1290,7 @@ nbody_status step_validated(nbody_ctx* c, double* x, double* v, const double* m,
 
 nbody_status nbody_energy(nbody_ctx* c, const double* x, const double* v, const double* m, double* out) {
   if (!c) return fail(nullptr, NBODY_EINVAL, "ctx is NULL");
+  NvtxRange range(c->nvtx, "nbody_energy");
   nbody_status s;
   if ((s = check_dev(c, out, (size_t)c->n_sys * 9 * sizeof(double), "out"))) return s;
   if (c->n_total == 0) {
@@ -1288,6 +1313,7 @@ nbody_status nbody_energy(nbody_ctx* c, const double* x, const double* v, const 
 
 nbody_status nbody_virial(nbody_ctx* c, const double* x, const double* v, const double* m, double* out) {
   if (!c) return fail(nullptr, NBODY_EINVAL, "ctx is NULL");
+  NvtxRange range(c->nvtx, "nbody_virial");
   nbody_status s;
   if ((s = check_dev(c, out, (size_t)c->n_sys * 3 * sizeof(double), "out"))) return s;
   if (c->n_total == 0) {
@@ -1324,6 +1350,7 @@ nbody_status nbody_adjoint_params(nbody_ctx* c, const double* x0, const double* 
 nbody_status nbody_step_host(nbody_ctx* c, double* x, double* v, const double* m, double* a, int32_t a_valid,
                              int32_t n_steps, double* energy_log) {
   if (!c) return fail(nullptr, NBODY_EINVAL, "ctx is NULL");
+  NvtxRange range(c->nvtx, "nbody_step_host");
   if (c->n_total == 0) return NBODY_OK;
   if (!x || !v || !m || !a) return fail(c, NBODY_EINVAL, "x, v, m and a must be non-NULL host pointers");
   if (n_steps < 0) return fail(c, NBODY_EINVAL, "n_steps < 0");

@@ -453,3 +453,23 @@ def test_register_capped_packed_variant(nb):
     with pytest.raises(nb.NBodyError):  # capped build exists for the 128 x 2 tilings only
         nb.nbody_init(G=1.0, eps=0.01, dt=1e-3, precision=nb.MIXED, n=4099, variant=3, block=256,
                       i_per_thread=1, j_tile=256)
+
+
+def test_nvtx_ranges_enabled(nb, monkeypatch):
+    """NBODY_NVTX=1 wraps the API calls in NVTX ranges; results are unchanged."""
+    import torch
+    x, v, m = inputs.plummer(1000, seed=81)
+    outs = []
+    for flag in ("0", "1"):
+        monkeypatch.setenv("NBODY_NVTX", flag)
+        ctx = nb.nbody_init(G=1.0, eps=0.01, dt=1e-3, precision=nb.MIXED, n=1000, energy_every=1,
+                            block=128, i_per_thread=2, j_tile=256, slice=512, variant=2)
+        xt, vt, mt = to_dev(x, v, m)
+        at = torch.empty_like(xt)
+        log = nb.nbody_step(ctx, xt, vt, mt, at, False, 3)
+        g = nb.nbody_adjoint(ctx, xt, vt, mt, 3, 2, at.clone(), at.clone())
+        nb.nbody_sync(ctx)
+        outs.append((xt.cpu(), log.cpu(), g[0].cpu()))
+        ctx.close()
+    for p, q in zip(*outs):
+        assert torch.equal(p, q)
