@@ -988,16 +988,18 @@ nbody_status adjoint_sweep(nbody_ctx* c, const double* x0, const double* v0, con
     return run_post(c, post_launch(c, kCombine | kKickEnd, xw, vw, m, aw, nullptr), st);
   };
 
-  // forward pass: checkpoints (x, v, a) at the start of every segment
+  // forward pass: checkpoints (x, v, a) at the start of every segment; it stops at
+  // the last checkpoint, since the reverse sweep recomputes the last segment anyway
   std::unique_ptr<NvtxRange> fwd(new NvtxRange(c->nvtx, "forward"));
-  for (int t = 0; t < T; ++t) {
+  const int last_ckpt = (nseg - 1) * K;
+  for (int t = 0; t <= last_ckpt; ++t) {
     if (t % K == 0) {
       double* cp = ck + (size_t)(t / K) * 3 * n3;
       NB_CUDA(c, cudaMemcpyAsync(cp, xw, n3b, cudaMemcpyDeviceToDevice, st));
       NB_CUDA(c, cudaMemcpyAsync(cp + n3, vw, n3b, cudaMemcpyDeviceToDevice, st));
       NB_CUDA(c, cudaMemcpyAsync(cp + 2 * n3, aw, n3b, cudaMemcpyDeviceToDevice, st));
     }
-    if ((s = step(nullptr))) return s;
+    if (t < last_ckpt && (s = step(nullptr))) return s;
   }
 
   fwd.reset();
@@ -1036,9 +1038,11 @@ nbody_status adjoint_sweep(nbody_ctx* c, const double* x0, const double* v0, con
     NB_CUDA(c, cudaMemcpyAsync(vw, cp + n3, n3b, cudaMemcpyDeviceToDevice, st));
     NB_CUDA(c, cudaMemcpyAsync(aw, cp + 2 * n3, n3b, cudaMemcpyDeviceToDevice, st));
     NB_CUDA(c, cudaMemcpyAsync(X, xw, n3b, cudaMemcpyDeviceToDevice, st));
-    for (int t = 0; t < len; ++t)
-      if ((s = step(X + (size_t)(t + 1) * n3))) return s;
+    // positions s0 .. top; a segment's end state is the next segment's start, whose
+    // VJP that segment has already taken, so only the last segment steps to its end
     const int top = (k == nseg - 1) ? s1 : s1 - 1;
+    for (int t = 0; t < top - s0; ++t)
+      if ((s = step(X + (size_t)(t + 1) * n3))) return s;
     NB_CUDA(c, launch_stage_vec(vch, nch, c->cfg.precision, X + (size_t)(top - s0) * n3, m,
                                 static_cast<const double*>(c->centre.p), c->stage.p, 1, st));
     ++c->launches;
