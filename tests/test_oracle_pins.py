@@ -496,3 +496,21 @@ def test_lj_gas_generator():
     assert abs((v ** 2).mean() - 2.0) < 0.15
     d = np.linalg.norm(x[:, None, :] - x[None, :, :], axis=-1) + np.eye(1000) * 1e9
     assert d.min() > 0.5  # no overlapping pairs at the start
+
+
+def test_lj_forces_at_equals_rows_of_lj_forces():
+    x, v, m, box = inputs.lj_gas(300, seed=4, density=0.2)
+    m = m * np.exp(0.2 * np.random.default_rng(8).standard_normal(300))
+    a, phi = oracle.lj_forces(x, m, eps_lj=1.1, sigma=0.9)
+    idx = np.array([0, 17, 299, 150, 17])
+    ai, phii = oracle.lj_forces_at(x, m, idx, eps_lj=1.1, sigma=0.9)
+    assert np.array_equal(ai, a[idx]) and np.array_equal(phii, phi[idx])
+
+
+@pytest.mark.parametrize("gen", ["plummer", "two_spheres", "lj_gas", "targets"])
+def test_generators_are_deterministic_by_seed(gen):
+    f = getattr(inputs, gen)
+    a1, a2, b = f(64, seed=3), f(64, seed=3), f(64, seed=4)
+    flat = lambda r: np.concatenate([np.ravel(np.asarray(t, dtype=float)) for t in (r if isinstance(r, tuple) else (r,))])
+    assert np.array_equal(flat(a1), flat(a2))
+    assert not np.array_equal(flat(a1), flat(b))
