@@ -172,9 +172,16 @@ def cpu_baseline(x, m, G, eps, a_gpu, budget_s=12.0):
     a_ref, _ = oracle.forces_at(x, m, idx, G=G, eps=eps, threads=threads)
     dt = time.perf_counter() - t0
     err = rel_force_error(a_gpu[idx], a_ref)
+    # the same oracle on one host thread, on a smaller sample (about 2 s)
+    k1 = int(max(16, min(n, 2.0 / max(per_body * threads, 1e-9))))
+    idx1 = inputs.sample_indices(n, k1, seed=8)
+    t0 = time.perf_counter()
+    oracle.forces_at(x, m, idx1, G=G, eps=eps, threads=1)
+    dt1 = time.perf_counter() - t0
     base = {"value": k * n / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": f"FP64 direct-sum forces of {k} seeded bodies against all {n} (1 force pass, "
-                      f"{k * n:.3e} interactions, {dt:.1f} s)"}
+                      f"{k * n:.3e} interactions, {dt:.1f} s)",
+            "one_thread": {"value": k1 * n / dt1, "sample": f"{k1} seeded bodies against all {n}, {dt1:.1f} s"}}
     return base, {"median": float(np.median(err)), "max": float(err.max()), "bodies": int(k)}
 
 
