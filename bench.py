@@ -185,6 +185,33 @@ def cpu_baseline(x, m, G, eps, a_gpu, budget_s=12.0):
     return base, {"median": float(np.median(err)), "max": float(err.max()), "bodies": int(k)}
 
 
+def energy_vs_oracle(nb, dev, x, v, m, G, eps, dt, xf, vf, E_final, steps=3):
+    """The mixed path's energy of the bench's final state against the oracle's pair-sum energy of the
+    same state, and the energy drift over the first `steps` KDK steps from the initial state of the
+    mixed and FP64 GPU paths beside the oracle's own KDK run."""
+    import numpy as np
+    import torch
+
+    import oracle
+    threads = oracle.default_threads()
+    E_or_final = oracle.energy(xf, vf, m, G=G, eps=eps, threads=threads)[0]
+    E_or0 = oracle.energy(x, v, m, G=G, eps=eps, threads=threads)[0]
+    _, _, _, log_or = oracle.kdk(x, v, m, G, eps, dt, steps, energy_every=1, threads=threads)
+    out = {"final_state_rel_err": abs(E_final - E_or_final) / abs(E_or_final),
+           f"drift_first_{steps}_steps": {"oracle": float(np.abs(log_or[:, 0] - E_or0).max() / abs(E_or0))},
+           f"err_vs_oracle_first_{steps}_steps": {}}
+    for prec, name in ((nb.MIXED, "gpu_mixed"), (nb.FP64, "gpu_fp64")):
+        c = nb.nbody_init(G=G, eps=eps, dt=dt, precision=prec, n=len(m), energy_every=1)
+        xs, vs, ms = (torch.from_numpy(t).to(dev) for t in (x, v, m))
+        E0 = nb.nbody_energy(c, xs, vs, ms).cpu().numpy()[0, 0]
+        lg = nb.nbody_step(c, xs, vs, ms, torch.empty_like(xs), False, steps).cpu().numpy()[:, 0, 0]
+        nb.nbody_sync(c)
+        c.close()
+        out[f"drift_first_{steps}_steps"][name] = float(np.abs(lg - E0).max() / abs(E0))
+        out[f"err_vs_oracle_first_{steps}_steps"][name] = float(np.abs(lg - log_or[:, 0]).max() / abs(E_or0))
+    return out
+
+
 def _event_time(fn, stream, nvtx=None):
     """CUDA-event seconds of fn() on stream; the launches sit in NVTX range `nvtx` (for ncu filters)."""
     import torch
@@ -201,54 +228,106 @@ def _event_time(fn, stream, nvtx=None):
     return e0.elapsed_time(e1) * 1e-3
 
 
-def aux_measurements(dev):
-    """The other workloads, each measured briefly (rank 0, one GPU): CUDA-event times around
-    nbody_step / nbody_adjoint calls, initialisation and autotuning excluded."""
+def _err_stats(err):
+    import numpy as np
+    err = np.asarray(err)
+    return {"median": float(np.median(err)), "max": float(err.max()), "n": int(err.size)}
+
+
+def _elem_err(g, g_ref, guard=1e-3):
+    """Per-element relative error, floored at guard * rms(g_ref) (cancellation guard)."""
+    import numpy as np
+    g, g_ref = np.asarray(g).ravel(), np.asarray(g_ref).ravel()
+    rms = float(np.sqrt(np.mean(g_ref ** 2)))
+    return np.abs(g - g_ref) / np.maximum(np.abs(g_ref), guard * rms)
+
+
+def _timed(fn):
+    t0 = time.perf_counter()
+    out = fn()
+    return out, time.perf_counter() - t0
+
+
+def aux_two_spheres(dev, stream):
+    """Two Plummer spheres, N = 1 048 576, eps = 0.002, dt = 5e-4, mixed: throughput, force error
+    against the oracle on 16 384 sampled bodies at the start and after the timed steps, energy drift,
+    and the oracle's rate on those samples extrapolated to a whole force pass."""
     import numpy as np
     import torch
 
+    import oracle
     import paper_2511_02655_gb300 as nb
     from paper_2511_02655_gb300 import inputs
-    stream = torch.cuda.current_stream()
-    out = {}
-    # two Plummer spheres, N = 1 048 576, eps = 0.002, dt = 5e-4, mixed
-    n = 1048576
+    n, G, eps, dt, k, ks = 1048576, 1.0, 0.002, 5e-4, 3, 16384
     x, v, m = inputs.two_spheres(n, seed=3)
-    ctx = nb.nbody_init(G=1.0, eps=0.002, dt=5e-4, precision=nb.MIXED, n=n)
+    ctx = nb.nbody_init(G=G, eps=eps, dt=dt, precision=nb.MIXED, n=n)
     xt, vt, mt = (torch.from_numpy(t).to(dev) for t in (x, v, m))
     at = torch.empty_like(xt)
     nb.nbody_forces(ctx, xt, mt, at, None, with_phi=False)
+    a0 = at.cpu().numpy()
+    E0 = nb.nbody_energy(ctx, xt, vt, mt).cpu().numpy()[0, 0]
     nb.nbody_profile(ctx, True)
-    k = 3
     sec = _event_time(lambda: nb.nbody_step(ctx, xt, vt, mt, at, True, k), stream, "aux_two_spheres")
     kms, kl = nb.nbody_kernel_time(ctx, 0)
+    nb.nbody_profile(ctx, False)
+    E1 = nb.nbody_energy(ctx, xt, vt, mt).cpu().numpy()[0, 0]
     nb.nbody_sync(ctx)
-    out["two_spheres_1m"] = {"interactions_per_s": float(n) * n * k / sec, "steps": k,
-                             "force_kernel_ms": kms / kl, "tuning": nb.nbody_get_tuning(ctx)}
+    xf, af = xt.cpu().numpy(), at.cpu().numpy()
+    tuning = nb.nbody_get_tuning(ctx)
     ctx.close()
     del xt, vt, mt, at
-    # ensemble: 512 Plummer systems, N log-uniform in [64, 16384], eps = 0.01, dt = 1e-3
+    threads = oracle.default_threads()
+    idx0, idx1 = inputs.sample_indices(n, ks, seed=17), inputs.sample_indices(n, ks, seed=19)
+    (ref0, _), t0 = _timed(lambda: oracle.forces_at(x, m, idx0, G=G, eps=eps, threads=threads))
+    (ref1, _), t1 = _timed(lambda: oracle.forces_at(xf, m, idx1, G=G, eps=eps, threads=threads))
+    rate = 2.0 * ks * n / (t0 + t1)
+    return {"interactions_per_s": float(n) * n * k / sec, "steps": k, "force_kernel_ms": kms / kl, "tuning": tuning,
+            "force_err_vs_oracle": {"step_0": _err_stats(rel_force_error(a0[idx0], ref0)),
+                                    f"step_{k}": _err_stats(rel_force_error(af[idx1], ref1)),
+                                    "sample": f"{ks} seeded bodies against all {n}, FP64 oracle"},
+            "energy_drift_rel": float(abs(E1 - E0) / abs(E0)),
+            "cpu_baseline": {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": f"FP64 forces of 2 x {ks} seeded bodies against all {n} (the error samples), "
+                                       f"{t0 + t1:.1f} s",
+                             "extrapolated_s_per_force_pass": float(n) * n / rate,
+                             "extrapolation": "extrapolated by N^2 from the sampled rows"}}
+
+
+def aux_ensemble(dev, stream):
+    """512 Plummer systems, N log-uniform in [64, 16384], eps = 0.01, dt = 1e-3, 50 steps per call in one
+    persistent launch per step replayed as a CUDA graph, beside 512 per-system FP64 launch sequences;
+    per-system sampled force error and energy drift; the oracle on a seeded subset of whole systems,
+    extrapolated by sum N^2."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import paper_2511_02655_gb300 as nb
+    from paper_2511_02655_gb300 import inputs
+    G, eps, dt, T = 1.0, 0.01, 1e-3, 50
     ens = inputs.ensemble(512, seed=4)
     off = [int(o) for o in ens.offsets]
-    pairs = float((np.diff(ens.offsets).astype(np.float64) ** 2).sum())
-    ctx = nb.nbody_init(G=1.0, eps=0.01, dt=1e-3, precision=nb.MIXED, offsets=off, energy_every=50,
-                        flags=nb.FLAG_GRAPH)
+    sizes = np.diff(ens.offsets).astype(np.int64)
+    pairs = float((sizes.astype(np.float64) ** 2).sum())
+    ctx = nb.nbody_init(G=G, eps=eps, dt=dt, precision=nb.MIXED, offsets=off, energy_every=T, flags=nb.FLAG_GRAPH)
     xt, vt, mt = (torch.from_numpy(t).to(dev) for t in (ens.x, ens.v, ens.m))
     at = torch.empty_like(xt)
     log = torch.empty((1, 512, 9), dtype=torch.float64, device=dev)
     nb.nbody_forces(ctx, xt, mt, at, None, with_phi=False)
-    nb.nbody_step(ctx, xt, vt, mt, at, True, 50, log)  # captures the graph
+    nb.nbody_step(ctx, xt, vt, mt, at, True, T, log)  # captures the graph
+    E0 = nb.nbody_energy(ctx, xt, vt, mt).cpu().numpy()[:, 0]
     l0 = nb.nbody_launch_count(ctx)
-    sec = _event_time(lambda: nb.nbody_step(ctx, xt, vt, mt, at, True, 50, log), stream, "aux_ensemble")
+    sec = _event_time(lambda: nb.nbody_step(ctx, xt, vt, mt, at, True, T, log), stream, "aux_ensemble")
     nb.nbody_sync(ctx)
     launches = nb.nbody_launch_count(ctx) - l0
+    E1 = log.cpu().numpy()[0, :, 0]
+    xf, af = xt.cpu().numpy(), at.cpu().numpy()
     ctx.close()
     # the same systems as 512 separate FP64 contexts, one launch sequence per system, 1 step
     ctxs, bufs = [], []
     for s_ in range(512):
         b, e = off[s_], off[s_ + 1]
-        c1 = nb.nbody_init(G=1.0, eps=0.01, dt=1e-3, precision=nb.FP64, n=e - b, block=128, i_per_thread=1,
-                           j_tile=128)
+        c1 = nb.nbody_init(G=G, eps=eps, dt=dt, precision=nb.FP64, n=e - b, block=128, i_per_thread=1, j_tile=128)
         xs, vs, ms = (torch.from_numpy(np.ascontiguousarray(t[b:e])).to(dev) for t in (ens.x, ens.v, ens.m))
         a1 = torch.empty_like(xs)
         nb.nbody_forces(c1, xs, ms, a1, None, with_phi=False)
@@ -261,21 +340,63 @@ def aux_measurements(dev):
     sec64 = _event_time(per_system, stream, "aux_ensemble_fp64")
     for c1 in ctxs:
         c1.close()
-    out["ensemble_512"] = {"mixed_graph_interactions_per_s": pairs * 50 / sec, "steps": 50,
-                           "fp64_per_system_interactions_per_s": pairs / sec64,
-                           "graph_over_fp64_per_system": (pairs * 50 / sec) / (pairs / sec64),
-                           "pairs_per_step": pairs, "launches_per_50_steps": int(launches)}
-    # the paper's own system: Lennard-Jones gas, 10 000 particles, 2500 KDK steps with the total
-    # energy reduced every step, reflecting walls (reduced units, density 0.05, T = 2, dt = 5e-3)
-    n, steps = 10000, 2500
+    # force error at the final state: up to 32 seeded bodies of every system against its own bodies
+    errs, worst = [], 0.0
+    for s_ in range(512):
+        b, e = off[s_], off[s_ + 1]
+        idx = inputs.sample_indices(e - b, min(32, e - b), seed=1000 + s_)
+        ref, _ = oracle.forces_at(xf[b:e], ens.m[b:e], idx, G=G, eps=eps, threads=1)
+        err = rel_force_error(af[b:e][idx], ref)
+        errs.append(err)
+        worst = max(worst, float(err.max()))
+    # the oracle on 16 seeded whole systems (one force pass each), extrapolated by sum N^2
+    threads = oracle.default_threads()
+    sel = np.random.default_rng(77).choice(512, 16, replace=False)
+    _, t_or = _timed(lambda: [oracle.forces(ens.x[off[s_]:off[s_ + 1]], ens.m[off[s_]:off[s_ + 1]], G=G, eps=eps,
+                                            threads=threads, with_phi=False) for s_ in sel])
+    sub_pairs = float((sizes[sel].astype(np.float64) ** 2).sum())
+    rate = sub_pairs / t_or
+    drift = np.abs(E1 - E0) / np.abs(E0)
+    return {"mixed_graph_interactions_per_s": pairs * T / sec, "steps": T,
+            "fp64_per_system_interactions_per_s": pairs / sec64,
+            "graph_over_fp64_per_system": (pairs * T / sec) / (pairs / sec64),
+            "pairs_per_step": pairs, "launches_per_50_steps": int(launches),
+            "force_err_vs_oracle": dict(_err_stats(np.concatenate(errs)), worst_system_max=worst,
+                                        sample="final state, up to 32 seeded bodies of each of the 512 systems "
+                                               "against that system, FP64 oracle"),
+            "energy_drift_rel_over_50_steps": {"max": float(drift.max()), "median": float(np.median(drift))},
+            "cpu_baseline": {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": f"FP64 force pass of 16 seeded whole systems ({sub_pairs:.3e} interactions, "
+                                       f"{t_or:.2f} s)",
+                             "extrapolated_s_per_step": pairs / rate,
+                             "extrapolation": "extrapolated by sum N^2 over the 512 systems"}}
+
+
+def aux_lj(dev, stream):
+    """The paper's own system: Lennard-Jones gas, 10 000 particles, 2500 KDK steps with the total energy
+    reduced every step, reflecting walls (reduced units, density 0.05, T = 2, dt = 5e-3); sampled force
+    error at the end, energy drift beside the oracle's over the first 20 steps, and the oracle's time for
+    those 20 steps extrapolated to the whole run."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import paper_2511_02655_gb300 as nb
+    from paper_2511_02655_gb300 import inputs
+    n, steps, dt, k20 = 10000, 2500, 5e-3, 20
     x, v, m, box = inputs.lj_gas(n, seed=9)
+    E_or0 = oracle.lj_energy(x, v, m)[0]
+    threads = oracle.default_threads()
+    (_, _, _, log_or), t_or = _timed(lambda: oracle.lj_kdk(x, v, m, 1.0, 1.0, 0.0, box, dt, k20, energy_every=1,
+                                                           threads=threads))
     lj = {}
     for prec, flags, name in ((nb.MIXED, nb.FLAG_GRAPH, "mixed_graph"), (nb.FP64, 0, "fp64")):
-        ctx = nb.nbody_init(law=nb.LENNARD_JONES, precision=prec, n=n, dt=5e-3, box=box, energy_every=1,
+        ctx = nb.nbody_init(law=nb.LENNARD_JONES, precision=prec, n=n, dt=dt, box=box, energy_every=1,
                             flags=flags)
         xt, vt, mt = (torch.from_numpy(a).to(dev) for a in (x, v, m))
         at = torch.empty_like(xt)
         logt = torch.empty((steps, 1, 9), dtype=torch.float64, device=dev)
+        E_gpu0 = nb.nbody_energy(ctx, xt, vt, mt).cpu().numpy()[0, 0]
         if flags:  # capture once on a copy of the state, replay on the real one
             x2, v2, a2 = xt.clone(), vt.clone(), torch.empty_like(xt)
             nb.nbody_step(ctx, x2, v2, mt, a2, False, steps, logt)
@@ -285,28 +406,137 @@ def aux_measurements(dev):
         sec = _event_time(lambda: nb.nbody_step(ctx, xt, vt, mt, at, False, steps, logt), stream, f"aux_lj_{name}")
         nb.nbody_sync(ctx)
         e = logt.cpu().numpy()[:, 0, 0]
+        xf, af = xt.cpu().numpy(), at.cpu().numpy()
+        idx = inputs.sample_indices(n, 2048, seed=29)
+        ref, _ = oracle.lj_forces_at(xf, m, idx, threads=threads)
         lj[name] = {"seconds": sec, "interactions_per_s": float(n) * n * (steps + 1) / sec,
-                    "energy_drift_max_rel": float(np.abs(e - e[0]).max() / abs(e[0]))}
+                    "energy_drift_max_rel": float(np.abs(e - E_gpu0).max() / abs(E_gpu0)),
+                    "energy_drift_first_20_steps": float(np.abs(e[:k20] - E_gpu0).max() / abs(E_gpu0)),
+                    "energy_err_vs_oracle_first_20_steps": float(np.abs(e[:k20] - log_or[:, 0]).max() / abs(E_or0)),
+                    "force_err_vs_oracle_at_end": dict(_err_stats(rel_force_error(af[idx], ref)),
+                                                       sample="2048 seeded particles after 2500 steps, FP64 oracle")}
         ctx.close()
-    out["paper_lj_gas_10000x2500"] = dict(lj, context="paper (Sec. VI): 19.02 s median, RAJA, 4x A100, FP64, "
-                                                      "with energy reduction; other hardware, context only")
-    # adjoint: N = 16384 Plummer, 200 KDK steps, dt = 1e-3, checkpoints every 20, loss sum |x_T - t|^2
+    return dict(lj, oracle_energy_drift_first_20_steps=float(np.abs(log_or[:, 0] - E_or0).max() / abs(E_or0)),
+                cpu_baseline={"value": float(n) * n * (k20 + 1) / t_or, "unit": UNIT, "cores": threads,
+                              "kind": "oracle", "sample": f"the FP64 oracle's KDK run of the first {k20} steps "
+                                                          f"with the energy every step, {t_or:.1f} s",
+                              "extrapolated_s_for_2500_steps": t_or * steps / k20,
+                              "extrapolation": "extrapolated by the step count"},
+                context="paper (Sec. VI): 19.02 s median, RAJA, 4x A100, FP64, with energy reduction; other "
+                        "hardware, context only")
+
+
+def aux_adjoint(dev, stream):
+    """Adjoint: N = 16384 Plummer, 200 KDK steps, dt = 1e-3, checkpoints every 20, loss sum |x_T - t|^2.
+    Times both precisions; the mixed gradients per element against the FP64 ones; both against FP64
+    central differences (h = 1e-6) of the FP64 GPU trajectory on 3 seeded coordinates; and the CPU
+    reference adjoint (the oracle) at N = 2048, timed and compared with the GPU adjoints there."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import paper_2511_02655_gb300 as nb
+    from paper_2511_02655_gb300 import inputs
+    G, eps, dt, T, K = 1.0, 0.01, 1e-3, 200, 20
+    out, grads = {}, {}
+
+    def final_lam(n):
+        """dL/dx_T = 2 (x_T - t) from the FP64 GPU trajectory (shared by both precisions' adjoints, so
+        that their gradients differ only by the adjoint's own arithmetic)."""
+        x, v, m = inputs.plummer(n, seed=5)
+        t = torch.from_numpy(inputs.targets(n, seed=6)).to(dev)
+        ctx = nb.nbody_init(G=G, eps=eps, dt=dt, precision=nb.FP64, n=n)
+        xs, vs, mt = (torch.from_numpy(a).to(dev) for a in (x, v, m))
+        nb.nbody_step(ctx, xs, vs, mt, torch.empty_like(xs), False, T)
+        nb.nbody_sync(ctx)
+        ctx.close()
+        return 2 * (xs - t)
+
+    def run(n, prec, lam, timed_name=None):
+        x, v, m = inputs.plummer(n, seed=5)
+        ctx = nb.nbody_init(G=G, eps=eps, dt=dt, precision=prec, n=n)
+        xt, vt, mt = (torch.from_numpy(a).to(dev) for a in (x, v, m))
+        zero = torch.zeros_like(xt)
+        g = nb.nbody_adjoint(ctx, xt, vt, mt, T, K, lam, zero)  # tunes the VJP tiling
+        sec = None
+        if timed_name:
+            sec = _event_time(lambda: nb.nbody_adjoint(ctx, xt, vt, mt, T, K, lam, zero, *g), stream,
+                              f"aux_{timed_name}")
+        nb.nbody_sync(ctx)
+        ctx.close()
+        return sec, [a.cpu().numpy() for a in g]
+
     n = 16384
+    lam = final_lam(n)
+    for prec, name in ((nb.MIXED, "adjoint_16384_mixed"), (nb.FP64, "adjoint_16384_fp64")):
+        sec, grads[prec] = run(n, prec, lam, name)
+        out[name] = {"seconds": sec, "steps": T, "checkpoint_every": K,
+                     "force_passes": T + 1 + (T // K - 1) * (K - 1), "vjp_passes": T + 1}
+    out["adjoint_16384_mixed"]["grad_err_vs_fp64_gpu"] = {  # same dL/dx_T for both
+        nm: _err_stats(_elem_err(gm, g64)) for nm, gm, g64 in zip(("x0", "v0", "m"), grads[nb.MIXED], grads[nb.FP64])}
+    # central differences on the FP64 GPU path: one position, one velocity and one mass coordinate
     x, v, m = inputs.plummer(n, seed=5)
     t = torch.from_numpy(inputs.targets(n, seed=6)).to(dev)
+    rng = np.random.default_rng(7)
+    i_x, c_x, i_v, c_v, i_m = (int(rng.integers(n)), int(rng.integers(3)), int(rng.integers(n)), int(rng.integers(3)),
+                               int(rng.integers(n)))
+    h, copies = 1e-6, []
+    for sgn in (1.0, -1.0):
+        for kind in ("x", "v", "m"):
+            xx, vv, mm = x.copy(), v.copy(), m.copy()
+            if kind == "x":
+                xx[i_x, c_x] += sgn * h
+            elif kind == "v":
+                vv[i_v, c_v] += sgn * h
+            else:
+                mm[i_m] += sgn * h
+            copies.append((xx, vv, mm))
+    offs = [k_ * n for k_ in range(7)]
+    ctxb = nb.nbody_init(G=G, eps=eps, dt=dt, precision=nb.FP64, offsets=offs)
+    xb, vb, mb = (torch.from_numpy(np.concatenate([c[j] for c in copies])).to(dev) for j in range(3))
+    nb.nbody_step(ctxb, xb, vb, mb, torch.empty_like(xb), False, T)
+    nb.nbody_sync(ctxb)
+    ctxb.close()
+    xr = xb.view(6, n, 3)
+    dL = ((xr[0:3] - xr[3:6]) * (xr[0:3] + xr[3:6] - 2 * t)).sum(dim=(1, 2)).cpu().numpy()
+    fd = dL / (2 * h)
     for prec, name in ((nb.MIXED, "adjoint_16384_mixed"), (nb.FP64, "adjoint_16384_fp64")):
-        ctx = nb.nbody_init(G=1.0, eps=0.01, dt=1e-3, precision=prec, n=n)
-        xt, vt, mt = (torch.from_numpy(a).to(dev) for a in (x, v, m))
-        xs, vs, at = xt.clone(), vt.clone(), torch.empty_like(xt)
-        nb.nbody_step(ctx, xs, vs, mt, at, False, 200)
-        lam = 2 * (xs - t)
-        nb.nbody_adjoint(ctx, xt, vt, mt, 200, 20, lam, torch.zeros_like(vs))  # tunes the VJP tiling
-        sec = _event_time(lambda: nb.nbody_adjoint(ctx, xt, vt, mt, 200, 20, lam, torch.zeros_like(vs)), stream,
-                          f"aux_{name}")
-        nb.nbody_sync(ctx)
-        out[name] = {"seconds": sec, "steps": 200, "checkpoint_every": 20,
-                     "force_passes": 200 + 1 + (10 - 1) * (20 - 1), "vjp_passes": 201}
-        ctx.close()
+        gx, gv, gm = grads[prec]
+        ad = np.array([gx[i_x, c_x], gv[i_v, c_v], gm[i_m]])
+        out[name]["grad_err_vs_central_differences"] = {
+            "max": float((np.abs(ad - fd) / np.abs(fd)).max()), "coordinates": 3,
+            "note": "x, v and m coordinates of seeded bodies; FP64 GPU trajectories, h = 1e-6"}
+    # CPU reference adjoint (the oracle) at reduced N, beside the GPU adjoints at that N
+    n2 = 2048
+    x2, v2, m2 = inputs.plummer(n2, seed=5)
+    threads = oracle.default_threads()
+    lam2 = final_lam(n2)
+    _, g_mixed = run(n2, nb.MIXED, lam2)
+    _, g_fp64 = run(n2, nb.FP64, lam2)
+    lam2 = lam2.cpu().numpy()
+    (gref), t_or = _timed(lambda: oracle.adjoint(x2, v2, m2, G, eps, dt, T, lam2, np.zeros_like(lam2),
+                                                 threads=threads))
+    out["adjoint_reduced_n2048"] = {
+        "grad_err_vs_oracle": {
+            pname: {nm: _err_stats(_elem_err(g, r)) for nm, g, r in zip(("x0", "v0", "m"), gg, gref)}
+            for pname, gg in (("mixed", g_mixed), ("fp64", g_fp64))},
+        "cpu_baseline": {"value": t_or, "unit": "s", "cores": threads, "kind": "oracle",
+                         "sample": f"the CPU reference adjoint (full trajectory stored, FP64) at N = {n2}, {T} steps",
+                         "extrapolated_s_at_n16384": t_or * (16384 / n2) ** 2,
+                         "extrapolation": "extrapolated by N^2 from the reduced N"}}
+    return out
+
+
+def aux_measurements(dev):
+    """The other workloads, each measured briefly (rank 0, one GPU): CUDA-event times around
+    nbody_step / nbody_adjoint calls, initialisation and autotuning excluded; beside each throughput
+    its error against the FP64 oracle and the oracle's own (sampled, extrapolated) time."""
+    import torch
+    stream = torch.cuda.current_stream()
+    out = {"two_spheres_1m": aux_two_spheres(dev, stream)}
+    out["ensemble_512"] = aux_ensemble(dev, stream)
+    out["paper_lj_gas_10000x2500"] = aux_lj(dev, stream)
+    out.update(aux_adjoint(dev, stream))
     return out
 
 
@@ -463,10 +693,13 @@ def run_ours(args):
            "call": "nbody_step_host (1 KDK step per call, pinned host x, v, m, a in; x, v, a, energy out; "
                    "step replayed as a CUDA graph; L2 flushed between calls, outside the timing)"}
 
-    # ---- CPU oracle on this host (rank 0, N = 1 only), which also gives the force error
-    base, ferr = None, None
+    # ---- CPU oracle on this host (rank 0, N = 1 only), which also gives the force error, the
+    # energy error of the final state and the oracle's own energy drift beside the GPU's
+    base, ferr, eerr = None, None, None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         base, ferr = cpu_baseline(x, m, G, eps, a0)
+        eerr = energy_vs_oracle(nb, dev, x, v, m, G, eps, dt, xt.cpu().numpy(), vt.cpu().numpy(),
+                                float(elog[-1]))
     ctx.close()
     aux = None
     if rank == 0 and world == 1 and not args.no_aux:
@@ -490,6 +723,7 @@ def run_ours(args):
                 "mixed_over_fp64": value / world / fp64_value,
                 "force_err_vs_oracle": ferr,
                 "energy_drift_max_rel": drift,
+                "energy_vs_oracle": eerr,
                 "interactions_per_step": interactions,
             },
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s (FP32 pipe)",

@@ -51,7 +51,8 @@ typedef enum {
   NBODY_ECUDA = 3,      /* a CUDA runtime call failed (text in nbody_last_error) */
   NBODY_ETIMEOUT = 4,   /* a bounded device-side wait gave up */
   NBODY_ENONFINITE = 5, /* a non-finite acceleration or energy was produced */
-  NBODY_EUNSUPPORTED = 6 /* no sm_103a device / operation not available */
+  NBODY_EUNSUPPORTED = 6, /* no sm_103a device / operation not available */
+  NBODY_EINTERNAL = 7     /* NBODY_DEBUG builds: a device-side index check failed (the access was skipped) */
 } nbody_status;
 
 typedef enum {
@@ -245,8 +246,9 @@ int64_t nbody_launch_count(const nbody_ctx* ctx);
 
 /*
  * Largest body count nbody_forces_noalloc accepts. Its scratch is a fixed
- * 16 MiB + 256 B __device__ array (16 bytes per body), reserved on every GPU
- * that loads the library for the life of the process.
+ * 32 MiB + 256 B __device__ array (32 bytes per body: the float32 staging
+ * entry and the float32 remainders of the near-pair refinement), held on every
+ * GPU that loads the library's device code, for the life of the process.
  */
 #define NBODY_NOALLOC_MAX_BODIES 1048576
 
@@ -259,20 +261,34 @@ int64_t nbody_launch_count(const nbody_ctx* ctx);
  * The paper has no counterpart; this is a deployment convenience.
  *
  * x [n,3], m [n] (read), a [n,3] (written), phi [n] (written, nullable) are
- * device pointers on the current device; the work is queued on cuda_stream
- * (NULL = legacy default stream) and is asynchronous. Same pair arithmetic as
- * nbody_forces with NBODY_MIXED (float32 pairs, compensated float32 tile sums,
- * float64 result), but one CTA per i-tile and no j-slices, so results agree
- * with nbody_forces to rounding, not bit for bit.
+ * float64 device pointers on the current device, each holding at least that
+ * many elements (checked where the driver reports the allocation's extent);
+ * the work is queued on cuda_stream (NULL = legacy default stream) and is
+ * asynchronous. Same pair arithmetic as nbody_forces with NBODY_MIXED:
+ * float32 pairs with the near-pair refinement (pairs closer than 4 eps
+ * recomputed from the staged float32 remainders), compensated float32 tile
+ * sums, float64 result; the same error bounds against the float64 direct sum
+ * (median <= 1e-6, max <= 1e-4 relative per body). One CTA per i-tile and no
+ * j-slices, so results agree with nbody_forces to rounding, not bit for bit.
  *
  * Scratch is a static __device__ array shared by every call in the process:
  * calls that overlap on the GPU (different streams, or different host threads)
  * race on it and must be serialised by the caller. Each call overwrites
- * everything it reads, so no state carries over from an earlier call. The
- * first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call before
- * any stream capture. Returns NBODY_EINVAL for n > NBODY_NOALLOC_MAX_BODIES,
- * n < 0, bad pointers or parameters (message in nbody_last_error(NULL)).
+ * everything it reads, so no state carries over from an earlier call.
+ *
+ * The first call on a device is a warm-up: it looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current, which makes the
+ * CUDA runtime load the library's device code on that device if it has not
+ * yet, and loading reserves the 32 MiB array and the kernels' code there (it
+ * can fail with NBODY_ECUDA when the device is out of memory, and may
+ * synchronise). Make that first call before the region that must not
+ * allocate, and before any stream capture; later calls on that device
+ * allocate nothing. The looked-up address belongs to the device's current
+ * CUDA context: do not use the library across a cudaDeviceReset (which ends
+ * that context and invalidates every nbody_ctx as well).
+ *
+ * Returns NBODY_EINVAL for n > NBODY_NOALLOC_MAX_BODIES, n < 0, bad or short
+ * pointers or bad parameters (message in nbody_last_error(NULL)).
  */
 nbody_status nbody_forces_noalloc(const double* x, const double* m, int64_t n, double G, double eps, double* a,
                                   double* phi, void* cuda_stream);
@@ -285,6 +301,16 @@ void nbody_destroy(nbody_ctx* ctx);
 
 /* ABI version: (major << 16) | minor. */
 int32_t nbody_version(void);
+
+/*
+ * Build options of the loaded library, as bits: 1 = NBODY_DEBUG, a build
+ * whose kernels check every work item, chunk and per-system range they read
+ * against the buffers it indexes (body rows, partial-sum slices, chunk and
+ * system tables) before using it. A failed check skips the access and latches
+ * a device status bit that the next nbody_sync reports as NBODY_EINTERNAL. It
+ * stands in for a device memory checker; release builds return 0.
+ */
+int32_t nbody_build_flags(void);
 
 #ifdef __cplusplus
 }

@@ -27,18 +27,20 @@ __all__ = [
     "nbody_adjoint_params",
     "nbody_step_host",
     "nbody_sync", "nbody_get_tuning", "nbody_launch_count", "nbody_last_error", "nbody_destroy",
-    "nbody_version", "nbody_profile", "nbody_kernel_time", "nbody_forces_noalloc", "NOALLOC_MAX_BODIES",
+    "nbody_version", "nbody_build_flags", "nbody_profile", "nbody_kernel_time", "nbody_forces_noalloc", "NOALLOC_MAX_BODIES",
     "NBodyAdjoint", "ENERGY_FIELDS",
 ]
 
 FP64, MIXED = 0, 1
 GRAVITY, LENNARD_JONES = 0, 1
 FLAG_GRAPH, FLAG_NOCHECK = 1, 2
-STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "ENONFINITE", 6: "EUNSUPPORTED"}
+STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "ENONFINITE", 6: "EUNSUPPORTED",
+          7: "EINTERNAL"}
 ENERGY_FIELDS = ("E", "K", "U", "Px", "Py", "Pz", "Lx", "Ly", "Lz")
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_LIB_PATH = os.path.join(_HERE, "libnbody.so")
+# NBODY_DEBUG_LIB=1 selects the build with device-side index checks (build.build(debug=True))
+_LIB_PATH = os.path.join(_HERE, "libnbody_debug.so" if os.environ.get("NBODY_DEBUG_LIB") == "1" else "libnbody.so")
 _lib = None
 _lock = threading.Lock()
 
@@ -71,7 +73,8 @@ def load():
         if _lib is not None:
             return _lib
         if not os.path.exists(_LIB_PATH):
-            raise RuntimeError(f"libnbody.so not found at {_LIB_PATH}: run paper_2511_02655_gb300.build.build()")
+            raise RuntimeError(f"{os.path.basename(_LIB_PATH)} not found at {_LIB_PATH}: run "
+                               "paper_2511_02655_gb300.build.build()")
         try:  # let the library resolve the CUDA runtime torch already loaded
             import torch  # noqa: F401
         except Exception:
@@ -97,6 +100,7 @@ def load():
             "nbody_forces_noalloc": (i32, [p, p, i64, ctypes.c_double, ctypes.c_double, p, p, p]),
             "nbody_destroy": (None, [p]),
             "nbody_version": (i32, []),
+            "nbody_build_flags": (i32, []),
         }
         for name, (res, args) in sigs.items():
             f = getattr(lib, name)
@@ -107,6 +111,11 @@ def load():
 
 def nbody_version() -> int:
     return int(load().nbody_version())
+
+
+def nbody_build_flags() -> int:
+    """Build options of the loaded library (bit 0: NBODY_DEBUG device-side index checks)."""
+    return int(load().nbody_build_flags())
 
 
 def nbody_last_error(ctx=None) -> str:
@@ -359,22 +368,33 @@ def nbody_forces_noalloc(x, m, G, eps, a=None, phi=None):
     """Forces of one system through the allocation-free entry point (no context).
 
     For callers that cannot allocate device memory at this point: the library
-    uses a fixed static device array as scratch. Output tensors are allocated
-    here by torch only when not supplied. Calls overlapping on the GPU race on
-    the shared scratch.
+    uses a fixed static device array as scratch (the first call on a device
+    loads it; make that call early). Output tensors are allocated here by torch
+    only when not supplied. Calls overlapping on the GPU race on the shared
+    scratch.
     """
     torch = _torch()
     n = int(m.shape[0])
-    for t, name, shape in ((x, "x", (n, 3)), (m, "m", (n,))):
+
+    def check(t, name, shape):
         if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()
-                and tuple(t.shape) == shape):
-            raise ValueError(f"{name} must be a contiguous CUDA float64 tensor of shape {shape}")
+                and tuple(t.shape) == shape and t.device == x.device):
+            raise ValueError(f"{name} must be a contiguous CUDA float64 tensor of shape {shape} on {x.device}")
+
+    if not isinstance(x, torch.Tensor):
+        raise ValueError("x must be a CUDA tensor")
+    check(x, "x", (n, 3))
+    check(m, "m", (n,))
     if a is None:
         a = torch.empty((n, 3), dtype=torch.float64, device=x.device)
-    stream = torch.cuda.current_stream().cuda_stream
-    st = load().nbody_forces_noalloc(ctx_ptr(x.data_ptr()), ctx_ptr(m.data_ptr()), n, float(G), float(eps),
-                                     ctx_ptr(a.data_ptr()), ctx_ptr(phi.data_ptr()) if phi is not None else None,
-                                     ctx_ptr(stream))
+    check(a, "a", (n, 3))
+    if phi is not None:
+        check(phi, "phi", (n,))
+    stream = torch.cuda.current_stream(x.device).cuda_stream
+    with torch.cuda.device(x.device):
+        st = load().nbody_forces_noalloc(ctx_ptr(x.data_ptr()), ctx_ptr(m.data_ptr()), n, float(G), float(eps),
+                                         ctx_ptr(a.data_ptr()), ctx_ptr(phi.data_ptr()) if phi is not None else None,
+                                         ctx_ptr(stream))
     _check(st)
     return a, phi
 

@@ -1,6 +1,12 @@
 """Builds libnbody.so (sm_103a) in-tree with nvcc: one object per .cu file,
 compiled in parallel, then linked as a shared library with the shared CUDA
-runtime (so that it shares the runtime instance torch has loaded)."""
+runtime (so that it shares the runtime instance torch has loaded).
+
+build(debug=True) builds libnbody_debug.so instead: the same sources with
+NBODY_DEBUG defined, whose kernels check every work item, chunk and system
+range against the buffers it indexes (a failed check skips the access and is
+reported by nbody_sync as NBODY_EINTERNAL). The binding loads it when the
+environment variable NBODY_DEBUG_LIB is 1."""
 
 from __future__ import annotations
 
@@ -15,9 +21,11 @@ ROOT = os.path.dirname(HERE)
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libnbody.so")
 BUILD_DIR = os.path.join(HERE, "_build")
+DEBUG_LIB = os.path.join(HERE, "libnbody_debug.so")
+DEBUG_BUILD_DIR = os.path.join(HERE, "_build_debug")
 
 SOURCES = ["force_kernels.cu", "adjoint_kernels.cu", "post_kernels.cu", "capi.cu", "noalloc.cu"]
-HEADERS = ["nbody_internal.h", "pair_common.cuh"]
+HEADERS = ["nbody_internal.h", "pair_common.cuh", "post_common.cuh"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE,
@@ -38,16 +46,18 @@ def _newer(target: str, deps: list[str]) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
-    os.makedirs(BUILD_DIR, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False, debug: bool = False) -> str:
+    lib_out, build_dir = (DEBUG_LIB, DEBUG_BUILD_DIR) if debug else (LIB, BUILD_DIR)
+    os.makedirs(build_dir, exist_ok=True)
     nvcc = _nvcc()
     hdrs = [os.path.join(CSRC, h) for h in HEADERS] + [os.path.join(INCLUDE, "nbody.h")]
+    flags = NVCC_FLAGS + (["-DNBODY_DEBUG"] if debug else [])
     jobs = []
     for src in SOURCES:
         s = os.path.join(CSRC, src)
-        o = os.path.join(BUILD_DIR, src.replace(".cu", ".o"))
+        o = os.path.join(build_dir, src.replace(".cu", ".o"))
         if force or ptxas_info or _newer(o, [s] + hdrs):
-            cmd = [nvcc] + NVCC_FLAGS + (["-Xptxas", "-v"] if ptxas_info else []) + ["-c", s, "-o", o]
+            cmd = [nvcc] + flags + (["-Xptxas", "-v"] if ptxas_info else []) + ["-c", s, "-o", o]
             jobs.append(cmd)
 
     def run(cmd):
@@ -61,18 +71,19 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
                     sys.stderr.write(" ".join(cmd) + "\n" + r.stdout + r.stderr)
                 if r.returncode:
                     raise RuntimeError(f"nvcc failed for {cmd[-3]}")
-    objs = [os.path.join(BUILD_DIR, s.replace(".cu", ".o")) for s in SOURCES]
-    if force or jobs or _newer(LIB, objs):
-        tmp = LIB + f".tmp{os.getpid()}"
+    objs = [os.path.join(build_dir, s.replace(".cu", ".o")) for s in SOURCES]
+    if force or jobs or _newer(lib_out, objs):
+        tmp = lib_out + f".tmp{os.getpid()}"
         cmd = [nvcc] + ARCH + ["-shared", "-cudart", "shared", "-o", tmp] + objs + \
               ["-Xlinker", "-rpath,/usr/local/cuda/lib64"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode:
             sys.stderr.write(" ".join(cmd) + "\n" + r.stdout + r.stderr)
-            raise RuntimeError("link of libnbody.so failed")
-        os.replace(tmp, LIB)
-    return LIB
+            raise RuntimeError(f"link of {os.path.basename(lib_out)} failed")
+        os.replace(tmp, lib_out)
+    return lib_out
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose=True, ptxas_info="--ptxas" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose=True, ptxas_info="--ptxas" in sys.argv,
+                debug="--debug" in sys.argv))

@@ -13,8 +13,10 @@
 //   Pg = sum m_j (d.w_k) / s^3   (w_k . da_k/dG),
 //   Pe = sum m_j (d.w_k) / s^5   (w_k . da_k/deps = -3 G eps Pe),
 // cost two float32 operations more per pair and a third double4 per body and slice.
-// Tiling, work distribution, self-pair masking and the compensated per-tile
-// fold are those of the force kernels.
+// Tiling, work distribution, self-pair masking, the compensated per-tile fold
+// and the near-pair refinement (pairs with s^2 below r2_near recomputed from the
+// staged float32 remainders, found through a running minimum of s^2 per
+// sub-block of kSubV j-bodies) are those of the force kernels.
 #include <algorithm>
 #include <type_traits>
 
@@ -24,6 +26,8 @@
 namespace nbody {
 namespace {
 
+constexpr int kSubV = 32;  // j-bodies per near-pair check
+
 struct Acc8f {
   float a1x, a1y, a1z, a2, gbx, gby, gbz, gm, pg, pe;
 };
@@ -31,11 +35,13 @@ struct Acc8f {
 template <bool MASK, bool P>
 __device__ __forceinline__ void vjp_pair_f32(const float4 q, const float4 wj, const float xk, const float yk,
                                              const float zk, const float mk, const float wkx, const float wky,
-                                             const float wkz, const float eps2, Acc8f& s, const bool self) {
+                                             const float wkz, const float eps2, Acc8f& s, const bool self,
+                                             float& mn) {
   const float dx = q.x - xk;
   const float dy = q.y - yk;
   const float dz = q.z - zk;
   const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
+  mn = fminf(mn, r2);
   float inv = rsq_approx(r2);
   if (MASK) inv = self ? 0.f : inv;
   const float inv2 = inv * inv;
@@ -58,6 +64,60 @@ __device__ __forceinline__ void vjp_pair_f32(const float4 q, const float4 wj, co
   s.a1y = fmaf(inv3, wj.y, s.a1y);
   s.a1z = fmaf(inv3, wj.z, s.a1z);
   s.a2 = fmaf(q.w, inv3, s.a2);
+}
+
+// The VJP terms of one pair with separation d and s^2 = r2, scaled by sg
+// (+1 adds them, -1 removes them): the same operations as vjp_pair_f32 and
+// vjp_pair2, so that a removed unrefined term matches the one accumulated.
+template <bool P>
+__device__ __forceinline__ void vjp_terms_f32(const float dx, const float dy, const float dz, const float r2,
+                                              const float mj, const float wjx, const float wjy, const float wjz,
+                                              const float mk, const float wkx, const float wky, const float wkz,
+                                              const float sg, Acc8f& s) {
+  const float inv = rsq_approx(r2);
+  const float inv2 = inv * inv;
+  const float inv3 = inv2 * inv;
+  const float dwj = fmaf(dx, wjx, fmaf(dy, wjy, dz * wjz));
+  const float dwk = fmaf(dx, wkx, fmaf(dy, wky, dz * wkz));
+  const float pk = mj * dwk;
+  const float du = fmaf(mk, dwj, -pk);
+  const float inv5 = inv3 * inv2;
+  const float t = (du * inv5) * sg;
+  const float i3 = inv3 * sg;
+  s.gm = fmaf(dwj, i3, s.gm);
+  if (P) {
+    s.pg = fmaf(pk, i3, s.pg);
+    s.pe = fmaf(pk, inv5 * sg, s.pe);
+  }
+  s.gbx = fmaf(t, dx, s.gbx);
+  s.gby = fmaf(t, dy, s.gby);
+  s.gbz = fmaf(t, dz, s.gbz);
+  s.a1x = fmaf(i3, wjx, s.a1x);
+  s.a1y = fmaf(i3, wjy, s.a1y);
+  s.a1z = fmaf(i3, wjz, s.a1z);
+  s.a2 = fmaf(mj, i3, s.a2);
+}
+
+// Second look at one pair of a flagged sub-block (j-body at global index jg
+// with staged (q, m_j) and weight w_j, i-body k at ig): if it is near and not
+// the self pair, its unrefined terms in s are replaced by those of the
+// separation refined with the staged remainders (refine_pair).
+template <bool P>
+__device__ __forceinline__ void vjp_correct_f32(const float qx, const float qy, const float qz, const float mj,
+                                                const float wjx, const float wjy, const float wjz, const int jg,
+                                                const int ig, const int i_end, const float xk, const float yk,
+                                                const float zk, const float mk, const float wkx, const float wky,
+                                                const float wkz, const float eps2, const float r2c,
+                                                const float4* __restrict__ lo, Acc8f& s) {
+  const float dx = qx - xk;
+  const float dy = qy - yk;
+  const float dz = qz - zk;
+  const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
+  if (!(r2 < r2c) || ig >= i_end || jg < 0 || ig == jg) return;
+  float rx, ry, rz, rr2;
+  refine_pair(lo, ig, jg, dx, dy, dz, eps2, rx, ry, rz, rr2);
+  vjp_terms_f32<P>(dx, dy, dz, r2, mj, wjx, wjy, wjz, mk, wkx, wky, wkz, -1.f, s);
+  vjp_terms_f32<P>(rx, ry, rz, rr2, mj, wjx, wjy, wjz, mk, wkx, wky, wkz, 1.f, s);
 }
 
 struct Acc8d {
@@ -106,11 +166,14 @@ __global__ void __launch_bounds__(BLOCK) k_vjp_mixed(const PairLaunch L) {
   const float4* __restrict__ sw = static_cast<const float4*>(L.stage_w);
   double4_32a* __restrict__ part = reinterpret_cast<double4_32a*>(L.part);
   const float eps2 = (float)L.eps2;
+  const float r2c = L.r2_near;
+  const float4* __restrict__ slo = L.stage_lo;
 
   for (;;) {
     const int it = next_item(L.counter, &s_item);
     if (it >= L.n_items) break;
     const WorkItem w = L.items[it];
+    if (!item_ok(w, L)) continue;  // NBODY_DEBUG builds only
 
     float xk[R], yk[R], zk[R], mk[R], wkx[R], wky[R], wkz[R];
     Acc8f hi[R], lo[R];
@@ -154,21 +217,35 @@ __global__ void __launch_bounds__(BLOCK) k_vjp_mixed(const PairLaunch L) {
 #pragma unroll
       for (int r = 0; r < R; ++r) s[r] = Acc8f{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
       const bool diag = (jt < w.i_end) && (w.i_begin < jt + nj);
-      if (diag) {
-        for (int j = 0; j < nj; ++j) {
-          const float4 q = tx[j], u = tw[j];
+      for (int jb = 0; jb < nj; jb += kSubV) {
+        const int je = min(nj, jb + kSubV);
+        float mn = 3.0e38f;
+        if (diag) {
+          for (int j = jb; j < je; ++j) {
+            const float4 q = tx[j], u = tw[j];
 #pragma unroll
-          for (int r = 0; r < R; ++r)
-            vjp_pair_f32<true, P>(q, u, xk[r], yk[r], zk[r], mk[r], wkx[r], wky[r], wkz[r], eps2, s[r],
-                               jt + j == ig[r]);
-        }
-      } else {
+            for (int r = 0; r < R; ++r)
+              vjp_pair_f32<true, P>(q, u, xk[r], yk[r], zk[r], mk[r], wkx[r], wky[r], wkz[r], eps2, s[r],
+                                    jt + j == ig[r], mn);
+          }
+        } else {
 #pragma unroll 4
-        for (int j = 0; j < nj; ++j) {
-          const float4 q = tx[j], u = tw[j];
+          for (int j = jb; j < je; ++j) {
+            const float4 q = tx[j], u = tw[j];
 #pragma unroll
-          for (int r = 0; r < R; ++r)
-            vjp_pair_f32<false, P>(q, u, xk[r], yk[r], zk[r], mk[r], wkx[r], wky[r], wkz[r], eps2, s[r], false);
+            for (int r = 0; r < R; ++r)
+              vjp_pair_f32<false, P>(q, u, xk[r], yk[r], zk[r], mk[r], wkx[r], wky[r], wkz[r], eps2, s[r], false,
+                                     mn);
+          }
+        }
+        if (mn < r2c) {
+          for (int j = jb; j < je; ++j) {
+            const float4 q = tx[j], u = tw[j];
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+              vjp_correct_f32<P>(q.x, q.y, q.z, q.w, u.x, u.y, u.z, jt + j, ig[r], w.i_end, xk[r], yk[r], zk[r],
+                                 mk[r], wkx[r], wky[r], wkz[r], eps2, r2c, slo, s[r]);
+          }
         }
       }
 #pragma unroll
@@ -223,6 +300,7 @@ __global__ void __launch_bounds__(BLOCK) k_vjp_fp64(const PairLaunch L) {
     const int it = next_item(L.counter, &s_item);
     if (it >= L.n_items) break;
     const WorkItem w = L.items[it];
+    if (!item_ok(w, L)) continue;  // NBODY_DEBUG builds only
 
     double xk[R], yk[R], zk[R], mk[R], wkx[R], wky[R], wkz[R];
     Acc8d s[R];
@@ -310,11 +388,12 @@ __device__ __forceinline__ void vjp_pair2(const float2 xj, const float2 yj, cons
                                           const float2 wxj, const float2 wyj, const float2 wzj, const int jg0,
                                           const int ig, const float2 nx, const float2 ny, const float2 nz,
                                           const float2 mk, const float2 wkx, const float2 wky, const float2 wkz,
-                                          const float2 e2, Acc2& s) {
+                                          const float2 e2, Acc2& s, float& mn) {
   const float2 dx = __fadd2_rn(xj, nx);
   const float2 dy = __fadd2_rn(yj, ny);
   const float2 dz = __fadd2_rn(zj, nz);
   const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __ffma2_rn(dz, dz, e2)));
+  mn = fminf(mn, fminf(r2.x, r2.y));
   float2 inv = make_float2(rsq_approx(r2.x), rsq_approx(r2.y));
   if (MASK) {
     inv.x = (jg0 == ig) ? 0.f : inv.x;
@@ -358,6 +437,8 @@ __global__ void __launch_bounds__(BLOCK) k_vjp_mixed2(const PairLaunch L) {
   double4_32a* __restrict__ part = reinterpret_cast<double4_32a*>(L.part);
   const float eps2 = (float)L.eps2;
   const float2 e2 = make_float2(eps2, eps2);
+  const float r2c = L.r2_near;
+  const float4* __restrict__ slo = L.stage_lo;
 
   auto put = [&](const int b, const int t, const float4 q, const float4 u) {
     tx[b][t] = q.x, ty[b][t] = q.y, tz[b][t] = q.z, tmn[b][t] = -q.w;
@@ -372,6 +453,7 @@ __global__ void __launch_bounds__(BLOCK) k_vjp_mixed2(const PairLaunch L) {
     const int it = next_item(L.counter, &s_item);
     if (it >= L.n_items) break;
     const WorkItem w = L.items[it];
+    if (!item_ok(w, L)) continue;  // NBODY_DEBUG builds only
 
     float2 nx[R], ny[R], nz[R], mk[R], wkx[R], wky[R], wkz[R];
     float hi[R][NC], lo[R][NC];
@@ -423,7 +505,7 @@ __global__ void __launch_bounds__(BLOCK) k_vjp_mixed2(const PairLaunch L) {
       const bool diag = (jt < w.i_end) && (w.i_begin < jt + nj);
       const float *cx = tx[buf], *cy = ty[buf], *cz = tz[buf], *cm = tmn[buf];
       const float *cwx = twx[buf], *cwy = twy[buf], *cwz = twz[buf];
-      auto quad = [&](const int j, auto mask) {
+      auto quad = [&](const int j, auto mask, float& mn) {
         constexpr bool M = decltype(mask)::value;
         const float4 X = *reinterpret_cast<const float4*>(cx + j);
         const float4 Y = *reinterpret_cast<const float4*>(cy + j);
@@ -437,18 +519,47 @@ __global__ void __launch_bounds__(BLOCK) k_vjp_mixed2(const PairLaunch L) {
           vjp_pair2<M, P>(make_float2(X.x, X.y), make_float2(Y.x, Y.y), make_float2(Z.x, Z.y),
                           make_float2(Mn.x, Mn.y), make_float2(WX.x, WX.y), make_float2(WY.x, WY.y),
                           make_float2(WZ.x, WZ.y), jt + j, ig[r], nx[r], ny[r], nz[r], mk[r], wkx[r], wky[r],
-                          wkz[r], e2, s[r]);
+                          wkz[r], e2, s[r], mn);
           vjp_pair2<M, P>(make_float2(X.z, X.w), make_float2(Y.z, Y.w), make_float2(Z.z, Z.w),
                           make_float2(Mn.z, Mn.w), make_float2(WX.z, WX.w), make_float2(WY.z, WY.w),
                           make_float2(WZ.z, WZ.w), jt + j + 2, ig[r], nx[r], ny[r], nz[r], mk[r], wkx[r], wky[r],
-                          wkz[r], e2, s[r]);
+                          wkz[r], e2, s[r], mn);
         }
       };
-      if (diag) {
-        for (int j = 0; j < nj4; j += 4) quad(j, std::true_type{});
-      } else {
+      // near-pair corrections of one j-body of the tile for every i-body of the thread,
+      // added to lane 0 of the packed sums (the lanes are added at the fold; A2, Pg, Pe
+      // are held negated)
+      auto correct = [&](const int j) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          Acc8f d{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+          vjp_correct_f32<P>(cx[j], cy[j], cz[j], -cm[j], cwx[j], cwy[j], cwz[j], jt + j, ig[r], w.i_end, -nx[r].x,
+                             -ny[r].x, -nz[r].x, mk[r].x, wkx[r].x, wky[r].x, wkz[r].x, eps2, r2c, slo, d);
+          s[r].a1x.x += d.a1x, s[r].a1y.x += d.a1y, s[r].a1z.x += d.a1z, s[r].a2n.x -= d.a2;
+          s[r].gbx.x += d.gbx, s[r].gby.x += d.gby, s[r].gbz.x += d.gbz, s[r].gm.x += d.gm;
+          if (P) s[r].pgn.x -= d.pg, s[r].pen.x -= d.pe;
+        }
+      };
+      // first pass: one bit per sub-block whose minimum s^2 fell below the radius; the
+      // flagged sub-blocks are revisited after the whole tile (fewer live registers in
+      // the pair loop than a rescan inside it)
+      static_assert(J / kSubV <= 32, "one flag bit per sub-block of a tile");
+      unsigned flagged = 0u;
+      for (int jb = 0; jb < nj4; jb += kSubV) {
+        const int je = min(nj4, jb + kSubV);
+        float mn = 3.0e38f;
+        if (diag) {
+          for (int j = jb; j < je; j += 4) quad(j, std::true_type{}, mn);
+        } else {
 #pragma unroll 2
-        for (int j = 0; j < nj4; j += 4) quad(j, std::false_type{});
+          for (int j = jb; j < je; j += 4) quad(j, std::false_type{}, mn);
+        }
+        if (mn < r2c) flagged |= 1u << (jb / kSubV);
+      }
+      while (flagged) {
+        const int jb = (__ffs(flagged) - 1) * kSubV;
+        flagged &= flagged - 1u;
+        for (int j = jb; j < min(jb + kSubV, nj); ++j) correct(j);
       }
 #pragma unroll
       for (int r = 0; r < R; ++r) {

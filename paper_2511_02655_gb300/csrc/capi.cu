@@ -31,6 +31,7 @@ constexpr size_t kMaxPartialBytes = size_t(1) << 30;  // cap on per-slice partia
 constexpr int kMinTilesPerSlice = 1;  // shortest slice in j-tiles (small systems need many items)
 constexpr double kTuneLargePairs = 4.0e10;  // above this many pairs per force pass, tune on short slices
 constexpr int kTuneSlice = 8192;
+constexpr int kSliceQuantum = 4;  // slice lengths are multiples of this many bodies
 
 struct Tiling {
   int block = 0, ipt = 0, jtile = 0, slice = 0, n_ctas = 0;
@@ -86,6 +87,17 @@ void load_addr_range() {
 namespace nbody {
 // Error text reported by nbody_last_error(NULL), for entry points without a context.
 void set_global_error_text(const char* msg) { set_global_error(msg); }
+
+bool allocation_holds(const void* p, size_t bytes, size_t* avail) {
+  load_addr_range();
+  if (!g_addr_range) return true;
+  CUdeviceptr base = 0;
+  size_t size = 0;
+  if (g_addr_range(&base, &size, reinterpret_cast<CUdeviceptr>(p)) != CUDA_SUCCESS) return true;
+  const uintptr_t end = static_cast<uintptr_t>(base) + size, at = reinterpret_cast<uintptr_t>(p);
+  if (avail) *avail = end > at ? static_cast<size_t>(end - at) : 0;
+  return at + bytes <= end;
+}
 }  // namespace nbody
 
 struct nbody_ctx {
@@ -115,6 +127,8 @@ struct nbody_ctx {
   WorkItem* d_items = nullptr;
   int n_items = 0;
   int max_slices = 1;
+  int n_tiles = 0;                // (system, i-range) tiles of the force work list
+  int32_t* d_sys_tile = nullptr;  // [n_sys + 1] tile range of each system
   // VJP work list (built on first adjoint)
   Tiling vt;
   WorkItem* d_vitems = nullptr;
@@ -125,8 +139,10 @@ struct nbody_ctx {
   bool nvtx = false;        // NBODY_NVTX=1: NVTX ranges around the API calls and the adjoint's phases
   bool vjp_params = false;  // VJP launches also form the G and eps gradient sums
 
-  // scratch
+  // scratch (stage_alt, stage_lo_alt: the second staging buffers of the fused
+  // step, which stages step k+1 while step k's force kernel still reads step k's)
   DevBuf stage, stage_lo, stage_w, part, centre, epart, status_counter, a_scratch;
+  DevBuf stage_alt, stage_lo_alt, tile_done, tpart;
   unsigned* counter = nullptr;  // [2]
   unsigned* status = nullptr;   // [1]
 
@@ -233,17 +249,9 @@ nbody_status check_dev(nbody_ctx* c, const void* p, size_t bytes, const char* na
     return fail(c, NBODY_EINVAL, "%s is not device memory", name);
   if (at.type == cudaMemoryTypeDevice && at.device != c->device)
     return fail(c, NBODY_EINVAL, "%s lives on device %d, context on device %d", name, at.device, c->device);
-  load_addr_range();
-  if (g_addr_range) {
-    CUdeviceptr base = 0;
-    size_t size = 0;
-    if (g_addr_range(&base, &size, reinterpret_cast<CUdeviceptr>(p)) == CUDA_SUCCESS) {
-      const uintptr_t end = reinterpret_cast<uintptr_t>(p) + bytes;
-      if (end > static_cast<uintptr_t>(base) + size)
-        return fail(c, NBODY_EINVAL, "%s: %zu bytes needed, allocation holds %zu from that address", name, bytes,
-                    static_cast<size_t>(static_cast<uintptr_t>(base) + size - reinterpret_cast<uintptr_t>(p)));
-    }
-  }
+  size_t avail = 0;
+  if (!allocation_holds(p, bytes, &avail))
+    return fail(c, NBODY_EINVAL, "%s: %zu bytes needed, allocation holds %zu from that address", name, bytes, avail);
   return NBODY_OK;
 }
 
@@ -288,7 +296,7 @@ int64_t count_items(const nbody_ctx* c, const Tiling& t, int64_t L) {
     if (n <= 0) continue;
     int64_t ns = (n + L - 1) / L;
     int64_t len = (n + ns - 1) / ns;
-    len = ((len + t.jtile - 1) / t.jtile) * t.jtile;
+    len = ((len + kSliceQuantum - 1) / kSliceQuantum) * kSliceQuantum;
     ns = (n + len - 1) / len;
     items += ((n + itile - 1) / itile) * ns;
   }
@@ -296,22 +304,26 @@ int64_t count_items(const nbody_ctx* c, const Tiling& t, int64_t L) {
 }
 
 void build_items(const nbody_ctx* c, const Tiling& t, std::vector<WorkItem>& items, std::vector<int>& sys_slices,
-                 int& max_slices) {
+                 int& max_slices, std::vector<int32_t>* sys_tile = nullptr) {
   items.clear();
   sys_slices.assign(c->n_sys, 1);
   max_slices = 1;
   const int64_t itile = (int64_t)t.block * t.ipt;
+  int32_t tile = 0;
+  if (sys_tile) sys_tile->assign(c->n_sys + 1, 0);
   for (int s = 0; s < c->n_sys; ++s) {
     const int64_t b = c->offsets[s], n = c->offsets[s + 1] - b;
+    if (sys_tile) (*sys_tile)[s] = tile;
     if (n <= 0) continue;
     int64_t ns = (n + t.slice - 1) / t.slice;
-    // balance the slices, each a multiple of the j-tile
+    // balance the slices (lengths a multiple of four: whole quads of the packed kernels'
+    // tiles; a slice's last j-tile may be partial)
     int64_t len = (n + ns - 1) / ns;
-    len = ((len + t.jtile - 1) / t.jtile) * t.jtile;
+    len = ((len + kSliceQuantum - 1) / kSliceQuantum) * kSliceQuantum;
     ns = (n + len - 1) / len;
     sys_slices[s] = (int)ns;
     max_slices = std::max(max_slices, (int)ns);
-    for (int64_t i0 = 0; i0 < n; i0 += itile) {
+    for (int64_t i0 = 0; i0 < n; i0 += itile, ++tile) {
       for (int64_t k = 0; k < ns; ++k) {
         WorkItem w;
         w.sys = s;
@@ -320,10 +332,13 @@ void build_items(const nbody_ctx* c, const Tiling& t, std::vector<WorkItem>& ite
         w.j_begin = (int32_t)(b + k * len);
         w.j_end = (int32_t)(b + std::min(n, (k + 1) * len));
         w.slice = (int32_t)k;
+        w.tile = tile;
+        w.n_slices = (int32_t)ns;
         items.push_back(w);
       }
     }
   }
+  if (sys_tile) (*sys_tile)[c->n_sys] = tile;
   // longest-processing-time-first order for the dynamic persistent schedule
   std::stable_sort(items.begin(), items.end(), [](const WorkItem& a, const WorkItem& b) {
     const int64_t ca = (int64_t)(a.i_end - a.i_begin) * (a.j_end - a.j_begin);
@@ -373,16 +388,35 @@ nbody_status install_tiling(nbody_ctx* c, Tiling t, bool vjp) {
     return fail(c, NBODY_EINVAL, "unsupported tiling block=%d ipt=%d jtile=%d variant=%d", t.block, t.ipt, t.jtile,
                 t.variant);
   if (t.slice <= 0) t.slice = auto_slice(c, t, occ * c->sm_count);
-  t.slice = std::max(t.jtile, (t.slice / t.jtile) * t.jtile);
+  t.slice = std::max(kSliceQuantum, (t.slice / kSliceQuantum) * kSliceQuantum);
   std::vector<WorkItem> items;
   std::vector<int> sys_slices;
+  std::vector<int32_t> sys_tile;
   int max_slices = 1;
-  build_items(c, t, items, sys_slices, max_slices);
+  build_items(c, t, items, sys_slices, max_slices, &sys_tile);
   t.n_ctas = std::max(1, std::min<int>(occ * c->sm_count, (int)std::max<size_t>(1, items.size())));
   nbody_status s = upload_items(c, items, vjp ? &c->d_vitems : &c->d_items);
   if (s) return s;
   s = upload_chunks(c, sys_slices, vjp ? &c->d_vchunks : &c->d_chunks);
   if (s) return s;
+  if (!vjp) {
+    // tile tables of the fused step epilogue: tickets (zero between launches) and energy partials
+    const int n_tiles = sys_tile.back();
+    if ((s = ensure(c, c->tile_done, (size_t)std::max(1, n_tiles) * sizeof(unsigned))) ||
+        (s = ensure(c, c->tpart, (size_t)std::max(1, n_tiles) * kEnergyVals * sizeof(double))))
+      return s;
+    NB_CUDA(c, cudaMemset(c->tile_done.p, 0, (size_t)std::max(1, n_tiles) * sizeof(unsigned)));
+    if (!c->d_sys_tile) {
+      if (cudaMalloc(&c->d_sys_tile, (size_t)(c->n_sys + 1) * sizeof(int32_t)) != cudaSuccess) {
+        cudaGetLastError();
+        c->d_sys_tile = nullptr;
+        return fail(c, NBODY_ENOMEM, "cudaMalloc of the tile table failed");
+      }
+    }
+    NB_CUDA(c, cudaMemcpy(c->d_sys_tile, sys_tile.data(), sys_tile.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    NB_CUDA(c, cudaDeviceSynchronize());
+    c->n_tiles = n_tiles;
+  }
   const size_t per = vjp ? 64 : 32;
   s = ensure(c, c->part, (size_t)max_slices * (size_t)c->n_total * per);
   if (s) return s;
@@ -394,10 +428,10 @@ nbody_status install_tiling(nbody_ctx* c, Tiling t, bool vjp) {
   return NBODY_OK;
 }
 
-// refine: the mixed force kernel may use the staged remainders (near pairs).
-PairLaunch pair_launch(nbody_ctx* c, bool vjp, bool refine = false, bool phi = true) {
+// refine: the mixed force and VJP kernels may use the staged remainders (near pairs).
+PairLaunch pair_launch(nbody_ctx* c, bool vjp, bool refine = true, bool phi = true) {
   PairLaunch L{};
-  const bool lo = refine && !vjp && c->cfg.precision == NBODY_MIXED && c->stage_lo.p;
+  const bool lo = refine && c->cfg.precision == NBODY_MIXED && c->stage_lo.p;
   L.stage_lo = lo ? static_cast<const float4*>(c->stage_lo.p) : nullptr;
   L.law = vjp ? 0 : c->cfg.law;
   L.sigma2 = c->cfg.lj_sigma * c->cfg.lj_sigma;
@@ -419,7 +453,23 @@ PairLaunch pair_launch(nbody_ctx* c, bool vjp, bool refine = false, bool phi = t
   L.variant = t.variant;
   L.params = vjp && c->vjp_params ? 1 : 0;
   L.phi = phi ? 1 : 0;
+  L.status = c->status;
+  L.block_bodies = t.block * t.ipt;
+  L.fuse = 0;
+  L.tile_done = static_cast<unsigned*>(c->tile_done.p);
+  L.tpart = static_cast<double*>(c->tpart.p);
+  L.sys_tile = c->d_sys_tile;
+  L.n_tiles = c->n_tiles;
+  L.fin_done = c->counter + 7;
+  const size_t per = vjp ? (L.params ? 96 : 64) : 32;  // partial-sum bytes per body and slice
+  L.part_slices = c->n_total > 0 ? (int32_t)std::min<size_t>(INT32_MAX, c->part.bytes / ((size_t)c->n_total * per)) : 0;
   return L;
+}
+
+// Slices of float64 partials (bytes_per_body each) the partial-sum buffer holds.
+int32_t part_slices(const nbody_ctx* c, size_t bytes_per_body) {
+  if (c->n_total <= 0) return 0;
+  return (int32_t)std::min<size_t>(INT32_MAX, c->part.bytes / ((size_t)c->n_total * bytes_per_body));
 }
 
 cudaEvent_t pooled_event(nbody_ctx* c) {
@@ -440,14 +490,14 @@ cudaEvent_t pooled_event(nbody_ctx* c) {
 // eager (non-capturing) stream.
 nbody_status run_pair(nbody_ctx* c, cudaStream_t st, bool vjp, bool phi = true) {
   if (c->n_total == 0) return NBODY_OK;
-  PairLaunch L = pair_launch(c, vjp, !vjp, phi);
+  PairLaunch L = pair_launch(c, vjp, true, phi);
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (c->profiling && !c->capturing) {
     e0 = pooled_event(c);
     e1 = pooled_event(c);
     if (e0 && e1) NB_CUDA(c, cudaEventRecord(e0, st));
   }
-  NB_CUDA(c, vjp ? launch_vjp(c->cfg.precision, L, st) : launch_force(c->cfg.precision, L, st));
+  NB_CUDA(c, vjp ? launch_vjp(c->cfg.precision, L, st) : launch_force(c->cfg.precision, L, nullptr, st));
   if (e0 && e1) {
     NB_CUDA(c, cudaEventRecord(e1, st));
     c->ev_used.push_back({vjp ? 1 : 0, {e0, e1}});
@@ -459,6 +509,31 @@ nbody_status run_pair(nbody_ctx* c, cudaStream_t st, bool vjp, bool phi = true) 
 // phi: whether the potential is needed (an energy record, a phi output); only
 // the packed mixed kernel can skip it, the others always form it.
 nbody_status run_force(nbody_ctx* c, cudaStream_t st, bool phi) { return run_pair(c, st, false, phi); }
+
+// One force pass with the fused step epilogue: the force kernel reads the
+// staging buffers (stage_x, stage_lo) and its epilogue runs P's O(N) work,
+// staging the next positions into P.stage / P.stage_lo (the other buffers).
+nbody_status run_force_fused(nbody_ctx* c, cudaStream_t st, bool phi, const void* stage_x, const void* stage_lo,
+                             const PostLaunch& P) {
+  if (c->n_total == 0) return NBODY_OK;
+  PairLaunch L = pair_launch(c, false, true, phi);
+  L.stage_x = stage_x;
+  if (L.stage_lo) L.stage_lo = static_cast<const float4*>(stage_lo);
+  L.fuse = 1;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (c->profiling && !c->capturing) {
+    e0 = pooled_event(c);
+    e1 = pooled_event(c);
+    if (e0 && e1) NB_CUDA(c, cudaEventRecord(e0, st));
+  }
+  NB_CUDA(c, launch_force(c->cfg.precision, L, &P, st));
+  if (e0 && e1) {
+    NB_CUDA(c, cudaEventRecord(e1, st));
+    c->ev_used.push_back({0, {e0, e1}});
+  }
+  ++c->launches;
+  return NBODY_OK;
+}
 nbody_status run_vjp(nbody_ctx* c, cudaStream_t st) { return run_pair(c, st, true); }
 
 PostLaunch post_launch(nbody_ctx* c, unsigned mode, double* x, double* v, const double* m, double* a, double* phi) {
@@ -486,6 +561,7 @@ PostLaunch post_launch(nbody_ctx* c, unsigned mode, double* x, double* v, const 
   P.sys_chunk = c->d_sys_chunk;
   P.n_sys = c->n_sys;
   P.done = c->counter + 4;
+  P.part_slices = part_slices(c, 32);
   return P;
 }
 
@@ -499,7 +575,8 @@ nbody_status run_post(nbody_ctx* c, const PostLaunch& P, cudaStream_t st) {
 nbody_status run_centre(nbody_ctx* c, const double* x, const double* m, cudaStream_t st) {
   if (c->cfg.precision != NBODY_MIXED || c->n_total == 0) return NBODY_OK;
   NB_CUDA(c, launch_centre(c->d_chunks, (int)c->chunks.size(), c->d_sys_chunk, c->d_off, c->n_sys, x, m,
-                           static_cast<double*>(c->epart.p), static_cast<double*>(c->centre.p), c->counter + 5, st));
+                           static_cast<double*>(c->epart.p), static_cast<double*>(c->centre.p), c->counter + 5,
+                           c->n_total, c->status, st));
   c->launches += c->chunks.empty() ? 0 : 1;
   return NBODY_OK;
 }
@@ -516,18 +593,24 @@ nbody_status enqueue_step(nbody_ctx* c, double* x, double* v, const double* m, d
     if ((s = run_post(c, post_launch(c, kCombine, x, v, m, a, nullptr), st))) return s;
   }
   if (n_steps == 0) return NBODY_OK;
+  // Step k's force kernel reads staging buffer k % 2 while its fused epilogue
+  // (combine, closing half-kick, energy record, opening half-kick and drift of
+  // step k+1) stages the new positions into the other one.
+  void* const hi_buf[2] = {c->stage.p, c->stage_alt.p};
+  void* const lo_buf[2] = {c->stage_lo.p, c->stage_lo.p ? c->stage_lo_alt.p : nullptr};
   if ((s = run_post(c, post_launch(c, kDrift | kStage, x, v, m, a, nullptr), st))) return s;
   const int every = c->cfg.energy_every;
   int rec = 0;
   for (int k = 0; k < n_steps; ++k) {
     const bool rec_now = elog && every > 0 && (k + 1) % every == 0;
-    if ((s = run_force(c, st, rec_now))) return s;
     unsigned mode = kCombine | kKickEnd;
     if (rec_now) mode |= kEnergy;
     if (k + 1 < n_steps) mode |= kDrift | kStage;
     PostLaunch P = post_launch(c, mode, x, v, m, a, nullptr);
+    P.stage = hi_buf[(k + 1) & 1];
+    P.stage_lo = lo_buf[(k + 1) & 1];
     if (rec_now) P.eout = elog + (int64_t)rec++ * c->n_sys * 9;
-    if ((s = run_post(c, P, st))) return s;
+    if ((s = run_force_fused(c, st, rec_now, hi_buf[k & 1], lo_buf[k & 1], P))) return s;
   }
   return NBODY_OK;
 }
@@ -614,10 +697,10 @@ nbody_status fill_synthetic(nbody_ctx* c, bool with_w) {
 // slices pay for their partial-sum traffic and the tail of the schedule
 // counts; long lists are timed on a prefix of two items per persistent CTA.
 nbody_status time_tiling(nbody_ctx* c, bool vjp, double* cost) {
-  PairLaunch L = pair_launch(c, vjp, !vjp);
+  PairLaunch L = pair_launch(c, vjp);
   const Tiling& t = vjp ? c->vt : c->ft;
   auto launch = [&](const PairLaunch& P) {
-    return vjp ? launch_vjp(c->cfg.precision, P, c->stream) : launch_force(c->cfg.precision, P, c->stream);
+    return vjp ? launch_vjp(c->cfg.precision, P, c->stream) : launch_force(c->cfg.precision, P, nullptr, c->stream);
   };
   PostLaunch C{};
   C.chunks = vjp ? c->d_vchunks : c->d_chunks;
@@ -628,6 +711,8 @@ nbody_status time_tiling(nbody_ctx* c, bool vjp, double* cost) {
   C.a = static_cast<double*>(c->a_scratch.p);
   C.mode = kCombine;
   C.status = c->status;
+  C.n_sys = c->n_sys;
+  C.part_slices = part_slices(c, vjp ? 64 : 32);
   cudaEvent_t ev[4];
   for (auto& e : ev) NB_CUDA(c, cudaEventCreate(&e));
   auto timed = [&](const PairLaunch& P, bool combine, float* best_ms) -> cudaError_t {
@@ -825,28 +910,43 @@ nbody_status autotune(nbody_ctx* c, bool vjp) {
   Tiling bt = timed[0].second;
   for (size_t k = 1; k < top; ++k)
     if (timed[k].first < best) best = timed[k].first, bt = timed[k].second;
-  // slice-length refinement around the automatic choice for the best tiling
+  // slice-length refinement for the best tiling: the automatic choice, half and
+  // twice it, and (one system) the lengths whose work list fills a whole number
+  // of waves of the persistent grid (equal items, a multiple of the CTA count,
+  // leave no CTA idle at the end of the launch); each timed twice, interleaved
   if (!vjp && g.slice == 0 && !large) {
     Tiling base = bt;
     base.slice = 0;
     if ((s = install_tiling(c, base, vjp))) return s;
     const int L0 = c->ft.slice;
-    double bc = 1e300;
-    int bl = L0;
-    double lc[3] = {1e300, 1e300, 1e300};
-    const int ls[3] = {L0 / 2, L0, L0 * 2};
+    const int64_t n_ctas = c->ft.n_ctas;
+    std::vector<int> ls = {L0 / 2, L0, L0 * 2};
+    if (c->n_sys == 1) {
+      const int64_t n = c->offsets[1], tiles = (n + (int64_t)base.block * base.ipt - 1) / ((int64_t)base.block * base.ipt);
+      for (int64_t W = 1; W <= 64 && ls.size() < 7; ++W) {
+        const int64_t ns = W * n_ctas / tiles;  // slices per tile with tiles x ns <= W x CTAs
+        if (ns < 1 || (double)(tiles * ns) < 0.98 * (double)(W * n_ctas)) continue;
+        int64_t len = (n + ns - 1) / ns;
+        len = ((len + kSliceQuantum - 1) / kSliceQuantum) * kSliceQuantum;
+        if ((n + len - 1) / len != ns || len < L0 / 4 || len > 4 * (int64_t)L0) continue;
+        if (std::find(ls.begin(), ls.end(), (int)len) == ls.end()) ls.push_back((int)len);
+      }
+    }
+    std::vector<double> lc(ls.size(), 1e300);
     for (int round = 0; round < 2; ++round)  // two interleaved timings each, the best kept
-      for (int k = 0; k < 3; ++k) {
-        if (ls[k] < base.jtile * kMinTilesPerSlice) continue;
+      for (size_t k = 0; k < ls.size(); ++k) {
+        if (ls[k] < kSliceQuantum) continue;
         Tiling t = base;
         t.slice = ls[k];
         if ((s = install_tiling(c, t, vjp))) return s;
         double cost = 0;
         if ((s = time_tiling(c, vjp, &cost))) return s;
-        if (verbose) fprintf(stderr, "nbody tune slice=%d -> %.4g ps/pair\n", ls[k], cost * 1e12);
+        if (verbose) fprintf(stderr, "nbody tune slice=%d items=%d -> %.4g ps/pair\n", ls[k], c->n_items, cost * 1e12);
         lc[k] = std::min(lc[k], cost);
       }
-    for (int k = 0; k < 3; ++k)
+    double bc = 1e300;
+    int bl = L0;
+    for (size_t k = 0; k < ls.size(); ++k)
       if (lc[k] < bc) bc = lc[k], bl = ls[k];
     bt = base;
     bt.slice = bl;
@@ -891,8 +991,10 @@ void free_ctx(nbody_ctx* c) {
   for (auto& u : c->ev_used) cudaEventDestroy(u.second.first), cudaEventDestroy(u.second.second);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   for (DevBuf* b : {&c->stage, &c->stage_lo, &c->stage_w, &c->part, &c->centre, &c->epart, &c->status_counter, &c->a_scratch,
-                    &c->xw, &c->vw, &c->aw, &c->ckpt, &c->traj, &c->hx, &c->hv, &c->hm, &c->ha, &c->hlog})
+                    &c->xw, &c->vw, &c->aw, &c->ckpt, &c->traj, &c->hx, &c->hv, &c->hm, &c->ha, &c->hlog,
+                    &c->stage_alt, &c->stage_lo_alt, &c->tile_done, &c->tpart})
     release(*b);
+  if (c->d_sys_tile) cudaFree(c->d_sys_tile);
   if (c->h_status) cudaFreeHost(c->h_status);
   if (c->d_chunks) cudaFree(c->d_chunks);
   if (c->d_vchunks) cudaFree(c->d_vchunks);
@@ -1021,6 +1123,7 @@ nbody_status adjoint_sweep(nbody_ctx* c, const double* x0, const double* v0, con
   A.precision = c->cfg.precision;
   A.stage_x = c->stage.p;
   A.stage_w = c->stage_w.p;
+  A.stage_lo = c->stage_lo.p;
   A.centre = static_cast<const double*>(c->centre.p);
   A.status = c->status;
   A.g_params = g_params;
@@ -1029,6 +1132,7 @@ nbody_status adjoint_sweep(nbody_ctx* c, const double* x0, const double* v0, con
   A.sys_chunk = c->d_sys_chunk;
   A.n_sys = c->n_sys;
   A.done = c->counter + 6;
+  A.part_slices = part_slices(c, g_params ? 96 : 64);
   const Chunk* vch = c->d_vchunks;
   const int nch = (int)c->chunks.size();
   for (int k = nseg - 1; k >= 0; --k) {
@@ -1044,11 +1148,12 @@ nbody_status adjoint_sweep(nbody_ctx* c, const double* x0, const double* v0, con
     for (int t = 0; t < top - s0; ++t)
       if ((s = step(X + (size_t)(t + 1) * n3))) return s;
     NB_CUDA(c, launch_stage_vec(vch, nch, c->cfg.precision, X + (size_t)(top - s0) * n3, m,
-                                static_cast<const double*>(c->centre.p), c->stage.p, 1, st));
+                                static_cast<const double*>(c->centre.p), c->stage.p, c->stage_lo.p, 1, c->n_total,
+                                c->n_sys, c->status, st));
     ++c->launches;
     if (k == nseg - 1) {
       NB_CUDA(c, launch_stage_vec(vch, nch, c->cfg.precision, g_v0, m, static_cast<const double*>(c->centre.p),
-                                  c->stage_w.p, 0, st));
+                                  c->stage_w.p, nullptr, 0, c->n_total, c->n_sys, c->status, st));
       ++c->launches;
     }
     for (int t = top; t >= s0; --t) {
@@ -1088,7 +1193,15 @@ double* mapped_host(const void* p) {
 
 extern "C" {
 
-int32_t nbody_version(void) { return (1 << 16) | 0; }
+int32_t nbody_version(void) { return (1 << 16) | 1; }
+
+int32_t nbody_build_flags(void) {
+#ifdef NBODY_DEBUG
+  return 1;
+#else
+  return 0;
+#endif
+}
 
 const char* nbody_last_error(const nbody_ctx* ctx) {
   if (ctx) return ctx->err.c_str();
@@ -1160,11 +1273,14 @@ nbody_status nbody_init(nbody_ctx** out, const nbody_config* cfg, int64_t n_syst
   };
   const size_t n = (size_t)c->n_total;
   const size_t stage_bytes = n * (cfg->precision == NBODY_MIXED ? sizeof(float4) : sizeof(double4_32a));
-  if ((s = ensure(c, c->stage, stage_bytes))) return bail(s);
-  if (cfg->precision == NBODY_MIXED && (s = ensure(c, c->stage_lo, n * sizeof(float4)))) return bail(s);
+  if ((s = ensure(c, c->stage, stage_bytes)) || (s = ensure(c, c->stage_alt, stage_bytes))) return bail(s);
+  if (cfg->precision == NBODY_MIXED &&
+      ((s = ensure(c, c->stage_lo, n * sizeof(float4))) || (s = ensure(c, c->stage_lo_alt, n * sizeof(float4)))))
+    return bail(s);
   if ((s = ensure(c, c->centre, (size_t)c->n_sys * 3 * sizeof(double)))) return bail(s);
   if ((s = ensure(c, c->epart, std::max<size_t>(1, c->chunks.size()) * kEnergyVals * sizeof(double)))) return bail(s);
-  // [0..1] work counter, [2] status word, [4] energy ticket, [5] centre ticket, [6] adjoint-parameter ticket
+  // [0..1] work counter, [2] status word, [4] energy ticket, [5] centre ticket, [6] adjoint-parameter ticket,
+  // [7] fused-epilogue record ticket
   if ((s = ensure(c, c->status_counter, 8 * sizeof(unsigned)))) return bail(s);
   c->counter = static_cast<unsigned*>(c->status_counter.p);
   c->status = c->counter + 2;
@@ -1415,6 +1531,7 @@ nbody_status nbody_sync(nbody_ctx* c) {
   NB_CUDA(c, cudaStreamSynchronize(c->stream));
   const unsigned st = *c->h_status;
   if (st) NB_CUDA(c, cudaMemset(c->status, 0, sizeof(unsigned)));
+  if (st & kFlagIndex) return fail(c, NBODY_EINTERNAL, "a device-side index check failed (NBODY_DEBUG build)");
   if (st & kFlagTimeout) return fail(c, NBODY_ETIMEOUT, "a bounded device-side wait gave up");
   if ((st & kFlagNonFinite) && !(c->cfg.flags & NBODY_FLAG_NOCHECK))
     return fail(c, NBODY_ENONFINITE, "non-finite acceleration, potential or gradient produced");

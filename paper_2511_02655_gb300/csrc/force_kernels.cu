@@ -25,6 +25,7 @@
 
 #include "nbody_internal.h"
 #include "pair_common.cuh"
+#include "post_common.cuh"
 
 namespace nbody {
 namespace {
@@ -32,7 +33,8 @@ namespace {
 // Near-pair refinement. The float32 staging coordinates carry an absolute
 // rounding error of about |x - c| 2^-24, harmless for distant pairs but
 // dominant for pairs closer than a few softening lengths. Pairs with s^2 below
-// the refinement radius get d recomputed with the staged remainders (below).
+// the refinement radius get d recomputed with the staged remainders
+// (refine_pair, correct_pair in pair_common.cuh).
 // For gravity such pairs are rare, so they are found without a branch per
 // pair: every pair folds its s^2 into a running minimum (one FMNMX), and after
 // each sub-block of kSub j-bodies a thread whose minimum fell below the radius
@@ -60,59 +62,18 @@ namespace {
 constexpr int kSub = NBODY_SUB;  // j-bodies per near-pair check
 constexpr int kQuadUnroll = NBODY_QUAD_UNROLL;
 
-// d of a near pair from the staged float32 parts x - c = hi + lo (lo is the
-// float32 remainder of the float64 value): the hi difference is exact for close
-// pairs (Sterbenz) and the lo difference restores the bits the staging dropped,
-// so d is good to a rounding of |d| itself, in float32 arithmetic only.
-__device__ __forceinline__ void refine_pair(const float4* __restrict__ lo, const int i, const int j, const float dhx,
-                                            const float dhy, const float dhz, const float eps2, float& dx, float& dy,
-                                            float& dz, float& r2) {
-  const float4 lj = lo[j], li = lo[i];
-  dx = dhx + (lj.x - li.x);
-  dy = dhy + (lj.y - li.y);
-  dz = dhz + (lj.z - li.z);
-  r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
-}
-
-// Second look at one pair (j-body q at global index jg, i-body at ig) of a
-// flagged sub-block: if it is near and not the self pair, replace its
-// unrefined contribution in (ax, ay, az, pp) by the refined one. The
-// unrefined terms are recomputed with exactly the first pass's operations.
-// LAW 0: softened gravity (q.w = m_j); LAW 1: Lennard-Jones (s2 = sigma^2).
-template <int LAW = 0>
-__device__ __forceinline__ void correct_pair(const float4 q, const int jg, const int ig, const int i_end,
-                                             const float xi, const float yi, const float zi, const float eps2,
-                                             const float r2c, const float4* __restrict__ lo, float& ax, float& ay,
-                                             float& az, float& pp, const float s2 = 0.f) {
-  const float dx = q.x - xi;
-  const float dy = q.y - yi;
-  const float dz = q.z - zi;
-  const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
-  if (!(r2 < r2c) || ig >= i_end || jg < 0 || ig == jg) return;
-  float rx, ry, rz, rr2;
-  refine_pair(lo, ig, jg, dx, dy, dz, eps2, rx, ry, rz, rr2);
-  if (LAW == 0) {
-    const float iu = rsq_approx(r2);
-    const float msu = q.w * iu;
-    const float wu = msu * (iu * iu);
-    const float ir = rsq_approx(rr2);
-    const float msr = q.w * ir;
-    const float wr = msr * (ir * ir);
-    ax += fmaf(rx, wr, -(dx * wu));
-    ay += fmaf(ry, wr, -(dy * wu));
-    az += fmaf(rz, wr, -(dz * wu));
-    pp += msr - msu;
-  } else {
-    const float iu = rcp_approx(r2);
-    const float su2 = s2 * iu, su6 = su2 * (su2 * su2), su12 = su6 * su6;
-    const float wu = fmaf(su12, -2.f, su6) * iu;
-    const float ir = rcp_approx(rr2);
-    const float sr2 = s2 * ir, sr6 = sr2 * (sr2 * sr2), sr12 = sr6 * sr6;
-    const float wr = fmaf(sr12, -2.f, sr6) * ir;
-    ax += fmaf(rx, wr, -(dx * wu));
-    ay += fmaf(ry, wr, -(dy * wu));
-    az += fmaf(rz, wr, -(dz * wu));
-    pp += fmaf(sr6, -1.f, sr12) - fmaf(su6, -1.f, su12);
+// The item's float64 partial of each of its bodies into its slice. A fused
+// launch keeps a single-slice system's partial in registers only: its item is
+// the tile's only one, so the epilogue reads nothing back.
+template <int BLOCK, int R>
+__device__ __forceinline__ void store_partial(const PairLaunch& L, const WorkItem& w, double4_32a* part,
+                                              const double4_32a (&own)[R]) {
+  if (L.fuse && w.n_slices == 1) return;
+  double4_32a* out = part + (int64_t)w.slice * L.n_total;
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int i = w.i_begin + (int)threadIdx.x + r * BLOCK;
+    if (i < w.i_end) out[i] = own[r];
   }
 }
 
@@ -174,7 +135,7 @@ __device__ __forceinline__ void tile_pass_f32(const float4* tile, const int jt, 
 }
 
 template <int BLOCK, int R, int J>
-__global__ void __launch_bounds__(BLOCK) k_force_mixed(const PairLaunch L) {
+__global__ void __launch_bounds__(BLOCK) k_force_mixed(const PairLaunch L, const PostLaunch P) {
   constexpr int LPT = (J + BLOCK - 1) / BLOCK;  // tile entries loaded per thread
   __shared__ __align__(16) float4 tile[2][J];   // double buffer: one barrier per tile
   __shared__ int s_item;
@@ -188,6 +149,7 @@ __global__ void __launch_bounds__(BLOCK) k_force_mixed(const PairLaunch L) {
     const int it = next_item(L.counter, &s_item);  // also a barrier: the buffers are free
     if (it >= L.n_items) break;
     const WorkItem w = L.items[it];
+    if (!item_ok(w, L)) continue;  // NBODY_DEBUG builds only
 
     float xi[R], yi[R], zi[R];
     float hx[R], hy[R], hz[R], hp[R], lx[R], ly[R], lz[R], lp[R];
@@ -247,13 +209,13 @@ __global__ void __launch_bounds__(BLOCK) k_force_mixed(const PairLaunch L) {
       __syncthreads();
     }
 
-    double4_32a* out = part + (int64_t)w.slice * L.n_total;
+    double4_32a own[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-      if (ig[r] < w.i_end)
-        out[ig[r]] = make_double4_32a((double)hx[r] + (double)lx[r], (double)hy[r] + (double)ly[r],
-                                      (double)hz[r] + (double)lz[r], (double)hp[r] + (double)lp[r]);
-    }
+    for (int r = 0; r < R; ++r)
+      own[r] = make_double4_32a((double)hx[r] + (double)lx[r], (double)hy[r] + (double)ly[r],
+                                (double)hz[r] + (double)lz[r], (double)hp[r] + (double)lp[r]);
+    store_partial<BLOCK, R>(L, w, part, own);
+    if (L.fuse) fused_epilogue<BLOCK, R>(L, P, w, own);
   }
   retire_cta(L.counter);
 }
@@ -362,12 +324,16 @@ __device__ __forceinline__ void quad_f32x2(const float* tx, const float* ty, con
   }
 }
 
+// tlx, tly, tlz (Lennard-Jones): the tile's staged remainders; lix, liy, liz: the
+// i-bodies' remainders (gravity reads both from lo in global memory instead).
 template <int LAW, int R, bool MASK, bool PHI>
 __device__ __forceinline__ void tile_pass_f32x2(const float* tx, const float* ty, const float* tz, const float* tm,
                                                 const int jt, const int nj, const int (&ig)[R], const float2 (&nx)[R],
                                                 const float2 (&ny)[R], const float2 (&nz)[R], const int i_end,
                                                 const float2 e2, const float2 s2, const float r2c,
-                                                const float4* __restrict__ lo, float2 (&ax)[R], float2 (&ay)[R],
+                                                const float4* __restrict__ lo, const float* tlx, const float* tly,
+                                                const float* tlz, const float (&lix)[R], const float (&liy)[R],
+                                                const float (&liz)[R], float2 (&ax)[R], float2 (&ay)[R],
                                                 float2 (&az)[R], float2 (&pp)[R]) {
   static_assert(kSub <= 32, "one near-mask bit per j-body of a sub-block");
   const int nj4 = (nj + 3) & ~3;  // the tile is padded to a multiple of four
@@ -396,8 +362,9 @@ __device__ __forceinline__ void tile_pass_f32x2(const float* tx, const float* ty
           const int j = jb + __ffs(b) - 1;
           b &= b - 1u;
           if (j < nj)
-            correct_pair<LAW>(make_float4(tx[j], ty[j], tz[j], tm[j]), jt + j, ig[r], i_end, -nx[r].x, -ny[r].x,
-                              -nz[r].x, e2.x, r2c, lo, ax[r].x, ay[r].x, az[r].x, pp[r].x, s2.x);
+            correct_pair_lj(tx[j], ty[j], tz[j], jt + j, ig[r], i_end, -nx[r].x, -ny[r].x, -nz[r].x, e2.x, r2c,
+                            tlx[j], tly[j], tlz[j], lix[r], liy[r], liz[r], s2.x, ax[r].x, ay[r].x, az[r].x,
+                            pp[r].x);
         }
       }
     } else if (fminf(mn0, mn1) < r2c) {
@@ -435,13 +402,15 @@ __device__ __forceinline__ void tile_pass_f32x2(const float* tx, const float* ty
 // tile timed well on the tuner's synthetic sphere but 3% slower on real inputs.)
 template <int LAW, int BLOCK, int R, int J, bool PHI, int MINB = 0>
 __global__ void __launch_bounds__(BLOCK, (MINB > 0 ? MINB : (NBODY_MIN_CTAS > 0 ? NBODY_MIN_CTAS : 1)))
-    k_force_mixed2(const PairLaunch L) {
+    k_force_mixed2(const PairLaunch L, const PostLaunch P) {
   static_assert(J % 4 == 0, "tiles hold whole quads of j-bodies");
   constexpr int LPT = (J + BLOCK - 1) / BLOCK;
+  constexpr int JL = LAW == 1 ? J : 1;  // Lennard-Jones: the tile's staged remainders as well
   __shared__ __align__(16) float tx[2][J];  // double buffer: one barrier per tile
   __shared__ __align__(16) float ty[2][J];
   __shared__ __align__(16) float tz[2][J];
   __shared__ __align__(16) float tm[2][J];
+  __shared__ float tlx[2][JL], tly[2][JL], tlz[2][JL];
   __shared__ int s_item;
   const float4* __restrict__ st = static_cast<const float4*>(L.stage_x);
   double4_32a* __restrict__ part = reinterpret_cast<double4_32a*>(L.part);
@@ -455,9 +424,11 @@ __global__ void __launch_bounds__(BLOCK, (MINB > 0 ? MINB : (NBODY_MIN_CTAS > 0 
     const int it = next_item(L.counter, &s_item);  // also a barrier: the buffers are free
     if (it >= L.n_items) break;
     const WorkItem w = L.items[it];
+    if (!item_ok(w, L)) continue;  // NBODY_DEBUG builds only
 
     float2 nx[R], ny[R], nz[R];
     float hx[R], hy[R], hz[R], hp[R], lx[R], ly[R], lz[R], lp[R];
+    float lix[R], liy[R], liz[R];  // Lennard-Jones: the i-bodies' staged remainders
     int ig[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
@@ -468,6 +439,11 @@ __global__ void __launch_bounds__(BLOCK, (MINB > 0 ? MINB : (NBODY_MIN_CTAS > 0 
       nz[r] = make_float2(-q.z, -q.z);
       hx[r] = hy[r] = hz[r] = hp[r] = 0.f;
       lx[r] = ly[r] = lz[r] = lp[r] = 0.f;
+      lix[r] = liy[r] = liz[r] = 0.f;
+      if (LAW == 1 && lo && ig[r] < w.i_end) {
+        const float4 l = lo[ig[r]];
+        lix[r] = l.x, liy[r] = l.y, liz[r] = l.z;
+      }
     }
 
     // first tile straight into buffer 0 (padded to a whole quad with far, massless bodies)
@@ -479,6 +455,10 @@ __global__ void __launch_bounds__(BLOCK, (MINB > 0 ? MINB : (NBODY_MIN_CTAS > 0 
         if (t < nj) {
           const float4 q = st[w.j_begin + t];
           tx[0][t] = q.x, ty[0][t] = q.y, tz[0][t] = q.z, tm[0][t] = q.w;
+          if (LAW == 1 && lo) {
+            const float4 l = lo[w.j_begin + t];
+            tlx[0][t] = l.x, tly[0][t] = l.y, tlz[0][t] = l.z;
+          }
         } else if (t < nj4) {
           tx[0][t] = kFarAway, ty[0][t] = kFarAway, tz[0][t] = kFarAway, tm[0][t] = 0.f;
         }
@@ -490,12 +470,15 @@ __global__ void __launch_bounds__(BLOCK, (MINB > 0 ? MINB : (NBODY_MIN_CTAS > 0 
     for (int jt = w.j_begin; jt < w.j_end; jt += J, buf ^= 1) {
       const int nj = min(J, w.j_end - jt);
       const bool more = jt + J < w.j_end;
-      float4 pre[LPT];
+      float4 pre[LPT], plo[LAW == 1 ? LPT : 1];
       if (more) {
 #pragma unroll
         for (int k = 0; k < LPT; ++k) {
           const int jj = jt + J + (int)threadIdx.x + k * BLOCK;
-          if ((int)threadIdx.x + k * BLOCK < J && jj < w.j_end) pre[k] = st[jj];
+          if ((int)threadIdx.x + k * BLOCK < J && jj < w.j_end) {
+            pre[k] = st[jj];
+            if (LAW == 1 && lo) plo[LAW == 1 ? k : 0] = lo[jj];
+          }
         }
       }
 
@@ -503,12 +486,13 @@ __global__ void __launch_bounds__(BLOCK, (MINB > 0 ? MINB : (NBODY_MIN_CTAS > 0 
 #pragma unroll
       for (int r = 0; r < R; ++r) ax[r] = ay[r] = az[r] = pp[r] = make_float2(0.f, 0.f);
       const bool diag = (jt < w.i_end) && (w.i_begin < jt + nj);
+      const int bl = LAW == 1 ? buf : 0;
       if (diag)
         tile_pass_f32x2<LAW, R, true, PHI>(tx[buf], ty[buf], tz[buf], tm[buf], jt, nj, ig, nx, ny, nz, w.i_end, e2, s2,
-                                      r2c, lo, ax, ay, az, pp);
+                                           r2c, lo, tlx[bl], tly[bl], tlz[bl], lix, liy, liz, ax, ay, az, pp);
       else
-        tile_pass_f32x2<LAW, R, false, PHI>(tx[buf], ty[buf], tz[buf], tm[buf], jt, nj, ig, nx, ny, nz, w.i_end, e2, s2,
-                                       r2c, lo, ax, ay, az, pp);
+        tile_pass_f32x2<LAW, R, false, PHI>(tx[buf], ty[buf], tz[buf], tm[buf], jt, nj, ig, nx, ny, nz, w.i_end, e2,
+                                            s2, r2c, lo, tlx[bl], tly[bl], tlz[bl], lix, liy, liz, ax, ay, az, pp);
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         two_sum_acc(hx[r], lx[r], ax[r].x + ax[r].y);
@@ -524,6 +508,10 @@ __global__ void __launch_bounds__(BLOCK, (MINB > 0 ? MINB : (NBODY_MIN_CTAS > 0 
           const int t = (int)threadIdx.x + k * BLOCK;
           if (t < nn) {
             tx[b][t] = pre[k].x, ty[b][t] = pre[k].y, tz[b][t] = pre[k].z, tm[b][t] = pre[k].w;
+            if (LAW == 1 && lo) {
+              const float4 l = plo[LAW == 1 ? k : 0];
+              tlx[LAW == 1 ? b : 0][t] = l.x, tly[LAW == 1 ? b : 0][t] = l.y, tlz[LAW == 1 ? b : 0][t] = l.z;
+            }
           } else if (t < nn4) {
             tx[b][t] = kFarAway, ty[b][t] = kFarAway, tz[b][t] = kFarAway, tm[b][t] = 0.f;
           }
@@ -532,13 +520,13 @@ __global__ void __launch_bounds__(BLOCK, (MINB > 0 ? MINB : (NBODY_MIN_CTAS > 0 
       __syncthreads();
     }
 
-    double4_32a* out = part + (int64_t)w.slice * L.n_total;
+    double4_32a own[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-      if (ig[r] < w.i_end)
-        out[ig[r]] = make_double4_32a((double)hx[r] + (double)lx[r], (double)hy[r] + (double)ly[r],
-                                      (double)hz[r] + (double)lz[r], PHI ? (double)hp[r] + (double)lp[r] : 0.0);
-    }
+    for (int r = 0; r < R; ++r)
+      own[r] = make_double4_32a((double)hx[r] + (double)lx[r], (double)hy[r] + (double)ly[r],
+                                (double)hz[r] + (double)lz[r], PHI ? (double)hp[r] + (double)lp[r] : 0.0);
+    store_partial<BLOCK, R>(L, w, part, own);
+    if (L.fuse) fused_epilogue<BLOCK, R>(L, P, w, own);
   }
   retire_cta(L.counter);
 }
@@ -573,7 +561,7 @@ __device__ __forceinline__ void pair_f64(const double4_32a q, const double xi, c
 }
 
 template <int LAW, int BLOCK, int R, int J>
-__global__ void __launch_bounds__(BLOCK) k_force_fp64(const PairLaunch L) {
+__global__ void __launch_bounds__(BLOCK) k_force_fp64(const PairLaunch L, const PostLaunch P) {
   constexpr int LPT = (J + BLOCK - 1) / BLOCK;
   __shared__ __align__(32) double4_32a tile[J];
   __shared__ int s_item;
@@ -586,6 +574,7 @@ __global__ void __launch_bounds__(BLOCK) k_force_fp64(const PairLaunch L) {
     const int it = next_item(L.counter, &s_item);
     if (it >= L.n_items) break;
     const WorkItem w = L.items[it];
+    if (!item_ok(w, L)) continue;  // NBODY_DEBUG builds only
 
     double xi[R], yi[R], zi[R], ax[R], ay[R], az[R], pp[R];
     int ig[R];
@@ -639,10 +628,11 @@ __global__ void __launch_bounds__(BLOCK) k_force_fp64(const PairLaunch L) {
       }
     }
 
-    double4_32a* out = part + (int64_t)w.slice * L.n_total;
+    double4_32a own[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r)
-      if (ig[r] < w.i_end) out[ig[r]] = make_double4_32a(ax[r], ay[r], az[r], pp[r]);
+    for (int r = 0; r < R; ++r) own[r] = make_double4_32a(ax[r], ay[r], az[r], pp[r]);
+    store_partial<BLOCK, R>(L, w, part, own);
+    if (L.fuse) fused_epilogue<BLOCK, R>(L, P, w, own);
   }
   retire_cta(L.counter);
 }
@@ -670,15 +660,17 @@ int occupancy_of(K kern, int block) {
 
 }  // namespace
 
-cudaError_t launch_force(int precision, const PairLaunch& L, cudaStream_t st) {
+cudaError_t launch_force(int precision, const PairLaunch& L, const PostLaunch* Pp, cudaStream_t st) {
   if (L.n_ctas <= 0) return cudaErrorInvalidConfiguration;
+  if (L.fuse && !Pp) return cudaErrorInvalidValue;
+  const PostLaunch P = Pp ? *Pp : PostLaunch{};
   if (L.law == 1) {
 #define NBODY_X(B, R, J)                                               \
   if (L.block == B && L.ipt == R && L.jtile == J) {                    \
     if (L.phi)                                                         \
-      k_force_mixed2<1, B, R, J, true><<<L.n_ctas, B, 0, st>>>(L);     \
+      k_force_mixed2<1, B, R, J, true><<<L.n_ctas, B, 0, st>>>(L, P);     \
     else                                                               \
-      k_force_mixed2<1, B, R, J, false><<<L.n_ctas, B, 0, st>>>(L);    \
+      k_force_mixed2<1, B, R, J, false><<<L.n_ctas, B, 0, st>>>(L, P);    \
     return cudaGetLastError();                                         \
   }
     if (precision == 1) {
@@ -689,7 +681,7 @@ cudaError_t launch_force(int precision, const PairLaunch& L, cudaStream_t st) {
 #undef NBODY_X
 #define NBODY_X(B, R, J)                                               \
   if (L.block == B && L.ipt == R && L.jtile == J) {                    \
-    k_force_fp64<1, B, R, J><<<L.n_ctas, B, 0, st>>>(L);               \
+    k_force_fp64<1, B, R, J><<<L.n_ctas, B, 0, st>>>(L, P);               \
     return cudaGetLastError();                                         \
   }
     if (L.variant != 0) return cudaErrorInvalidConfiguration;
@@ -703,9 +695,9 @@ cudaError_t launch_force(int precision, const PairLaunch& L, cudaStream_t st) {
 #define NBODY_X(B, R, J)                                                \
   if (L.block == B && L.ipt == R && L.jtile == J) {                     \
     if (L.phi)                                                          \
-      k_force_mixed2<0, B, R, J, true, 4><<<L.n_ctas, B, 0, st>>>(L);   \
+      k_force_mixed2<0, B, R, J, true, 4><<<L.n_ctas, B, 0, st>>>(L, P);   \
     else                                                                \
-      k_force_mixed2<0, B, R, J, false, 4><<<L.n_ctas, B, 0, st>>>(L);  \
+      k_force_mixed2<0, B, R, J, false, 4><<<L.n_ctas, B, 0, st>>>(L, P);  \
     return cudaGetLastError();                                          \
   }
       NBODY_CAPPED_TILINGS(NBODY_X)
@@ -716,11 +708,11 @@ cudaError_t launch_force(int precision, const PairLaunch& L, cudaStream_t st) {
 #define NBODY_X(B, R, J)                                               \
   if (L.block == B && L.ipt == R && L.jtile == J) {                    \
     if (L.variant == 1 && L.phi)                                       \
-      k_force_mixed2<0, B, R, J, true><<<L.n_ctas, B, 0, st>>>(L);     \
+      k_force_mixed2<0, B, R, J, true><<<L.n_ctas, B, 0, st>>>(L, P);     \
     else if (L.variant == 1)                                           \
-      k_force_mixed2<0, B, R, J, false><<<L.n_ctas, B, 0, st>>>(L);    \
+      k_force_mixed2<0, B, R, J, false><<<L.n_ctas, B, 0, st>>>(L, P);    \
     else                                                               \
-      k_force_mixed<B, R, J><<<L.n_ctas, B, 0, st>>>(L);               \
+      k_force_mixed<B, R, J><<<L.n_ctas, B, 0, st>>>(L, P);               \
     return cudaGetLastError();                                         \
   }
     NBODY_MIXED_TILINGS(NBODY_X)
@@ -730,7 +722,7 @@ cudaError_t launch_force(int precision, const PairLaunch& L, cudaStream_t st) {
   if (L.variant != 0) return cudaErrorInvalidConfiguration;
 #define NBODY_X(B, R, J)                                               \
   if (L.block == B && L.ipt == R && L.jtile == J) {                    \
-    k_force_fp64<0, B, R, J><<<L.n_ctas, B, 0, st>>>(L);               \
+    k_force_fp64<0, B, R, J><<<L.n_ctas, B, 0, st>>>(L, P);               \
     return cudaGetLastError();                                         \
   }
   NBODY_FORCE_TILINGS(NBODY_X)

@@ -8,13 +8,16 @@
 namespace nbody {
 
 // One unit of all-pairs work: i-bodies [i_begin, i_end) of one system against
-// its j-bodies [j_begin, j_end), partial sums written to slice `slice`.
-// Indices are global body indices (rows of the caller's arrays).
+// its j-bodies [j_begin, j_end), partial sums written to slice `slice` of the
+// system's n_slices. Indices are global body indices (rows of the caller's
+// arrays); `tile` numbers the (system, i-range) pairs of the work list.
 struct WorkItem {
   int32_t sys;
   int32_t i_begin, i_end;
   int32_t j_begin, j_end;
   int32_t slice;
+  int32_t tile;
+  int32_t n_slices;
 };
 
 // A contiguous run of bodies of one system, the unit of the O(N) kernels and
@@ -33,6 +36,25 @@ constexpr int kAdjVals = 8;         // VJP partial values per body per slice
 // Device status word bits (latched, read by nbody_sync).
 constexpr unsigned kFlagNonFinite = 1u;
 constexpr unsigned kFlagTimeout = 2u;
+constexpr unsigned kFlagIndex = 4u;  // NBODY_DEBUG builds: an index check failed, the access was skipped
+
+// Index checks of NBODY_DEBUG builds: nb_debug_ok(cond, status) is true when
+// cond holds; otherwise it latches kFlagIndex in *status and returns false, and
+// the caller skips the access. Release builds compile it to `true`.
+#ifdef NBODY_DEBUG
+__device__ __forceinline__ bool nb_debug_ok(const bool cond, unsigned* status) {
+  if (!cond && status) atomicOr(status, kFlagIndex);
+  return cond;
+}
+#else
+__device__ __forceinline__ constexpr bool nb_debug_ok(const bool, unsigned*) { return true; }
+#endif
+
+// Host-side argument check (capi.cu): false when the driver reports that the
+// device allocation holding p ends before p + bytes (cuMemGetAddressRange);
+// *avail then holds the bytes left from p. True when the driver does not
+// expose the query or does not know p.
+bool allocation_holds(const void* p, size_t bytes, size_t* avail);
 
 // ---------------------------------------------------------------------------
 // all-pairs kernels (force_kernels.cu, adjoint_kernels.cu)
@@ -46,8 +68,8 @@ struct PairLaunch {
   double* part;          // force: double4_32a [slices][N]; VJP: (2 or 3 with params) x double4_32a [slices][N]
   int64_t n_total;
   double eps2;
-  const float4* stage_lo;  // force (mixed): float32 remainders (x - c) - hi [N], near-pair refinement
-  float r2_near;         // force (mixed): refine pairs with s^2 below this (0 = never)
+  const float4* stage_lo;  // mixed: float32 remainders (x - c) - hi [N], near-pair refinement
+  float r2_near;         // mixed: refine pairs with s^2 below this (0 = never)
   int variant;           // mixed kernels: 0 scalar float32, 1 packed float32x2
   int law;               // 0 softened gravity, 1 Lennard-Jones
   double sigma2;         // Lennard-Jones sigma^2
@@ -55,10 +77,53 @@ struct PairLaunch {
   int n_ctas;            // persistent grid size
   int params;            // VJP: also the sums for the G and eps gradients (third double4)
   int phi;               // force (mixed packed): accumulate the potential (0: skip it, partial .w = 0)
+  int32_t part_slices;   // slices the partial buffer holds (index checks of NBODY_DEBUG builds)
+  int32_t block_bodies;  // debug checks: i-bodies a work item may hold (block x ipt)
+  unsigned* status;      // device status word (index checks of NBODY_DEBUG builds)
+  // Fused step epilogue (force kernels, fuse = 1): the CTA that completes the
+  // last slice of an i-tile (ticket tile_done[tile]) adds the tile's slices and
+  // runs the O(N) work of the PostLaunch passed beside this struct for those
+  // bodies; per-tile energy partials go to tpart, and the last tile to finish
+  // (ticket fin_done) forms the per-system records over sys_tile.
+  int fuse;
+  unsigned* tile_done;      // [n_tiles], zero between launches
+  double* tpart;            // [n_tiles][kEnergyVals]
+  const int32_t* sys_tile;  // [n_sys + 1] tile range of each system
+  int32_t n_tiles;
+  unsigned* fin_done;       // zero between launches
 };
 
-// Returns cudaErrorInvalidConfiguration for an unsupported tiling.
-cudaError_t launch_force(int precision, const PairLaunch& L, cudaStream_t st);
+#ifdef NBODY_DEBUG
+// NBODY_DEBUG check of a work item against the buffers it indexes: its body
+// ranges inside the rows, its i-range inside one CTA's tile, its slice inside
+// the partial-sum buffer (and, fused, its tile inside the tile tables). The
+// kernel skips an item that fails.
+__device__ __forceinline__ bool item_ok(const WorkItem& w, const PairLaunch& L) {
+  return nb_debug_ok(w.i_begin >= 0 && w.i_begin < w.i_end && w.i_end <= L.n_total && w.j_begin >= 0 &&
+                         w.j_begin < w.j_end && w.j_end <= L.n_total && w.i_end - w.i_begin <= L.block_bodies &&
+                         w.slice >= 0 && w.slice < w.n_slices && w.n_slices <= L.part_slices &&
+                         (!L.fuse || (w.tile >= 0 && w.tile < L.n_tiles)),
+                     L.status);
+}
+
+// NBODY_DEBUG check of a chunk of an O(N) kernel: rows, system index and (when
+// part_slices > 0) its slice count against the partial-sum buffer. A chunk that
+// fails is processed as an empty one.
+__device__ __forceinline__ bool chunk_ok(const Chunk& c, const int64_t n_total, const int n_sys, const int part_slices,
+                                         unsigned* status) {
+  return nb_debug_ok(c.begin >= 0 && c.begin < c.end && c.end <= n_total && c.end - c.begin <= kChunk && c.sys >= 0 &&
+                         c.sys < n_sys && (part_slices <= 0 || (c.n_slices >= 1 && c.n_slices <= part_slices)),
+                     status);
+}
+#else
+__device__ __forceinline__ constexpr bool item_ok(const WorkItem&, const PairLaunch&) { return true; }
+__device__ __forceinline__ constexpr bool chunk_ok(const Chunk&, int64_t, int, int, unsigned*) { return true; }
+#endif
+
+struct PostLaunch;
+// Returns cudaErrorInvalidConfiguration for an unsupported tiling. P: the O(N)
+// work of the fused epilogue (used when L.fuse; may be NULL otherwise).
+cudaError_t launch_force(int precision, const PairLaunch& L, const PostLaunch* P, cudaStream_t st);
 cudaError_t launch_vjp(int precision, const PairLaunch& L, cudaStream_t st);
 // CTAs of the force kernel that fit on one SM for the tiling (0 if unsupported).
 int force_ctas_per_sm(int precision, int variant, int block, int ipt, int jtile, int law);
@@ -103,6 +168,7 @@ struct PostLaunch {
   const int32_t* sys_chunk;  // [n_sys + 1] chunk range of each system
   int n_sys;
   unsigned* done;          // last-CTA ticket (zero between launches)
+  int32_t part_slices;     // slices the partial buffer holds (index checks of NBODY_DEBUG builds)
 };
 cudaError_t launch_post(const PostLaunch& P, cudaStream_t st);
 
@@ -111,7 +177,7 @@ cudaError_t launch_post(const PostLaunch& P, cudaStream_t st);
 // order by the last CTA (ticket `done`, zero between launches).
 cudaError_t launch_centre(const Chunk* chunks, int n_chunks, const int32_t* sys_chunk, const int64_t* off, int n_sys,
                           const double* x, const double* m, double* cpart, double* centre, unsigned* done,
-                          cudaStream_t st);
+                          int64_t n_total, unsigned* status, cudaStream_t st);
 
 struct AdjLaunch {
   const Chunk* chunks;
@@ -128,6 +194,7 @@ struct AdjLaunch {
   int precision;
   void* stage_x;
   void* stage_w;
+  void* stage_lo;          // mixed: float4 remainders of the staged positions (nullable)
   const double* centre;
   unsigned* status;
   double* g_params;        // nullable [n_sys][2]: += coef (w.da/dG, w.da/deps), formed by the last CTA
@@ -136,6 +203,7 @@ struct AdjLaunch {
   const int32_t* sys_chunk;
   int n_sys;
   unsigned* done;          // last-CTA ticket (zero between launches)
+  int32_t part_slices;     // slices the partial buffer holds (index checks of NBODY_DEBUG builds)
 };
 cudaError_t launch_adj_update(const AdjLaunch& A, cudaStream_t st);
 
@@ -148,8 +216,10 @@ struct Copy4 {
 };
 cudaError_t launch_copy4(const Copy4& C, int n_sms, cudaStream_t st);
 
-// stage w = lam (float4 / double4_32a) and/or x for a VJP without an update
+// stage w = lam (float4 / double4_32a) or positions x (as_position; with their
+// float32 remainders into stage_lo when given) for a VJP without an update
 cudaError_t launch_stage_vec(const Chunk* chunks, int n_chunks, int precision, const double* vec, const double* m,
-                             const double* centre, void* stage, int as_position, cudaStream_t st);
+                             const double* centre, void* stage, void* stage_lo, int as_position, int64_t n_total,
+                             int n_sys, unsigned* status, cudaStream_t st);
 
 }  // namespace nbody

@@ -10,13 +10,13 @@
 // staging, partial-sum and work-list buffers; this entry point takes no
 // context and allocates nothing.
 //
-// Its scratch (the float32 staging copy of the bodies and the staging origin)
-// lives in one file-scope __device__ array of fixed size, reserved on every
-// GPU that loads the library until the process exits. Host code cannot use
-// the array's name as a device address (on the host it names a host-side
-// stand-in), so the device address is looked up with cudaGetSymbolAddress
-// once per device, on the first call made with that device current, and
-// passed to the kernels.
+// Its scratch (the float32 staging copy of the bodies, the float32 remainders
+// the near-pair refinement reads, and the staging origin) lives in one
+// file-scope __device__ array of fixed size, held on every GPU that loads the
+// library's module until the process exits. Host code cannot use the array's
+// name as a device address (on the host it names a host-side stand-in), so
+// the device address is looked up with cudaGetSymbolAddress once per device,
+// on the first call made with that device current, and passed to the kernels.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -39,10 +39,15 @@ constexpr int64_t kMaxBodies = NBODY_NOALLOC_MAX_BODIES;
 constexpr int kThreads = 256;  // threads per CTA of the force kernel
 constexpr int kIpt = 2;        // i-bodies per thread
 constexpr int kTile = 256;     // j-bodies per shared-memory tile
+constexpr int kSub = 32;       // j-bodies per near-pair check
 constexpr int kHeaderBytes = 256;
-constexpr size_t kScratchBytes = kHeaderBytes + sizeof(float4) * (size_t)kMaxBodies;
+constexpr size_t kStageBytes = sizeof(float4) * (size_t)kMaxBodies;
+constexpr size_t kScratchBytes = kHeaderBytes + 2 * kStageBytes;
+// Near-pair refinement radius: 4 softening lengths, as in the context path.
+constexpr double kNearRadiusEps = 4.0;
 
-// Layout: [0, 256) header (staging origin, 3 doubles); [256, ...) float4 staging [kMaxBodies].
+// Layout: [0, 256) header (staging origin, 3 doubles); then float4 staging
+// entries (x - c, m) [kMaxBodies]; then float4 remainders (x - c) - hi [kMaxBodies].
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 constexpr int kMaxDevices = 64;
@@ -59,7 +64,9 @@ nbody_status fail(nbody_status s, const char* fmt, ...) {
   return s;
 }
 
-nbody_status check_dev_ptr(const void* p, int dev, const char* name, bool nullable) {
+// Device memory of the current device holding at least `bytes` from p
+// (the extent is checked where the driver can report the allocation's range).
+nbody_status check_dev_ptr(const void* p, size_t bytes, int dev, const char* name, bool nullable) {
   if (!p) return nullable ? NBODY_OK : fail(NBODY_EINVAL, "nbody_forces_noalloc: %s is NULL", name);
   if (reinterpret_cast<uintptr_t>(p) % 8 != 0)
     return fail(NBODY_EINVAL, "nbody_forces_noalloc: %s is not 8-byte aligned", name);
@@ -72,6 +79,10 @@ nbody_status check_dev_ptr(const void* p, int dev, const char* name, bool nullab
     return fail(NBODY_EINVAL, "nbody_forces_noalloc: %s is not device memory", name);
   if (at.type == cudaMemoryTypeDevice && at.device != dev)
     return fail(NBODY_EINVAL, "nbody_forces_noalloc: %s is on device %d, current device is %d", name, at.device, dev);
+  size_t avail = 0;
+  if (!nbody::allocation_holds(p, bytes, &avail))
+    return fail(NBODY_EINVAL, "nbody_forces_noalloc: %s needs %zu bytes, its allocation holds %zu from that address",
+                name, bytes, avail);
   return NBODY_OK;
 }
 
@@ -111,17 +122,22 @@ __global__ void __launch_bounds__(256) k_na_centre(const double* x, const double
 __global__ void __launch_bounds__(256) k_na_stage(const double* x, const double* m, int n, unsigned char* scratch) {
   const double* c = reinterpret_cast<const double*>(scratch);
   float4* st = reinterpret_cast<float4*>(scratch + kHeaderBytes);
-  for (int i = blockIdx.x * 256 + threadIdx.x; i < n; i += gridDim.x * 256)
-    st[i] = make_float4((float)(x[3 * (int64_t)i] - c[0]), (float)(x[3 * (int64_t)i + 1] - c[1]),
-                        (float)(x[3 * (int64_t)i + 2] - c[2]), (float)m[i]);
+  float4* lo = reinterpret_cast<float4*>(scratch + kHeaderBytes + kStageBytes);
+  for (int i = blockIdx.x * 256 + threadIdx.x; i < n; i += gridDim.x * 256) {
+    const double X = x[3 * (int64_t)i] - c[0], Y = x[3 * (int64_t)i + 1] - c[1], Z = x[3 * (int64_t)i + 2] - c[2];
+    const float hx = (float)X, hy = (float)Y, hz = (float)Z;
+    st[i] = make_float4(hx, hy, hz, (float)m[i]);
+    lo[i] = make_float4((float)(X - (double)hx), (float)(Y - (double)hy), (float)(Z - (double)hz), 0.f);
+  }
 }
 
 template <bool MASK>
 __device__ __forceinline__ void na_pair(const float4 q, const float xi, const float yi, const float zi,
-                                        const float eps2, float& ax, float& ay, float& az, float& pp,
+                                        const float eps2, float& ax, float& ay, float& az, float& pp, float& mn,
                                         const bool self) {
   const float dx = q.x - xi, dy = q.y - yi, dz = q.z - zi;
   const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
+  mn = fminf(mn, r2);
   float inv = nbody::rsq_approx(r2);
   if (MASK) inv = self ? 0.f : inv;
   const float ms = q.w * inv;
@@ -131,11 +147,17 @@ __device__ __forceinline__ void na_pair(const float4 q, const float xi, const fl
 }
 
 // One CTA per i-tile of kThreads * kIpt bodies, each against all n j-bodies;
-// writes a and phi directly (no partial-sum buffer).
-__global__ void __launch_bounds__(kThreads) k_na_force(const unsigned char* scratch, int n, float eps2, double G,
-                                                       double* a, double* phi) {
+// writes a and phi directly (no partial-sum buffer). The pair arithmetic is
+// that of the context path's scalar mixed kernel, near-pair refinement
+// included: every pair folds s^2 into a running minimum, and a sub-block of
+// kSub j-bodies whose minimum fell below r2c is rescanned, each near pair's
+// contribution replaced by the one from the separation refined with the
+// staged remainders.
+__global__ void __launch_bounds__(kThreads) k_na_force(const unsigned char* scratch, int n, float eps2, float r2c,
+                                                       double G, double* a, double* phi) {
   __shared__ __align__(16) float4 tile[kTile];
   const float4* st = reinterpret_cast<const float4*>(scratch + kHeaderBytes);
+  const float4* lo = reinterpret_cast<const float4*>(scratch + kHeaderBytes + kStageBytes);
   const int i0 = blockIdx.x * kThreads * kIpt;
   float xi[kIpt], yi[kIpt], zi[kIpt], hx[kIpt], hy[kIpt], hz[kIpt], hp[kIpt], lx[kIpt], ly[kIpt], lz[kIpt],
       lp[kIpt];
@@ -156,17 +178,29 @@ __global__ void __launch_bounds__(kThreads) k_na_force(const unsigned char* scra
     float ax[kIpt], ay[kIpt], az[kIpt], pp[kIpt];
 #pragma unroll
     for (int r = 0; r < kIpt; ++r) ax[r] = ay[r] = az[r] = pp[r] = 0.f;
-    if (jt < i_end && i0 < jt + nj) {
-      for (int j = 0; j < nj; ++j)
+    const bool diag = jt < i_end && i0 < jt + nj;
+    for (int jb = 0; jb < nj; jb += kSub) {
+      const int je = min(nj, jb + kSub);
+      float mn = 3.0e38f;
+      if (diag) {
+        for (int j = jb; j < je; ++j)
 #pragma unroll
-        for (int r = 0; r < kIpt; ++r)
-          na_pair<true>(tile[j], xi[r], yi[r], zi[r], eps2, ax[r], ay[r], az[r], pp[r], jt + j == ig[r]);
-    } else {
-#pragma unroll 4
-      for (int j = 0; j < nj; ++j)
+          for (int r = 0; r < kIpt; ++r)
+            na_pair<true>(tile[j], xi[r], yi[r], zi[r], eps2, ax[r], ay[r], az[r], pp[r], mn, jt + j == ig[r]);
+      } else {
+#pragma unroll 8
+        for (int j = jb; j < je; ++j)
 #pragma unroll
-        for (int r = 0; r < kIpt; ++r)
-          na_pair<false>(tile[j], xi[r], yi[r], zi[r], eps2, ax[r], ay[r], az[r], pp[r], false);
+          for (int r = 0; r < kIpt; ++r)
+            na_pair<false>(tile[j], xi[r], yi[r], zi[r], eps2, ax[r], ay[r], az[r], pp[r], mn, false);
+      }
+      if (mn < r2c) {
+        for (int j = jb; j < je; ++j)
+#pragma unroll
+          for (int r = 0; r < kIpt; ++r)
+            nbody::correct_pair<0>(tile[j], jt + j, ig[r], n, xi[r], yi[r], zi[r], eps2, r2c, lo, ax[r], ay[r],
+                                   az[r], pp[r]);
+      }
     }
 #pragma unroll
     for (int r = 0; r < kIpt; ++r) {
@@ -202,8 +236,9 @@ extern "C" nbody_status nbody_forces_noalloc(const double* x, const double* m, i
     return fail(NBODY_EUNSUPPORTED, "nbody_forces_noalloc: no usable current CUDA device");
   }
   nbody_status s;
-  if ((s = check_dev_ptr(x, dev, "x", false)) || (s = check_dev_ptr(m, dev, "m", false)) ||
-      (s = check_dev_ptr(a, dev, "a", false)) || (s = check_dev_ptr(phi, dev, "phi", true)))
+  const size_t n3b = (size_t)n * 3 * sizeof(double), n1b = (size_t)n * sizeof(double);
+  if ((s = check_dev_ptr(x, n3b, dev, "x", false)) || (s = check_dev_ptr(m, n1b, dev, "m", false)) ||
+      (s = check_dev_ptr(a, n3b, dev, "a", false)) || (s = check_dev_ptr(phi, n1b, dev, "phi", true)))
     return s;
   void* scratch = nullptr;
   {
@@ -225,8 +260,9 @@ extern "C" nbody_status nbody_forces_noalloc(const double* x, const double* m, i
   const int ni = (int)n;
   k_na_centre<<<1, 256, 0, st>>>(x, m, ni, sp);
   k_na_stage<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, st>>>(x, m, ni, sp);
+  const float r2c = (float)(kNearRadiusEps * kNearRadiusEps * eps * eps);  // 0 for eps = 0: no refinement
   k_na_force<<<(unsigned)((n + kThreads * kIpt - 1) / (kThreads * kIpt)), kThreads, 0, st>>>(
-      sp, ni, (float)(eps * eps), G, a, phi);
+      sp, ni, (float)(eps * eps), r2c, G, a, phi);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(NBODY_ECUDA, "nbody_forces_noalloc: launch failed: %s", cudaGetErrorString(e));
   return NBODY_OK;

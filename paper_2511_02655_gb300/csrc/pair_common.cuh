@@ -1,4 +1,5 @@
-// Device helpers shared by the all-pairs kernels (force and force-VJP).
+// Device helpers shared by the all-pairs kernels (force, force-VJP and the
+// allocation-free entry point).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -31,6 +32,92 @@ __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float t) {
   const float err = (hi - (s - bp)) + (t - bp);
   hi = s;
   lo += err;
+}
+
+// d of a near pair from the staged float32 parts x - c = hi + lo (lo is the
+// float32 remainder of the float64 value): the hi difference is exact for close
+// pairs (Sterbenz) and the lo difference restores the bits the staging dropped,
+// so d is good to a rounding of |d| itself, in float32 arithmetic only.
+__device__ __forceinline__ void refine_pair(const float4* __restrict__ lo, const int i, const int j, const float dhx,
+                                            const float dhy, const float dhz, const float eps2, float& dx, float& dy,
+                                            float& dz, float& r2) {
+  const float4 lj = lo[j], li = lo[i];
+  dx = dhx + (lj.x - li.x);
+  dy = dhy + (lj.y - li.y);
+  dz = dhz + (lj.z - li.z);
+  r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
+}
+
+// The Lennard-Jones pair correction of correct_pair<1> with the remainders
+// given (lj of the j-body from the shared-memory tile, li of the i-body from
+// registers) instead of read from the staging remainders in global memory:
+// the gas has a dozen near pairs per particle, and the loads' latency would
+// stall the warp at every one.
+__device__ __forceinline__ void correct_pair_lj(const float qx, const float qy, const float qz, const int jg,
+                                                const int ig, const int i_end, const float xi, const float yi,
+                                                const float zi, const float eps2, const float r2c, const float ljx,
+                                                const float ljy, const float ljz, const float lix, const float liy,
+                                                const float liz, const float s2, float& ax, float& ay, float& az,
+                                                float& pp) {
+  const float dx = qx - xi;
+  const float dy = qy - yi;
+  const float dz = qz - zi;
+  const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
+  if (!(r2 < r2c) || ig >= i_end || ig == jg) return;
+  const float rx = dx + (ljx - lix), ry = dy + (ljy - liy), rz = dz + (ljz - liz);
+  const float rr2 = fmaf(rx, rx, fmaf(ry, ry, fmaf(rz, rz, eps2)));
+  const float iu = rcp_approx(r2);
+  const float su2 = s2 * iu, su6 = su2 * (su2 * su2), su12 = su6 * su6;
+  const float wu = fmaf(su12, -2.f, su6) * iu;
+  const float ir = rcp_approx(rr2);
+  const float sr2 = s2 * ir, sr6 = sr2 * (sr2 * sr2), sr12 = sr6 * sr6;
+  const float wr = fmaf(sr12, -2.f, sr6) * ir;
+  ax += fmaf(rx, wr, -(dx * wu));
+  ay += fmaf(ry, wr, -(dy * wu));
+  az += fmaf(rz, wr, -(dz * wu));
+  pp += fmaf(sr6, -1.f, sr12) - fmaf(su6, -1.f, su12);
+}
+
+// Second look at one pair (j-body q at global index jg, i-body at ig) of a
+// flagged sub-block: if it is near and not the self pair, replace its
+// unrefined contribution in (ax, ay, az, pp) by the refined one. The
+// unrefined terms are recomputed with exactly the first pass's operations.
+// LAW 0: softened gravity (q.w = m_j); LAW 1: Lennard-Jones (s2 = sigma^2).
+template <int LAW = 0>
+__device__ __forceinline__ void correct_pair(const float4 q, const int jg, const int ig, const int i_end,
+                                             const float xi, const float yi, const float zi, const float eps2,
+                                             const float r2c, const float4* __restrict__ lo, float& ax, float& ay,
+                                             float& az, float& pp, const float s2 = 0.f) {
+  const float dx = q.x - xi;
+  const float dy = q.y - yi;
+  const float dz = q.z - zi;
+  const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
+  if (!(r2 < r2c) || ig >= i_end || jg < 0 || ig == jg) return;
+  float rx, ry, rz, rr2;
+  refine_pair(lo, ig, jg, dx, dy, dz, eps2, rx, ry, rz, rr2);
+  if (LAW == 0) {
+    const float iu = rsq_approx(r2);
+    const float msu = q.w * iu;
+    const float wu = msu * (iu * iu);
+    const float ir = rsq_approx(rr2);
+    const float msr = q.w * ir;
+    const float wr = msr * (ir * ir);
+    ax += fmaf(rx, wr, -(dx * wu));
+    ay += fmaf(ry, wr, -(dy * wu));
+    az += fmaf(rz, wr, -(dz * wu));
+    pp += msr - msu;
+  } else {
+    const float iu = rcp_approx(r2);
+    const float su2 = s2 * iu, su6 = su2 * (su2 * su2), su12 = su6 * su6;
+    const float wu = fmaf(su12, -2.f, su6) * iu;
+    const float ir = rcp_approx(rr2);
+    const float sr2 = s2 * ir, sr6 = sr2 * (sr2 * sr2), sr12 = sr6 * sr6;
+    const float wr = fmaf(sr12, -2.f, sr6) * ir;
+    ax += fmaf(rx, wr, -(dx * wu));
+    ay += fmaf(ry, wr, -(dy * wu));
+    az += fmaf(rz, wr, -(dz * wu));
+    pp += fmaf(sr6, -1.f, sr12) - fmaf(su6, -1.f, su12);
+  }
 }
 
 // Persistent-kernel work distribution: CTAs take items from counter[0]; the

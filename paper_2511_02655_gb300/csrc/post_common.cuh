@@ -1,0 +1,273 @@
+// Device helpers of the O(N) work around the all-pairs passes, shared by the
+// O(N) kernels (post_kernels.cu) and the force kernels' fused step epilogue
+// (force_kernels.cu): the per-body combine / kick / drift / staging / energy
+// terms of one body, the fixed-order CTA and per-system float64 sums, and the
+// last-arrival ticket.
+#pragma once
+
+#include <math.h>
+
+#include "nbody_internal.h"
+
+namespace nbody {
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Deterministic CTA sum of NV values per thread; result valid in thread 0.
+template <int NV, int THREADS>
+__device__ __forceinline__ void block_sum(double (&v)[NV]) {
+  __shared__ double red[THREADS / 32][NV];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) v[k] = warp_sum(v[k]);
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) red[wid][k] = v[k];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      double s = 0.0;
+      for (int w = 0; w < THREADS / 32; ++w) s += red[w][k];
+      v[k] = s;
+    }
+  }
+}
+
+// Reflecting walls of [0, box] ("boundary checking"): a coordinate that left
+// the box is mirrored back across the wall and its velocity component flips;
+// repeated (bounded) for steps that cross the box more than once.
+__device__ __forceinline__ void reflect(double& x, double& v, const double box) {
+  for (int k = 0; k < 64; ++k) {
+    if (x < 0.0) {
+      x = -x, v = -v;
+    } else if (x > box) {
+      x = 2.0 * box - x, v = -v;
+    } else {
+      return;
+    }
+  }
+}
+
+// Staging entry of body i. Mixed: float4 (x - c, m) rounded to float32 and,
+// when lo is given, the float32 remainders (x - c) - hi used by the near-pair
+// refinement of the force kernels. FP64: double4 (x, m).
+__device__ __forceinline__ void stage_store(int precision, void* stage, int i, double x, double y, double z,
+                                            double m, const double* c, void* lo = nullptr) {
+  if (precision == 1) {
+    const double X = x - c[0], Y = y - c[1], Z = z - c[2];
+    const float hx = (float)X, hy = (float)Y, hz = (float)Z;
+    static_cast<float4*>(stage)[i] = make_float4(hx, hy, hz, (float)m);
+    if (lo)
+      static_cast<float4*>(lo)[i] =
+          make_float4((float)(X - (double)hx), (float)(Y - (double)hy), (float)(Z - (double)hz), 0.f);
+  } else {
+    static_cast<double4_32a*>(stage)[i] = make_double4_32a(x, y, z, m);
+  }
+}
+
+// Final per-system sums of partials [n_parts][kEnergyVals] (one per chunk, or
+// per i-tile in the fused epilogue), one warp per system, lanes striding over
+// the system's range, then a fixed xor-shuffle reduction: the same order
+// whichever CTA runs it. The partials were written by other CTAs of the same
+// launch, so they are read from L2 (ld.global.cg).
+template <int NV, int THREADS, typename Emit>
+__device__ __forceinline__ void systems_final(const int32_t* sys_part, const int n_sys, const double* part,
+                                              const int n_parts, unsigned* status, Emit emit) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int sy = wid; sy < n_sys; sy += THREADS / 32) {
+    double v[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] = 0.0;
+    // NBODY_DEBUG builds: the system's range lies inside the partials
+    const bool ok = nb_debug_ok(sys_part[sy] >= 0 && sys_part[sy] <= sys_part[sy + 1] && sys_part[sy + 1] <= n_parts,
+                                lane == 0 ? status : nullptr);
+    for (int c = sys_part[sy] + lane; ok && c < sys_part[sy + 1]; c += 32) {
+#pragma unroll
+      for (int k = 0; k < NV; ++k) v[k] += __ldcg(part + (int64_t)c * kEnergyVals + k);
+    }
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] = warp_sum(v[k]);
+    if (lane == 0) emit(sy, v);
+  }
+}
+
+// True in every thread of the CTA that arrives last of `expected` arrivals at
+// the ticket `done` (its results were published with a fence before the
+// ticket); that CTA resets the ticket for the next launch. No CTA waits.
+__device__ __forceinline__ bool last_of(unsigned* done, const unsigned expected) {
+  __shared__ bool s_last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    s_last = atomicAdd(done, 1u) == expected - 1u;
+    if (s_last) *done = 0u;
+  }
+  __syncthreads();
+  return s_last;
+}
+
+__device__ __forceinline__ void emit_energy(double* out, const int sy, const double (&v)[kEnergyVals]) {
+  double* o = out + 9 * (int64_t)sy;
+  o[0] = v[0] + v[1];
+  o[1] = v[0];
+  o[2] = v[1];
+#pragma unroll
+  for (int k = 2; k < kEnergyVals; ++k) o[k + 1] = v[k];
+}
+
+// The O(N) work of one body i in the modes of P (PostMode): with kCombine its
+// summed partials (sx, sy, sz, sp) become a = G S (or the Lennard-Jones
+// scaling) and phi; then the closing half-kick, the energy or virial terms
+// (accumulated into e), the opening half-kick and drift of the next step (with
+// the walls), and the staging entry of the new position. cen is the system's
+// staging origin. Returns true if a combined value is not finite.
+__device__ __forceinline__ bool post_body(const PostLaunch& P, const int i, const double* cen, const double sx,
+                                          const double sy, const double sz, const double sp,
+                                          double (&e)[kEnergyVals]) {
+  const unsigned mode = P.mode;
+  bool bad = false;
+  // every load of the body first, so that they are in flight together (x, v, m
+  // and a are distinct arrays; nothing below is stored before it is read)
+  const bool need_x = mode & (kKickEnd | kEnergy | kDrift | kStage | kVirial);
+  const bool need_v = mode & (kKickEnd | kEnergy | kDrift | kVirial);
+  const bool need_m = need_x || (mode & kCombine && P.law != 0);
+  double x0 = 0.0, x1 = 0.0, x2 = 0.0, v0 = 0.0, v1 = 0.0, v2 = 0.0, m = 0.0;
+  if (need_x) x0 = P.x[3 * i + 0], x1 = P.x[3 * i + 1], x2 = P.x[3 * i + 2];
+  if (need_v) v0 = P.v[3 * i + 0], v1 = P.v[3 * i + 1], v2 = P.v[3 * i + 2];
+  if (need_m) m = P.m[i];
+  double ax = 0.0, ay = 0.0, az = 0.0, ph = 0.0;
+  if (mode & kCombine) {
+    if (P.law == 0) {  // softened gravity
+      ax = P.G * sx, ay = P.G * sy, az = P.G * sz, ph = -P.G * sp;
+    } else {  // Lennard-Jones: per unit mass of body i
+      const double ca = 24.0 * P.lj_eps / m, cp = 4.0 * P.lj_eps / m;
+      ax = ca * sx, ay = ca * sy, az = ca * sz, ph = cp * sp;
+    }
+    P.a[3 * i + 0] = ax, P.a[3 * i + 1] = ay, P.a[3 * i + 2] = az;
+    if (P.phi) P.phi[i] = ph;
+    bad = !(isfinite(ax) && isfinite(ay) && isfinite(az) && isfinite(ph));
+  } else if (mode & (kKickEnd | kDrift)) {
+    ax = P.a[3 * i + 0], ay = P.a[3 * i + 1], az = P.a[3 * i + 2];
+  }
+  if (mode & kVirial) {
+    e[0] += 0.5 * m * (v0 * v0 + v1 * v1 + v2 * v2);
+    e[1] += m * (x0 * ax + x1 * ay + x2 * az);
+  }
+  if (!(mode & (kKickEnd | kEnergy | kDrift | kStage))) return bad;
+  if (mode & (kKickEnd | kEnergy | kDrift)) {
+    if (mode & kKickEnd) {
+      v0 += P.half_dt * ax, v1 += P.half_dt * ay, v2 += P.half_dt * az;
+    }
+    if (mode & kEnergy) {
+      e[0] += 0.5 * m * (v0 * v0 + v1 * v1 + v2 * v2);
+      e[1] += 0.5 * m * ph;
+      e[2] += m * v0, e[3] += m * v1, e[4] += m * v2;
+      e[5] += m * (x1 * v2 - x2 * v1);
+      e[6] += m * (x2 * v0 - x0 * v2);
+      e[7] += m * (x0 * v1 - x1 * v0);
+    }
+    if (mode & kDrift) {
+      v0 += P.half_dt * ax, v1 += P.half_dt * ay, v2 += P.half_dt * az;
+      x0 += P.dt * v0, x1 += P.dt * v1, x2 += P.dt * v2;
+      if (P.box > 0.0) {
+        reflect(x0, v0, P.box);
+        reflect(x1, v1, P.box);
+        reflect(x2, v2, P.box);
+      }
+      P.x[3 * i + 0] = x0, P.x[3 * i + 1] = x1, P.x[3 * i + 2] = x2;
+      if (P.x_copy) P.x_copy[3 * i + 0] = x0, P.x_copy[3 * i + 1] = x1, P.x_copy[3 * i + 2] = x2;
+    }
+    if (mode & (kKickEnd | kDrift)) P.v[3 * i + 0] = v0, P.v[3 * i + 1] = v1, P.v[3 * i + 2] = v2;
+  }
+  if (mode & kStage) stage_store(P.precision, P.stage, i, x0, x1, x2, m, cen, P.stage_lo);
+  return bad;
+}
+
+// float64 quadruple from L2 (data written by other CTAs of the same launch)
+__device__ __forceinline__ double4_32a ldcg_d4(const double4_32a* p) {
+  const double2 a = __ldcg(reinterpret_cast<const double2*>(p));
+  const double2 b = __ldcg(reinterpret_cast<const double2*>(p) + 1);
+  return make_double4_32a(a.x, a.y, b.x, b.y);
+}
+
+// Fused step epilogue of a force kernel, called by every thread of the CTA
+// after it finished work item w, with own[r] = the item's float64 partial of
+// its r-th body (i_begin + threadIdx.x + r BLOCK), already stored to the
+// item's slice unless the system has a single slice. The CTA that completes
+// the tile's last slice adds the tile's slices in slice order (the order of
+// k_post, so the results are the same bit for bit) and runs post_body for its
+// bodies; the energy partials of the tile go to L.tpart, and the last tile's
+// CTA forms the per-system records. No CTA waits on another.
+constexpr int kFuseBatch = 1;  // slice partials loaded together by the fused epilogue
+
+template <int BLOCK, int R>
+__device__ __forceinline__ void fused_epilogue(const PairLaunch& L, const PostLaunch& P, const WorkItem& w,
+                                               const double4_32a (&own)[R]) {
+  __shared__ int s_fin;
+  __syncthreads();  // every partial store of this item is issued
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned done = atomicAdd(&L.tile_done[w.tile], 1u);
+    s_fin = done == (unsigned)w.n_slices - 1u;
+    if (s_fin) L.tile_done[w.tile] = 0u;  // no other item of this tile is left in this launch
+  }
+  __syncthreads();
+  if (!s_fin) return;
+  __threadfence();
+  const double4_32a* part = reinterpret_cast<const double4_32a*>(L.part);
+  const double* cen = P.centre + 3 * w.sys;
+  double e[kEnergyVals];
+#pragma unroll
+  for (int k = 0; k < kEnergyVals; ++k) e[k] = 0.0;
+  bool bad = false;
+  // one body at a time (a loop the compiler keeps rolled), so that the epilogue
+  // needs fewer registers than the pair loop and leaves the kernel's count alone
+#pragma unroll 1
+  for (int r = 0; r < R; ++r) {
+    const int i = w.i_begin + (int)threadIdx.x + r * BLOCK;
+    if (i >= w.i_end) continue;
+    double sx = 0.0, sy = 0.0, sz = 0.0, sp = 0.0;
+    if (w.n_slices == 1) {  // the item's own partial is the sum
+      double4_32a o = own[0];
+#pragma unroll
+      for (int k = 1; k < R; ++k)
+        if (r == k) o = own[k];
+      sx = o.x, sy = o.y, sz = o.z, sp = o.w;
+    } else {
+      // every slice was stored (this item's too): batches of loads in flight
+      // together, added in slice order
+#pragma unroll 1
+      for (int s0 = 0; s0 < w.n_slices; s0 += kFuseBatch) {
+        double4_32a q[kFuseBatch];
+#pragma unroll
+        for (int u = 0; u < kFuseBatch; ++u)
+          if (s0 + u < w.n_slices) q[u] = ldcg_d4(part + (int64_t)(s0 + u) * L.n_total + i);
+#pragma unroll
+        for (int u = 0; u < kFuseBatch; ++u)
+          if (s0 + u < w.n_slices) sx += q[u].x, sy += q[u].y, sz += q[u].z, sp += q[u].w;
+      }
+    }
+    bad |= post_body(P, i, cen, sx, sy, sz, sp, e);
+  }
+  if (bad) atomicOr(P.status, kFlagNonFinite);
+  if (P.mode & kEnergy) {
+    block_sum<kEnergyVals, BLOCK>(e);
+    if (threadIdx.x == 0) {
+#pragma unroll
+      for (int k = 0; k < kEnergyVals; ++k) L.tpart[(int64_t)w.tile * kEnergyVals + k] = e[k];
+    }
+    if (P.eout && last_of(L.fin_done, (unsigned)L.n_tiles)) {
+      __threadfence();
+      systems_final<kEnergyVals, BLOCK>(L.sys_tile, P.n_sys, L.tpart, L.n_tiles, P.status,
+                                        [&](int sy, const double (&v)[kEnergyVals]) { emit_energy(P.eout, sy, v); });
+    }
+  }
+}
+
+}  // namespace nbody

@@ -9,116 +9,15 @@
 #include <algorithm>
 
 #include "nbody_internal.h"
+#include "post_common.cuh"
 
 namespace nbody {
 namespace {
 
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
-// Deterministic CTA sum of NV values per thread; result valid in thread 0.
-template <int NV, int THREADS>
-__device__ __forceinline__ void block_sum(double (&v)[NV]) {
-  __shared__ double red[THREADS / 32][NV];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-  for (int k = 0; k < NV; ++k) v[k] = warp_sum(v[k]);
-  if (lane == 0) {
-#pragma unroll
-    for (int k = 0; k < NV; ++k) red[wid][k] = v[k];
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-#pragma unroll
-    for (int k = 0; k < NV; ++k) {
-      double s = 0.0;
-      for (int w = 0; w < THREADS / 32; ++w) s += red[w][k];
-      v[k] = s;
-    }
-  }
-}
-
-// Reflecting walls of [0, box] ("boundary checking"): a coordinate that left
-// the box is mirrored back across the wall and its velocity component flips;
-// repeated (bounded) for steps that cross the box more than once.
-__device__ __forceinline__ void reflect(double& x, double& v, const double box) {
-  for (int k = 0; k < 64; ++k) {
-    if (x < 0.0) {
-      x = -x, v = -v;
-    } else if (x > box) {
-      x = 2.0 * box - x, v = -v;
-    } else {
-      return;
-    }
-  }
-}
-
-// Staging entry of body i. Mixed: float4 (x - c, m) rounded to float32 and,
-// when lo is given, the float32 remainders (x - c) - hi used by the near-pair
-// refinement of the force kernels. FP64: double4 (x, m).
-__device__ __forceinline__ void stage_store(int precision, void* stage, int i, double x, double y, double z,
-                                            double m, const double* c, void* lo = nullptr) {
-  if (precision == 1) {
-    const double X = x - c[0], Y = y - c[1], Z = z - c[2];
-    const float hx = (float)X, hy = (float)Y, hz = (float)Z;
-    static_cast<float4*>(stage)[i] = make_float4(hx, hy, hz, (float)m);
-    if (lo)
-      static_cast<float4*>(lo)[i] =
-          make_float4((float)(X - (double)hx), (float)(Y - (double)hy), (float)(Z - (double)hz), 0.f);
-  } else {
-    static_cast<double4_32a*>(stage)[i] = make_double4_32a(x, y, z, m);
-  }
-}
-
-// Final per-system sums of chunk partials [n_chunks][kEnergyVals], one warp per
-// system, lanes striding over the system's chunks, then a fixed xor-shuffle
-// reduction: the same order whichever CTA runs it.
-template <int NV, typename Emit>
-__device__ __forceinline__ void systems_final(const int32_t* sys_chunk, const int n_sys, const double* cpart,
-                                              Emit emit) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int sy = wid; sy < n_sys; sy += kPostThreads / 32) {
-    double v[NV];
-#pragma unroll
-    for (int k = 0; k < NV; ++k) v[k] = 0.0;
-    for (int c = sys_chunk[sy] + lane; c < sys_chunk[sy + 1]; c += 32) {
-#pragma unroll
-      for (int k = 0; k < NV; ++k) v[k] += cpart[(int64_t)c * kEnergyVals + k];
-    }
-#pragma unroll
-    for (int k = 0; k < NV; ++k) v[k] = warp_sum(v[k]);
-    if (lane == 0) emit(sy, v);
-  }
-}
-
-// True in every thread of the CTA that retires last among the grid's CTAs (its
-// partials were published with a fence before the ticket); it resets the ticket.
-__device__ __forceinline__ bool last_cta(unsigned* done) {
-  __shared__ bool s_last;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    s_last = atomicAdd(done, 1u) == gridDim.x - 1;
-  }
-  __syncthreads();
-  if (s_last && threadIdx.x == 0) *done = 0u;
-  return s_last;
-}
-
-__device__ __forceinline__ void emit_energy(double* out, const int sy, const double (&v)[kEnergyVals]) {
-  double* o = out + 9 * (int64_t)sy;
-  o[0] = v[0] + v[1];
-  o[1] = v[0];
-  o[2] = v[1];
-#pragma unroll
-  for (int k = 2; k < kEnergyVals; ++k) o[k + 1] = v[k];
-}
-
 __global__ void __launch_bounds__(kPostThreads) k_post(const PostLaunch P) {
-  const Chunk c = P.chunks[blockIdx.x];
+  Chunk c = P.chunks[blockIdx.x];
+  if (!chunk_ok(c, P.n_total, P.n_sys, (P.mode & kCombine) ? P.part_slices : 0, P.status))
+    c.begin = c.end = 0;  // NBODY_DEBUG builds only: processed as an empty chunk
   const double4_32a* part = reinterpret_cast<const double4_32a*>(P.part);
   const double* cen = P.centre + 3 * c.sys;
   double e[kEnergyVals];
@@ -128,63 +27,15 @@ __global__ void __launch_bounds__(kPostThreads) k_post(const PostLaunch P) {
   const unsigned mode = P.mode;
 
   for (int i = c.begin + (int)threadIdx.x; i < c.end; i += kPostThreads) {
-    double ax = 0.0, ay = 0.0, az = 0.0, ph = 0.0;
+    double sx = 0.0, sy = 0.0, sz = 0.0, sp = 0.0;
     if (mode & kCombine) {
-      double sx = 0.0, sy = 0.0, sz = 0.0, sp = 0.0;
 #pragma unroll 8
       for (int s = 0; s < c.n_slices; ++s) {
         const double4_32a q = part[(int64_t)s * P.n_total + i];
         sx += q.x, sy += q.y, sz += q.z, sp += q.w;
       }
-      if (P.law == 0) {  // softened gravity
-        ax = P.G * sx, ay = P.G * sy, az = P.G * sz, ph = -P.G * sp;
-      } else {  // Lennard-Jones: per unit mass of body i
-        const double mi = P.m[i];
-        const double ca = 24.0 * P.lj_eps / mi, cp = 4.0 * P.lj_eps / mi;
-        ax = ca * sx, ay = ca * sy, az = ca * sz, ph = cp * sp;
-      }
-      P.a[3 * i + 0] = ax, P.a[3 * i + 1] = ay, P.a[3 * i + 2] = az;
-      if (P.phi) P.phi[i] = ph;
-      bad |= !(isfinite(ax) && isfinite(ay) && isfinite(az) && isfinite(ph));
-    } else if (mode & (kKickEnd | kDrift)) {
-      ax = P.a[3 * i + 0], ay = P.a[3 * i + 1], az = P.a[3 * i + 2];
     }
-    if (mode & kVirial) {
-      const double mi = P.m[i];
-      const double v0 = P.v[3 * i + 0], v1 = P.v[3 * i + 1], v2 = P.v[3 * i + 2];
-      e[0] += 0.5 * mi * (v0 * v0 + v1 * v1 + v2 * v2);
-      e[1] += mi * (P.x[3 * i + 0] * ax + P.x[3 * i + 1] * ay + P.x[3 * i + 2] * az);
-    }
-    if (!(mode & (kKickEnd | kEnergy | kDrift | kStage))) continue;
-    double x0 = P.x[3 * i + 0], x1 = P.x[3 * i + 1], x2 = P.x[3 * i + 2];
-    const double m = P.m[i];
-    if (mode & (kKickEnd | kEnergy | kDrift)) {
-      double v0 = P.v[3 * i + 0], v1 = P.v[3 * i + 1], v2 = P.v[3 * i + 2];
-      if (mode & kKickEnd) {
-        v0 += P.half_dt * ax, v1 += P.half_dt * ay, v2 += P.half_dt * az;
-      }
-      if (mode & kEnergy) {
-        e[0] += 0.5 * m * (v0 * v0 + v1 * v1 + v2 * v2);
-        e[1] += 0.5 * m * ph;
-        e[2] += m * v0, e[3] += m * v1, e[4] += m * v2;
-        e[5] += m * (x1 * v2 - x2 * v1);
-        e[6] += m * (x2 * v0 - x0 * v2);
-        e[7] += m * (x0 * v1 - x1 * v0);
-      }
-      if (mode & kDrift) {
-        v0 += P.half_dt * ax, v1 += P.half_dt * ay, v2 += P.half_dt * az;
-        x0 += P.dt * v0, x1 += P.dt * v1, x2 += P.dt * v2;
-        if (P.box > 0.0) {
-          reflect(x0, v0, P.box);
-          reflect(x1, v1, P.box);
-          reflect(x2, v2, P.box);
-        }
-        P.x[3 * i + 0] = x0, P.x[3 * i + 1] = x1, P.x[3 * i + 2] = x2;
-        if (P.x_copy) P.x_copy[3 * i + 0] = x0, P.x_copy[3 * i + 1] = x1, P.x_copy[3 * i + 2] = x2;
-      }
-      if (mode & (kKickEnd | kDrift)) P.v[3 * i + 0] = v0, P.v[3 * i + 1] = v1, P.v[3 * i + 2] = v2;
-    }
-    if (mode & kStage) stage_store(P.precision, P.stage, i, x0, x1, x2, m, cen, P.stage_lo);
+    bad |= post_body(P, i, cen, sx, sy, sz, sp, e);
   }
   if (bad) atomicOr(P.status, kFlagNonFinite);
   if (mode & kVirial) {
@@ -192,14 +43,15 @@ __global__ void __launch_bounds__(kPostThreads) k_post(const PostLaunch P) {
     block_sum<2, kPostThreads>(kw);
     if (threadIdx.x == 0) P.epart[(int64_t)blockIdx.x * kEnergyVals + 0] = kw[0],
                           P.epart[(int64_t)blockIdx.x * kEnergyVals + 1] = kw[1];
-    if (last_cta(P.done)) {
+    if (last_of(P.done, gridDim.x)) {
       __threadfence();
-      systems_final<2>(P.sys_chunk, P.n_sys, P.epart, [&](int sy, const double (&v)[2]) {
-        double* o = P.vout + 3 * (int64_t)sy;
-        o[0] = v[0];
-        o[1] = v[1];
-        o[2] = v[1] != 0.0 ? -2.0 * v[0] / v[1] : 0.0;
-      });
+      systems_final<2, kPostThreads>(P.sys_chunk, P.n_sys, P.epart, gridDim.x, P.status,
+                                     [&](int sy, const double (&v)[2]) {
+                                       double* o = P.vout + 3 * (int64_t)sy;
+                                       o[0] = v[0];
+                                       o[1] = v[1];
+                                       o[2] = v[1] != 0.0 ? -2.0 * v[0] / v[1] : 0.0;
+                                     });
     }
     return;
   }
@@ -210,10 +62,12 @@ __global__ void __launch_bounds__(kPostThreads) k_post(const PostLaunch P) {
       for (int k = 0; k < kEnergyVals; ++k) P.epart[(int64_t)blockIdx.x * kEnergyVals + k] = e[k];
     }
     // the last CTA to finish forms the per-system records (no separate launch)
-    if (P.eout && last_cta(P.done)) {
+    if (P.eout && last_of(P.done, gridDim.x)) {
       __threadfence();
-      systems_final<kEnergyVals>(P.sys_chunk, P.n_sys, P.epart,
-                                 [&](int sy, const double (&v)[kEnergyVals]) { emit_energy(P.eout, sy, v); });
+      systems_final<kEnergyVals, kPostThreads>(P.sys_chunk, P.n_sys, P.epart, gridDim.x, P.status,
+                                               [&](int sy, const double (&v)[kEnergyVals]) {
+                                                 emit_energy(P.eout, sy, v);
+                                               });
     }
   }
 }
@@ -224,8 +78,9 @@ __global__ void __launch_bounds__(kPostThreads) k_post(const PostLaunch P) {
 __global__ void __launch_bounds__(kPostThreads) k_centre(const Chunk* chunks, const int32_t* sys_chunk,
                                                          const int64_t* off, const int n_sys, const double* x,
                                                          const double* m, double* cpart, double* centre,
-                                                         unsigned* done) {
-  const Chunk c = chunks[blockIdx.x];
+                                                         unsigned* done, const int64_t n_total, unsigned* status) {
+  Chunk c = chunks[blockIdx.x];
+  if (!chunk_ok(c, n_total, n_sys, 0, status)) c.begin = c.end = 0;  // NBODY_DEBUG builds only
   double v[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
   for (int i = c.begin + (int)threadIdx.x; i < c.end; i += kPostThreads) {
     const double mi = m[i];
@@ -238,9 +93,9 @@ __global__ void __launch_bounds__(kPostThreads) k_centre(const Chunk* chunks, co
 #pragma unroll
     for (int k = 0; k < 7; ++k) cpart[(int64_t)blockIdx.x * kEnergyVals + k] = v[k];
   }
-  if (!last_cta(done)) return;
+  if (!last_of(done, gridDim.x)) return;
   __threadfence();
-  systems_final<7>(sys_chunk, n_sys, cpart, [&](int sy, const double (&w)[7]) {
+  systems_final<7, kPostThreads>(sys_chunk, n_sys, cpart, gridDim.x, status, [&](int sy, const double (&w)[7]) {
     const int64_t n = off[sy + 1] - off[sy];
     double c0 = 0.0, c1 = 0.0, c2 = 0.0;
     if (w[3] > 0.0 && isfinite(w[3])) {
@@ -254,7 +109,8 @@ __global__ void __launch_bounds__(kPostThreads) k_centre(const Chunk* chunks, co
 }
 
 __global__ void __launch_bounds__(kPostThreads) k_adj_update(const AdjLaunch A) {
-  const Chunk c = A.chunks[blockIdx.x];
+  Chunk c = A.chunks[blockIdx.x];
+  if (!chunk_ok(c, A.n_total, A.n_sys, A.part_slices, A.status)) c.begin = c.end = 0;  // NBODY_DEBUG builds only
   const double4_32a* part = reinterpret_cast<const double4_32a*>(A.part);
   const double* cen = A.centre + 3 * c.sys;
   const int kw = A.g_params ? 3 : 2;  // double4 per body and slice
@@ -295,7 +151,7 @@ __global__ void __launch_bounds__(kPostThreads) k_adj_update(const AdjLaunch A) 
     }
     if (A.x_next)
       stage_store(A.precision, A.stage_x, i, A.x_next[3 * i + 0], A.x_next[3 * i + 1], A.x_next[3 * i + 2], mi,
-                  cen);
+                  cen, A.stage_lo);
   }
   if (bad) atomicOr(A.status, kFlagNonFinite);
   if (!A.g_params) return;
@@ -304,9 +160,9 @@ __global__ void __launch_bounds__(kPostThreads) k_adj_update(const AdjLaunch A) 
   block_sum<2, kPostThreads>(pv);
   if (threadIdx.x == 0) A.cpart[(int64_t)blockIdx.x * kEnergyVals + 0] = pv[0],
                         A.cpart[(int64_t)blockIdx.x * kEnergyVals + 1] = pv[1];
-  if (!last_cta(A.done)) return;
+  if (!last_of(A.done, gridDim.x)) return;
   __threadfence();
-  systems_final<2>(A.sys_chunk, A.n_sys, A.cpart, [&](int sy, const double (&v)[2]) {
+  systems_final<2, kPostThreads>(A.sys_chunk, A.n_sys, A.cpart, gridDim.x, A.status, [&](int sy, const double (&v)[2]) {
     const double dG = A.coef * v[0], de = A.coef * (-3.0 * A.G * A.eps) * v[1];
     if (!(isfinite(dG) && isfinite(de))) atomicOr(A.status, kFlagNonFinite);
     A.g_params[2 * sy + 0] += dG;
@@ -316,13 +172,15 @@ __global__ void __launch_bounds__(kPostThreads) k_adj_update(const AdjLaunch A) 
 
 __global__ void __launch_bounds__(kPostThreads) k_stage_vec(const Chunk* chunks, int precision, const double* vec,
                                                             const double* m, const double* centre, void* stage,
-                                                            int as_position) {
-  const Chunk c = chunks[blockIdx.x];
+                                                            void* stage_lo, int as_position, const int64_t n_total,
+                                                            const int n_sys, unsigned* status) {
+  Chunk c = chunks[blockIdx.x];
+  if (!chunk_ok(c, n_total, n_sys, 0, status)) c.begin = c.end = 0;  // NBODY_DEBUG builds only
   const double* cen = centre + 3 * c.sys;
   for (int i = c.begin + (int)threadIdx.x; i < c.end; i += kPostThreads) {
     const double v0 = vec[3 * i + 0], v1 = vec[3 * i + 1], v2 = vec[3 * i + 2];
     if (as_position) {
-      stage_store(precision, stage, i, v0, v1, v2, m[i], cen);
+      stage_store(precision, stage, i, v0, v1, v2, m[i], cen, stage_lo);
     } else if (precision == 1) {
       static_cast<float4*>(stage)[i] = make_float4((float)v0, (float)v1, (float)v2, 0.f);
     } else {
@@ -364,9 +222,10 @@ cudaError_t launch_post(const PostLaunch& P, cudaStream_t st) {
 
 cudaError_t launch_centre(const Chunk* chunks, int n_chunks, const int32_t* sys_chunk, const int64_t* off, int n_sys,
                           const double* x, const double* m, double* cpart, double* centre, unsigned* done,
-                          cudaStream_t st) {
+                          int64_t n_total, unsigned* status, cudaStream_t st) {
   if (n_sys <= 0 || n_chunks <= 0) return cudaSuccess;
-  k_centre<<<n_chunks, kPostThreads, 0, st>>>(chunks, sys_chunk, off, n_sys, x, m, cpart, centre, done);
+  k_centre<<<n_chunks, kPostThreads, 0, st>>>(chunks, sys_chunk, off, n_sys, x, m, cpart, centre, done, n_total,
+                                              status);
   return cudaGetLastError();
 }
 
@@ -377,9 +236,11 @@ cudaError_t launch_adj_update(const AdjLaunch& A, cudaStream_t st) {
 }
 
 cudaError_t launch_stage_vec(const Chunk* chunks, int n_chunks, int precision, const double* vec, const double* m,
-                             const double* centre, void* stage, int as_position, cudaStream_t st) {
+                             const double* centre, void* stage, void* stage_lo, int as_position, int64_t n_total,
+                             int n_sys, unsigned* status, cudaStream_t st) {
   if (n_chunks <= 0) return cudaSuccess;
-  k_stage_vec<<<n_chunks, kPostThreads, 0, st>>>(chunks, precision, vec, m, centre, stage, as_position);
+  k_stage_vec<<<n_chunks, kPostThreads, 0, st>>>(chunks, precision, vec, m, centre, stage, stage_lo, as_position,
+                                                 n_total, n_sys, status);
   return cudaGetLastError();
 }
 

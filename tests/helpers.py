@@ -20,3 +20,21 @@ def to_dev(*arrs, device="cuda:0"):
 
 def to_np(*ts):
     return tuple(t.detach().cpu().numpy() for t in ts)
+
+
+def elem_rel_err(g, g_ref, guard=1e-3):
+    """Per-element relative error |g - g_ref| / max(|g_ref|, guard * rms(g_ref)), over every
+    component of every body (cancellation guard as in force_rel_err)."""
+    g = np.asarray(g, dtype=np.float64).ravel()
+    g_ref = np.asarray(g_ref, dtype=np.float64).ravel()
+    rms = np.sqrt(np.mean(g_ref ** 2)) if g_ref.size else 1.0
+    return np.abs(g - g_ref) / np.maximum(np.abs(g_ref), guard * rms)
+
+
+def assert_elem_close(g, g_ref, tol, what=""):
+    """Every element within tol (elem_rel_err); the message names the worst element."""
+    e = elem_rel_err(g, g_ref)
+    if e.size:
+        k = int(np.argmax(e))
+        assert e[k] <= tol, f"{what}: max per-element rel err {e[k]:.3e} at flat index {k} (tol {tol:.1e})"
+    return e

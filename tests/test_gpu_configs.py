@@ -12,11 +12,13 @@ import pytest
 
 import oracle
 from paper_2511_02655_gb300 import inputs
-from helpers import force_rel_err, to_dev, to_np
+from helpers import assert_elem_close, force_rel_err, to_dev, to_np
 
 pytestmark = pytest.mark.gpu
 
 MIX_MED, MIX_MAX, FP64_TOL = 1e-6, 1e-4, 1e-12
+# the 1M two-sphere case: oracle forces on this many sampled bodies (each against all N)
+SAMPLE_1M = 16384
 
 
 def _sampled_err(x, m, a_gpu, G, eps, k=1024, seed=17):
@@ -69,18 +71,27 @@ def test_two_spheres_1m_mixed_10_steps(nb):
     xt, vt, mt = to_dev(x, v, m)
     at = torch.empty_like(xt)
     nb.nbody_forces(ctx, xt, mt, at)
-    e0 = _sampled_err(x, m, at.cpu().numpy(), G, eps)
+    e0 = _sampled_err(x, m, at.cpu().numpy(), G, eps, k=SAMPLE_1M)
     assert np.median(e0) <= MIX_MED and e0.max() <= MIX_MAX, (np.median(e0), e0.max())
     E0 = nb.nbody_energy(ctx, xt, vt, mt).cpu().numpy()[0]
     log = nb.nbody_step(ctx, xt, vt, mt, at, True, T)
     nb.nbody_sync(ctx)
     xf, af = to_np(xt, at)
-    e1 = _sampled_err(xf, m, af, G, eps, seed=19)
+    e1 = _sampled_err(xf, m, af, G, eps, k=SAMPLE_1M, seed=19)
     assert np.median(e1) <= MIX_MED and e1.max() <= MIX_MAX, (np.median(e1), e1.max())
     E1 = log.cpu().numpy()[-1, 0]
     assert abs(E1[0] - E0[0]) <= 1e-5 * abs(E0[0])
     np.testing.assert_allclose(E1[3:6], E0[3:6], atol=1e-9)
     ctx.close()
+
+
+# positions and velocities after the 50 ensemble steps against the oracle's KDK, per element
+# (relative, guard 1e-3 of the rms element): the mixed force error (<= 1e-4 per body, ~1e-7
+# typical) moves x by ~ t^2 |da| / 2 and v by ~ t |da| over t = 0.05
+ENS_X_TOL, ENS_V_TOL = 1e-6, 1e-5
+# largest relative energy drift of any system over the 50 steps (leapfrog error plus the
+# mixed energy evaluation); measured maximum 9.6e-6 on GB300, bound at about 3x that
+ENS_DRIFT = 3e-5
 
 
 @pytest.mark.parametrize("graph", [False, True])
@@ -102,23 +113,25 @@ def test_ensemble_512_systems_50_steps(nb, graph):
     E1 = log.cpu().numpy()[0]
     sizes = np.diff(off)
     order = np.argsort(sizes)
-    for s in list(order[:20]) + list(order[-3:]):  # the 20 smallest and the 3 largest systems
+    # forces at the start and at the end on sampled bodies: the 20 smallest and the 3 largest systems
+    for s in list(order[:20]) + list(order[-3:]):
         b, e = off[s], off[s + 1]
         k = min(256, e - b)
         for xx, aa, seed in ((ens.x[b:e], a0[b:e], 1), (xf[b:e], af[b:e], 2)):
             err = _sampled_err(xx, ens.m[b:e], aa, G, eps, k=k, seed=seed)
             assert err.max() <= MIX_MAX and np.median(err) <= MIX_MED, (s, sizes[s], err.max())
+    # whole trajectories against the oracle's KDK: the 20 smallest systems and the two closest
+    # to 2048 bodies; x, v per element and a per body
+    near2k = [int(i) for i in np.argsort(np.abs(sizes - 2048))[:2]]
+    for s in list(order[:20]) + near2k:
+        b, e = off[s], off[s + 1]
+        xr, vr, ar, _ = oracle.kdk(ens.x[b:e], ens.v[b:e], ens.m[b:e], G, eps, dt, T)
+        assert_elem_close(xf[b:e], xr, ENS_X_TOL, f"x of system {s} (N={sizes[s]})")
+        assert_elem_close(vf[b:e], vr, ENS_V_TOL, f"v of system {s} (N={sizes[s]})")
+        err = force_rel_err(af[b:e], ar)
+        assert err.max() <= MIX_MAX and np.median(err) <= MIX_MED, (s, sizes[s], err.max())
     # conservation per system: momentum stays ~0, energy drift small
     assert np.abs(E1[:, 3:6]).max() < 1e-9
     drift = np.abs(E1[:, 0] - E0[:, 0]) / np.abs(E0[:, 0])
-    assert drift.max() < 1e-3, drift.max()
-    # a batched step equals each system run on its own context (same kernels, own tiling) to rounding
-    for s in (int(np.argmax(sizes)), int(np.argmin(sizes))):
-        b, e = off[s], off[s + 1]
-        c1 = nb.nbody_init(G=G, eps=eps, dt=dt, precision=nb.MIXED, n=e - b)
-        x1, v1, m1 = to_dev(ens.x[b:e], ens.v[b:e], ens.m[b:e])
-        a1 = torch.empty_like(x1)
-        nb.nbody_step(c1, x1, v1, m1, a1, False, T)
-        assert np.abs(x1.cpu().numpy() - xf[b:e]).max() < 1e-9
-        c1.close()
+    assert drift.max() < ENS_DRIFT, drift.max()
     ctx.close()

@@ -10,12 +10,22 @@ import pytest
 
 import oracle
 from paper_2511_02655_gb300 import inputs
-from helpers import force_rel_err, to_dev, to_np
+from helpers import assert_elem_close, force_rel_err, to_dev, to_np
 
 pytestmark = pytest.mark.gpu
 
 FP64_TOL = 1e-12
 MIX_MED, MIX_MAX = 1e-6, 1e-4
+# mixed potential, per body: its pair terms all have the same sign, so a j-tile's float32 sum of
+# J <= 512 terms is good to (J - 1) 2^-24 < 3.1e-5 relative (recursive summation bound; it is
+# approached when one near pair dominates and the tile's small terms are added after it), and
+# the compensated fold across tiles adds ~2^-24: max 3e-5, median 1e-6 per body
+MIX_PHI_MED, MIX_PHI_MAX = 1e-6, 3e-5
+
+
+def _check_mixed_phi(phi, phi_ref):
+    e = assert_elem_close(phi, phi_ref, MIX_PHI_MAX, "phi")
+    assert np.median(e) <= MIX_PHI_MED, np.median(e)
 
 
 def _forces(nb, prec, x, m, G, eps, offsets=None, **kw):
@@ -37,7 +47,7 @@ def test_fp64_forces_n1024(nb):
     _, a, phi = _forces(nb, nb.FP64, x, m, 1.0, 0.01)
     a_ref, phi_ref = oracle.forces(x, m, G=1.0, eps=0.01)
     assert force_rel_err(a, a_ref).max() <= FP64_TOL
-    assert np.abs(phi - phi_ref).max() <= FP64_TOL * np.abs(phi_ref).max()
+    assert_elem_close(phi, phi_ref, FP64_TOL, "phi")
 
 
 def test_mixed_forces_n1024(nb):
@@ -46,7 +56,7 @@ def test_mixed_forces_n1024(nb):
     a_ref, phi_ref = oracle.forces(x, m, G=1.0, eps=0.01)
     e = force_rel_err(a, a_ref)
     assert np.median(e) <= MIX_MED and e.max() <= MIX_MAX, (np.median(e), e.max())
-    assert np.abs(phi - phi_ref).max() <= 1e-5 * np.abs(phi_ref).max()
+    _check_mixed_phi(phi, phi_ref)
 
 
 @pytest.mark.parametrize("prec", [0, 1])
@@ -110,8 +120,10 @@ def test_ragged_sizes(nb, n, prec):
     e = force_rel_err(a, a_ref)
     if prec == nb.FP64:
         assert e.max() <= FP64_TOL
+        assert_elem_close(phi, phi_ref, FP64_TOL, "phi")
     else:
         assert np.median(e) <= MIX_MED and e.max() <= MIX_MAX
+        _check_mixed_phi(phi, phi_ref)
 
 
 @pytest.mark.parametrize("tiling", [dict(block=128, i_per_thread=1, j_tile=128, slice=512),
@@ -283,7 +295,7 @@ def test_packed_and_scalar_mixed_kernels_agree(nb, tiling):
     for a, phi in outs:
         e = force_rel_err(a, a_ref)
         assert np.median(e) <= MIX_MED and e.max() <= MIX_MAX, (np.median(e), e.max())
-        assert np.abs(phi - phi_ref).max() <= 1e-5 * np.abs(phi_ref).max()
+        _check_mixed_phi(phi, phi_ref)
     assert force_rel_err(outs[1][0], outs[0][0]).max() <= 1e-5
 
 
@@ -303,6 +315,7 @@ def test_near_pairs_far_from_origin(nb, variant):
     a_ref, phi_ref = oracle.forces(x, m, G=1.0, eps=eps)
     e = force_rel_err(a, a_ref)
     assert np.median(e) <= MIX_MED and e.max() <= MIX_MAX, (np.median(e), e.max())
+    _check_mixed_phi(phi, phi_ref)
 
 
 @pytest.mark.parametrize("prec,tol", [(0, 1e-12), (1, 1e-6)])
