@@ -44,7 +44,9 @@ FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
 L2_FLUSH_BYTES = 256 << 20
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "force_mixed_n65536_full.md")
-FORCE_SRC = os.path.join(ROOT, "paper_2511_02655_gb300", "csrc", "force_kernels.cu")
+# sources of the timed force kernel: its traffic figure is valid while their hash matches
+FORCE_SRCS = [os.path.join(ROOT, "paper_2511_02655_gb300", "csrc", f)
+              for f in ("force_kernels.cu", "force_common.cuh", "pair_common.cuh")]
 
 
 def parse():
@@ -133,17 +135,27 @@ class ClockSampler:
 
 
 def traffic_per_launch():
-    """DRAM bytes per force launch from the committed ncu summary, if it still matches the source."""
+    """DRAM bytes per force launch from the committed ncu summary, if it still matches the sources."""
     try:
         text = open(TRAFFIC_FILE).read()
         nbytes = re.search(r"DRAM bytes per launch \(.*?\): (\d+)", text)
         src_sha = re.search(r"Kernel source SHA-256 \(.*?\): ([0-9a-f]{64})", text)
-        sha = hashlib.sha256(open(FORCE_SRC, "rb").read()).hexdigest()
+        h = hashlib.sha256()
+        for f in FORCE_SRCS:
+            h.update(open(f, "rb").read())
+        sha = h.hexdigest()
         if not nbytes or not src_sha or src_sha.group(1) != sha:
             return None
         return float(nbytes.group(1))
     except Exception:
         return None
+
+
+def fp32_peak_tops():
+    """FP32-pipe peak in T ops/s: SMs x 128 lanes x the maximum SM clock."""
+    import torch
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    return sms * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
 
 
 def rel_force_error(a, a_ref, guard=1e-3):
@@ -281,7 +293,10 @@ def aux_two_spheres(dev, stream):
     (ref0, _), t0 = _timed(lambda: oracle.forces_at(x, m, idx0, G=G, eps=eps, threads=threads))
     (ref1, _), t1 = _timed(lambda: oracle.forces_at(xf, m, idx1, G=G, eps=eps, threads=threads))
     rate = 2.0 * ks * n / (t0 + t1)
-    return {"interactions_per_s": float(n) * n * k / sec, "steps": k, "force_kernel_ms": kms / kl, "tuning": tuning,
+    return {"interactions_per_s": float(n) * n * k / sec, "steps": k, "force_kernel_ms": kms / kl,
+            "frac_fp32_roofline_force_kernel": (OPS_PER_INTERACTION - 1) * float(n) * n / (kms / kl * 1e-3) / 1e12
+                                               / fp32_peak_tops(),
+            "tuning": tuning,
             "force_err_vs_oracle": {"step_0": _err_stats(rel_force_error(a0[idx0], ref0)),
                                     f"step_{k}": _err_stats(rel_force_error(af[idx1], ref1)),
                                     "sample": f"{ks} seeded bodies against all {n}, FP64 oracle"},
@@ -641,11 +656,11 @@ def run_ours(args):
     elog = log.cpu().numpy()[:, 0, 0]
     drift = float(np.abs(elog - E0).max() / abs(E0))
 
-    # ---- dominant kernel vs its roofline (FP32 pipe, derived from SM count and max clock)
-    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    # ---- dominant kernel vs its roofline (FP32 pipe, derived from SM count and max clock): the force
+    # kernel of the timed steps (with the potential: every step records its energy)
     kernel_s = force_ms * 1e-3 / max(1, force_launches)
     achieved = OPS_PER_INTERACTION * interactions / kernel_s / 1e12
-    peak = sms * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
+    peak = fp32_peak_tops()
     traffic = traffic_per_launch()
 
     # ---- plain FP64 GPU path on the same state (a few steps)
@@ -728,9 +743,11 @@ def run_ours(args):
             },
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s (FP32 pipe)",
                          "frac": achieved / peak, "traffic": traffic,
-                         "kernel": "k_force_mixed", "ops_per_interaction": OPS_PER_INTERACTION,
+                         "kernel": "k_force_mixed2 (packed float32x2 pair arithmetic with the potential)",
+                         "ops_per_interaction": OPS_PER_INTERACTION,
                          "kernel_ms": kernel_s * 1e3,
-                         "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x {SM_MAX_MHZ:.0f} MHz"},
+                         "peak_basis": f"{torch.cuda.get_device_properties(dev).multi_processor_count} SMs x "
+                                       f"{FP32_LANES_PER_SM} FP32 lanes x {SM_MAX_MHZ:.0f} MHz"},
             "cpu_baseline": base,
             "e2e": e2e,
             "clocks": clk,

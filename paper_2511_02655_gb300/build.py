@@ -25,7 +25,7 @@ DEBUG_LIB = os.path.join(HERE, "libnbody_debug.so")
 DEBUG_BUILD_DIR = os.path.join(HERE, "_build_debug")
 
 SOURCES = ["force_kernels.cu", "adjoint_kernels.cu", "post_kernels.cu", "capi.cu", "noalloc.cu"]
-HEADERS = ["nbody_internal.h", "pair_common.cuh", "post_common.cuh"]
+HEADERS = ["nbody_internal.h", "pair_common.cuh", "post_common.cuh", "force_common.cuh"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE,

@@ -32,10 +32,12 @@ constexpr int kMinTilesPerSlice = 1;  // shortest slice in j-tiles (small system
 constexpr double kTuneLargePairs = 4.0e10;  // above this many pairs per force pass, tune on short slices
 constexpr int kTuneSlice = 8192;
 constexpr int kSliceQuantum = 4;  // slice lengths are multiples of this many bodies
+constexpr int64_t kTailMin = 64;   // shortest slice of a halving tail
 
 struct Tiling {
   int block = 0, ipt = 0, jtile = 0, slice = 0, n_ctas = 0;
   int variant = 0;  // mixed kernels: 0 scalar, 1 packed float32x2, 2 packed with a 4-CTA register cap (force)
+  int tail = 0;     // slicing of a system's j-range: 0 equal slices, 1 full slices and a halving tail
 };
 
 // Near-pair refinement radius of the mixed force kernels: 4 softening lengths
@@ -127,8 +129,6 @@ struct nbody_ctx {
   WorkItem* d_items = nullptr;
   int n_items = 0;
   int max_slices = 1;
-  int n_tiles = 0;                // (system, i-range) tiles of the force work list
-  int32_t* d_sys_tile = nullptr;  // [n_sys + 1] tile range of each system
   // VJP work list (built on first adjoint)
   Tiling vt;
   WorkItem* d_vitems = nullptr;
@@ -139,10 +139,8 @@ struct nbody_ctx {
   bool nvtx = false;        // NBODY_NVTX=1: NVTX ranges around the API calls and the adjoint's phases
   bool vjp_params = false;  // VJP launches also form the G and eps gradient sums
 
-  // scratch (stage_alt, stage_lo_alt: the second staging buffers of the fused
-  // step, which stages step k+1 while step k's force kernel still reads step k's)
+  // scratch
   DevBuf stage, stage_lo, stage_w, part, centre, epart, status_counter, a_scratch;
-  DevBuf stage_alt, stage_lo_alt, tile_done, tpart;
   unsigned* counter = nullptr;  // [2]
   unsigned* status = nullptr;   // [1]
 
@@ -288,57 +286,76 @@ int auto_slice(const nbody_ctx* c, const Tiling& t, int n_ctas) {
 }
 
 // Work items of tiling t with slice length L (the count build_items produces).
+// Slice lengths of a system of n bodies for slice length L. tail 0: equal
+// slices, each a multiple of kSliceQuantum bodies. tail 1: full slices of L
+// while more than 2 L bodies remain, then a tail of halving slices (half of
+// what remains each, down to kTailMin bodies): the work list, sorted longest
+// first, then ends in ever shorter items, so the CTAs of the persistent grid
+// run out of work at nearly the same time instead of one long item apart.
+void slice_lengths(int64_t n, int64_t L, int tail, std::vector<int64_t>& lens) {
+  lens.clear();
+  auto up = [](int64_t v) { return ((v + kSliceQuantum - 1) / kSliceQuantum) * kSliceQuantum; };
+  if (!tail || n <= 2 * L) {
+    int64_t ns = (n + L - 1) / L;
+    const int64_t len = up((n + ns - 1) / ns);
+    ns = (n + len - 1) / len;
+    for (int64_t k = 0; k < ns; ++k) lens.push_back(std::min(len, n - k * len));
+    return;
+  }
+  int64_t pos = 0;
+  while (n - pos > 2 * L) lens.push_back(L), pos += L;
+  while (pos < n) {
+    const int64_t r = n - pos;
+    const int64_t len = r <= 2 * kTailMin ? r : std::min<int64_t>(L, up(r / 2));
+    lens.push_back(len);
+    pos += len;
+  }
+}
+
 int64_t count_items(const nbody_ctx* c, const Tiling& t, int64_t L) {
   const int64_t itile = (int64_t)t.block * t.ipt;
   int64_t items = 0;
+  std::vector<int64_t> lens;
   for (int s = 0; s < c->n_sys; ++s) {
     const int64_t n = c->offsets[s + 1] - c->offsets[s];
     if (n <= 0) continue;
-    int64_t ns = (n + L - 1) / L;
-    int64_t len = (n + ns - 1) / ns;
-    len = ((len + kSliceQuantum - 1) / kSliceQuantum) * kSliceQuantum;
-    ns = (n + len - 1) / len;
-    items += ((n + itile - 1) / itile) * ns;
+    slice_lengths(n, L, t.tail, lens);
+    items += ((n + itile - 1) / itile) * (int64_t)lens.size();
   }
   return items;
 }
 
 void build_items(const nbody_ctx* c, const Tiling& t, std::vector<WorkItem>& items, std::vector<int>& sys_slices,
-                 int& max_slices, std::vector<int32_t>* sys_tile = nullptr) {
+                 int& max_slices) {
   items.clear();
   sys_slices.assign(c->n_sys, 1);
   max_slices = 1;
   const int64_t itile = (int64_t)t.block * t.ipt;
-  int32_t tile = 0;
-  if (sys_tile) sys_tile->assign(c->n_sys + 1, 0);
+  std::vector<int64_t> lens;
   for (int s = 0; s < c->n_sys; ++s) {
     const int64_t b = c->offsets[s], n = c->offsets[s + 1] - b;
-    if (sys_tile) (*sys_tile)[s] = tile;
     if (n <= 0) continue;
-    int64_t ns = (n + t.slice - 1) / t.slice;
-    // balance the slices (lengths a multiple of four: whole quads of the packed kernels'
-    // tiles; a slice's last j-tile may be partial)
-    int64_t len = (n + ns - 1) / ns;
-    len = ((len + kSliceQuantum - 1) / kSliceQuantum) * kSliceQuantum;
-    ns = (n + len - 1) / len;
+    // slice lengths a multiple of four (whole quads of the packed kernels' tiles;
+    // a slice's last j-tile may be partial), equal or with a halving tail
+    slice_lengths(n, t.slice, t.tail, lens);
+    const int64_t ns = (int64_t)lens.size();
     sys_slices[s] = (int)ns;
     max_slices = std::max(max_slices, (int)ns);
-    for (int64_t i0 = 0; i0 < n; i0 += itile, ++tile) {
-      for (int64_t k = 0; k < ns; ++k) {
+    for (int64_t i0 = 0; i0 < n; i0 += itile) {
+      int64_t j0 = 0;
+      for (int64_t k = 0; k < ns; j0 += lens[k], ++k) {
         WorkItem w;
         w.sys = s;
         w.i_begin = (int32_t)(b + i0);
         w.i_end = (int32_t)(b + std::min(n, i0 + itile));
-        w.j_begin = (int32_t)(b + k * len);
-        w.j_end = (int32_t)(b + std::min(n, (k + 1) * len));
+        w.j_begin = (int32_t)(b + j0);
+        w.j_end = (int32_t)(b + j0 + lens[k]);
         w.slice = (int32_t)k;
-        w.tile = tile;
         w.n_slices = (int32_t)ns;
         items.push_back(w);
       }
     }
   }
-  if (sys_tile) (*sys_tile)[c->n_sys] = tile;
   // longest-processing-time-first order for the dynamic persistent schedule
   std::stable_sort(items.begin(), items.end(), [](const WorkItem& a, const WorkItem& b) {
     const int64_t ca = (int64_t)(a.i_end - a.i_begin) * (a.j_end - a.j_begin);
@@ -391,32 +408,13 @@ nbody_status install_tiling(nbody_ctx* c, Tiling t, bool vjp) {
   t.slice = std::max(kSliceQuantum, (t.slice / kSliceQuantum) * kSliceQuantum);
   std::vector<WorkItem> items;
   std::vector<int> sys_slices;
-  std::vector<int32_t> sys_tile;
   int max_slices = 1;
-  build_items(c, t, items, sys_slices, max_slices, &sys_tile);
+  build_items(c, t, items, sys_slices, max_slices);
   t.n_ctas = std::max(1, std::min<int>(occ * c->sm_count, (int)std::max<size_t>(1, items.size())));
   nbody_status s = upload_items(c, items, vjp ? &c->d_vitems : &c->d_items);
   if (s) return s;
   s = upload_chunks(c, sys_slices, vjp ? &c->d_vchunks : &c->d_chunks);
   if (s) return s;
-  if (!vjp) {
-    // tile tables of the fused step epilogue: tickets (zero between launches) and energy partials
-    const int n_tiles = sys_tile.back();
-    if ((s = ensure(c, c->tile_done, (size_t)std::max(1, n_tiles) * sizeof(unsigned))) ||
-        (s = ensure(c, c->tpart, (size_t)std::max(1, n_tiles) * kEnergyVals * sizeof(double))))
-      return s;
-    NB_CUDA(c, cudaMemset(c->tile_done.p, 0, (size_t)std::max(1, n_tiles) * sizeof(unsigned)));
-    if (!c->d_sys_tile) {
-      if (cudaMalloc(&c->d_sys_tile, (size_t)(c->n_sys + 1) * sizeof(int32_t)) != cudaSuccess) {
-        cudaGetLastError();
-        c->d_sys_tile = nullptr;
-        return fail(c, NBODY_ENOMEM, "cudaMalloc of the tile table failed");
-      }
-    }
-    NB_CUDA(c, cudaMemcpy(c->d_sys_tile, sys_tile.data(), sys_tile.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
-    NB_CUDA(c, cudaDeviceSynchronize());
-    c->n_tiles = n_tiles;
-  }
   const size_t per = vjp ? 64 : 32;
   s = ensure(c, c->part, (size_t)max_slices * (size_t)c->n_total * per);
   if (s) return s;
@@ -455,12 +453,6 @@ PairLaunch pair_launch(nbody_ctx* c, bool vjp, bool refine = true, bool phi = tr
   L.phi = phi ? 1 : 0;
   L.status = c->status;
   L.block_bodies = t.block * t.ipt;
-  L.fuse = 0;
-  L.tile_done = static_cast<unsigned*>(c->tile_done.p);
-  L.tpart = static_cast<double*>(c->tpart.p);
-  L.sys_tile = c->d_sys_tile;
-  L.n_tiles = c->n_tiles;
-  L.fin_done = c->counter + 7;
   const size_t per = vjp ? (L.params ? 96 : 64) : 32;  // partial-sum bytes per body and slice
   L.part_slices = c->n_total > 0 ? (int32_t)std::min<size_t>(INT32_MAX, c->part.bytes / ((size_t)c->n_total * per)) : 0;
   return L;
@@ -497,7 +489,7 @@ nbody_status run_pair(nbody_ctx* c, cudaStream_t st, bool vjp, bool phi = true) 
     e1 = pooled_event(c);
     if (e0 && e1) NB_CUDA(c, cudaEventRecord(e0, st));
   }
-  NB_CUDA(c, vjp ? launch_vjp(c->cfg.precision, L, st) : launch_force(c->cfg.precision, L, nullptr, st));
+  NB_CUDA(c, vjp ? launch_vjp(c->cfg.precision, L, st) : launch_force(c->cfg.precision, L, st));
   if (e0 && e1) {
     NB_CUDA(c, cudaEventRecord(e1, st));
     c->ev_used.push_back({vjp ? 1 : 0, {e0, e1}});
@@ -509,32 +501,8 @@ nbody_status run_pair(nbody_ctx* c, cudaStream_t st, bool vjp, bool phi = true) 
 // phi: whether the potential is needed (an energy record, a phi output); only
 // the packed mixed kernel can skip it, the others always form it.
 nbody_status run_force(nbody_ctx* c, cudaStream_t st, bool phi) { return run_pair(c, st, false, phi); }
-
-// One force pass with the fused step epilogue: the force kernel reads the
-// staging buffers (stage_x, stage_lo) and its epilogue runs P's O(N) work,
-// staging the next positions into P.stage / P.stage_lo (the other buffers).
-nbody_status run_force_fused(nbody_ctx* c, cudaStream_t st, bool phi, const void* stage_x, const void* stage_lo,
-                             const PostLaunch& P) {
-  if (c->n_total == 0) return NBODY_OK;
-  PairLaunch L = pair_launch(c, false, true, phi);
-  L.stage_x = stage_x;
-  if (L.stage_lo) L.stage_lo = static_cast<const float4*>(stage_lo);
-  L.fuse = 1;
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
-  if (c->profiling && !c->capturing) {
-    e0 = pooled_event(c);
-    e1 = pooled_event(c);
-    if (e0 && e1) NB_CUDA(c, cudaEventRecord(e0, st));
-  }
-  NB_CUDA(c, launch_force(c->cfg.precision, L, &P, st));
-  if (e0 && e1) {
-    NB_CUDA(c, cudaEventRecord(e1, st));
-    c->ev_used.push_back({0, {e0, e1}});
-  }
-  ++c->launches;
-  return NBODY_OK;
-}
 nbody_status run_vjp(nbody_ctx* c, cudaStream_t st) { return run_pair(c, st, true); }
+
 
 PostLaunch post_launch(nbody_ctx* c, unsigned mode, double* x, double* v, const double* m, double* a, double* phi) {
   PostLaunch P{};
@@ -593,24 +561,18 @@ nbody_status enqueue_step(nbody_ctx* c, double* x, double* v, const double* m, d
     if ((s = run_post(c, post_launch(c, kCombine, x, v, m, a, nullptr), st))) return s;
   }
   if (n_steps == 0) return NBODY_OK;
-  // Step k's force kernel reads staging buffer k % 2 while its fused epilogue
-  // (combine, closing half-kick, energy record, opening half-kick and drift of
-  // step k+1) stages the new positions into the other one.
-  void* const hi_buf[2] = {c->stage.p, c->stage_alt.p};
-  void* const lo_buf[2] = {c->stage_lo.p, c->stage_lo.p ? c->stage_lo_alt.p : nullptr};
   if ((s = run_post(c, post_launch(c, kDrift | kStage, x, v, m, a, nullptr), st))) return s;
   const int every = c->cfg.energy_every;
   int rec = 0;
   for (int k = 0; k < n_steps; ++k) {
     const bool rec_now = elog && every > 0 && (k + 1) % every == 0;
+    if ((s = run_force(c, st, rec_now))) return s;
     unsigned mode = kCombine | kKickEnd;
     if (rec_now) mode |= kEnergy;
     if (k + 1 < n_steps) mode |= kDrift | kStage;
     PostLaunch P = post_launch(c, mode, x, v, m, a, nullptr);
-    P.stage = hi_buf[(k + 1) & 1];
-    P.stage_lo = lo_buf[(k + 1) & 1];
     if (rec_now) P.eout = elog + (int64_t)rec++ * c->n_sys * 9;
-    if ((s = run_force_fused(c, st, rec_now, hi_buf[k & 1], lo_buf[k & 1], P))) return s;
+    if ((s = run_post(c, P, st))) return s;
   }
   return NBODY_OK;
 }
@@ -700,7 +662,7 @@ nbody_status time_tiling(nbody_ctx* c, bool vjp, double* cost) {
   PairLaunch L = pair_launch(c, vjp);
   const Tiling& t = vjp ? c->vt : c->ft;
   auto launch = [&](const PairLaunch& P) {
-    return vjp ? launch_vjp(c->cfg.precision, P, c->stream) : launch_force(c->cfg.precision, P, nullptr, c->stream);
+    return vjp ? launch_vjp(c->cfg.precision, P, c->stream) : launch_force(c->cfg.precision, P, c->stream);
   };
   PostLaunch C{};
   C.chunks = vjp ? c->d_vchunks : c->d_chunks;
@@ -759,7 +721,7 @@ nbody_status time_tiling(nbody_ctx* c, bool vjp, double* cost) {
 
 // ---------------------------------------------------------------------------
 // tuning cache: NBODY_TUNE_CACHE=<file> keeps the tuner's choices across runs.
-// One line per choice, "<key>\t<block> <ipt> <jtile> <slice> <variant>"; the key
+// One line per choice, "<key>\t<block> <ipt> <jtile> <slice> <variant> <tail>"; the key
 // holds the device, the kernel (force or VJP), every configuration field the
 // choice depends on and a hash of the system layout, so an entry is reused only
 // for the same setup. A cached tiling that no longer installs is re-tuned.
@@ -773,7 +735,7 @@ std::string tune_key(const nbody_ctx* c, bool vjp) {
   }
   char buf[512];
   snprintf(buf, sizeof(buf),
-           "v1|%s|cc%d|sm%d|%s|prec%d|law%d|var%d|b%d|r%d|j%d|s%d|nsys%d|n%lld|lay%016llx|eps%.17g|sig%.17g|box%.17g",
+           "v2|%s|cc%d|sm%d|%s|prec%d|law%d|var%d|b%d|r%d|j%d|s%d|nsys%d|n%lld|lay%016llx|eps%.17g|sig%.17g|box%.17g",
            c->dev_name.c_str(), c->dev_cc, c->sm_count, vjp ? "vjp" : "force", g.precision, g.law, g.variant,
            vjp ? 0 : g.block, vjp ? 0 : g.i_per_thread, vjp ? 0 : g.j_tile, vjp ? 0 : g.slice, c->n_sys,
            (long long)c->n_total, (unsigned long long)h, g.eps, g.lj_sigma, g.box);
@@ -796,7 +758,8 @@ bool tune_cache_lookup(const nbody_ctx* c, bool vjp, Tiling* t) {
     *tab = '\0';
     if (key != line) continue;
     Tiling u;
-    if (sscanf(tab + 1, "%d %d %d %d %d", &u.block, &u.ipt, &u.jtile, &u.slice, &u.variant) == 5) *t = u, found = true;
+    if (sscanf(tab + 1, "%d %d %d %d %d %d", &u.block, &u.ipt, &u.jtile, &u.slice, &u.variant, &u.tail) == 6)
+      *t = u, found = true;
   }
   fclose(f);
   return found;
@@ -807,7 +770,7 @@ void tune_cache_store(const nbody_ctx* c, bool vjp, const Tiling& t) {
   if (!path || !*path) return;
   FILE* f = fopen(path, "a");
   if (!f) return;
-  fprintf(f, "%s\t%d %d %d %d %d\n", tune_key(c, vjp).c_str(), t.block, t.ipt, t.jtile, t.slice, t.variant);
+  fprintf(f, "%s\t%d %d %d %d %d %d\n", tune_key(c, vjp).c_str(), t.block, t.ipt, t.jtile, t.slice, t.variant, t.tail);
   fclose(f);
 }
 
@@ -932,24 +895,30 @@ nbody_status autotune(nbody_ctx* c, bool vjp) {
         if (std::find(ls.begin(), ls.end(), (int)len) == ls.end()) ls.push_back((int)len);
       }
     }
-    std::vector<double> lc(ls.size(), 1e300);
+    // each length with equal slices and with a halving tail
+    const size_t nc = 2 * ls.size();
+    std::vector<double> lc(nc, 1e300);
     for (int round = 0; round < 2; ++round)  // two interleaved timings each, the best kept
-      for (size_t k = 0; k < ls.size(); ++k) {
-        if (ls[k] < kSliceQuantum) continue;
+      for (size_t k = 0; k < nc; ++k) {
+        if (ls[k / 2] < kSliceQuantum) continue;
         Tiling t = base;
-        t.slice = ls[k];
+        t.slice = ls[k / 2];
+        t.tail = (int)(k % 2);
         if ((s = install_tiling(c, t, vjp))) return s;
         double cost = 0;
         if ((s = time_tiling(c, vjp, &cost))) return s;
-        if (verbose) fprintf(stderr, "nbody tune slice=%d items=%d -> %.4g ps/pair\n", ls[k], c->n_items, cost * 1e12);
+        if (verbose)
+          fprintf(stderr, "nbody tune slice=%d tail=%d items=%d -> %.4g ps/pair\n", t.slice, t.tail, c->n_items,
+                  cost * 1e12);
         lc[k] = std::min(lc[k], cost);
       }
     double bc = 1e300;
-    int bl = L0;
-    for (size_t k = 0; k < ls.size(); ++k)
-      if (lc[k] < bc) bc = lc[k], bl = ls[k];
+    size_t bk = 2;  // L0, equal slices
+    for (size_t k = 0; k < nc; ++k)
+      if (lc[k] < bc) bc = lc[k], bk = k;
     bt = base;
-    bt.slice = bl;
+    bt.slice = ls[bk / 2];
+    bt.tail = (int)(bk % 2);
   }
   bt.n_ctas = 0;
   if ((s = install_tiling(c, bt, vjp))) return s;
@@ -991,10 +960,8 @@ void free_ctx(nbody_ctx* c) {
   for (auto& u : c->ev_used) cudaEventDestroy(u.second.first), cudaEventDestroy(u.second.second);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   for (DevBuf* b : {&c->stage, &c->stage_lo, &c->stage_w, &c->part, &c->centre, &c->epart, &c->status_counter, &c->a_scratch,
-                    &c->xw, &c->vw, &c->aw, &c->ckpt, &c->traj, &c->hx, &c->hv, &c->hm, &c->ha, &c->hlog,
-                    &c->stage_alt, &c->stage_lo_alt, &c->tile_done, &c->tpart})
+                    &c->xw, &c->vw, &c->aw, &c->ckpt, &c->traj, &c->hx, &c->hv, &c->hm, &c->ha, &c->hlog})
     release(*b);
-  if (c->d_sys_tile) cudaFree(c->d_sys_tile);
   if (c->h_status) cudaFreeHost(c->h_status);
   if (c->d_chunks) cudaFree(c->d_chunks);
   if (c->d_vchunks) cudaFree(c->d_vchunks);
@@ -1273,14 +1240,11 @@ nbody_status nbody_init(nbody_ctx** out, const nbody_config* cfg, int64_t n_syst
   };
   const size_t n = (size_t)c->n_total;
   const size_t stage_bytes = n * (cfg->precision == NBODY_MIXED ? sizeof(float4) : sizeof(double4_32a));
-  if ((s = ensure(c, c->stage, stage_bytes)) || (s = ensure(c, c->stage_alt, stage_bytes))) return bail(s);
-  if (cfg->precision == NBODY_MIXED &&
-      ((s = ensure(c, c->stage_lo, n * sizeof(float4))) || (s = ensure(c, c->stage_lo_alt, n * sizeof(float4)))))
-    return bail(s);
+  if ((s = ensure(c, c->stage, stage_bytes))) return bail(s);
+  if (cfg->precision == NBODY_MIXED && (s = ensure(c, c->stage_lo, n * sizeof(float4)))) return bail(s);
   if ((s = ensure(c, c->centre, (size_t)c->n_sys * 3 * sizeof(double)))) return bail(s);
   if ((s = ensure(c, c->epart, std::max<size_t>(1, c->chunks.size()) * kEnergyVals * sizeof(double)))) return bail(s);
-  // [0..1] work counter, [2] status word, [4] energy ticket, [5] centre ticket, [6] adjoint-parameter ticket,
-  // [7] fused-epilogue record ticket
+  // [0..1] work counter, [2] status word, [4] energy ticket, [5] centre ticket, [6] adjoint-parameter ticket
   if ((s = ensure(c, c->status_counter, 8 * sizeof(unsigned)))) return bail(s);
   c->counter = static_cast<unsigned*>(c->status_counter.p);
   c->status = c->counter + 2;

@@ -10,13 +10,12 @@ namespace nbody {
 // One unit of all-pairs work: i-bodies [i_begin, i_end) of one system against
 // its j-bodies [j_begin, j_end), partial sums written to slice `slice` of the
 // system's n_slices. Indices are global body indices (rows of the caller's
-// arrays); `tile` numbers the (system, i-range) pairs of the work list.
+// arrays).
 struct WorkItem {
   int32_t sys;
   int32_t i_begin, i_end;
   int32_t j_begin, j_end;
   int32_t slice;
-  int32_t tile;
   int32_t n_slices;
 };
 
@@ -80,29 +79,16 @@ struct PairLaunch {
   int32_t part_slices;   // slices the partial buffer holds (index checks of NBODY_DEBUG builds)
   int32_t block_bodies;  // debug checks: i-bodies a work item may hold (block x ipt)
   unsigned* status;      // device status word (index checks of NBODY_DEBUG builds)
-  // Fused step epilogue (force kernels, fuse = 1): the CTA that completes the
-  // last slice of an i-tile (ticket tile_done[tile]) adds the tile's slices and
-  // runs the O(N) work of the PostLaunch passed beside this struct for those
-  // bodies; per-tile energy partials go to tpart, and the last tile to finish
-  // (ticket fin_done) forms the per-system records over sys_tile.
-  int fuse;
-  unsigned* tile_done;      // [n_tiles], zero between launches
-  double* tpart;            // [n_tiles][kEnergyVals]
-  const int32_t* sys_tile;  // [n_sys + 1] tile range of each system
-  int32_t n_tiles;
-  unsigned* fin_done;       // zero between launches
 };
 
 #ifdef NBODY_DEBUG
 // NBODY_DEBUG check of a work item against the buffers it indexes: its body
 // ranges inside the rows, its i-range inside one CTA's tile, its slice inside
-// the partial-sum buffer (and, fused, its tile inside the tile tables). The
-// kernel skips an item that fails.
+// the partial-sum buffer. The kernel skips an item that fails.
 __device__ __forceinline__ bool item_ok(const WorkItem& w, const PairLaunch& L) {
   return nb_debug_ok(w.i_begin >= 0 && w.i_begin < w.i_end && w.i_end <= L.n_total && w.j_begin >= 0 &&
                          w.j_begin < w.j_end && w.j_end <= L.n_total && w.i_end - w.i_begin <= L.block_bodies &&
-                         w.slice >= 0 && w.slice < w.n_slices && w.n_slices <= L.part_slices &&
-                         (!L.fuse || (w.tile >= 0 && w.tile < L.n_tiles)),
+                         w.slice >= 0 && w.slice < w.n_slices && w.n_slices <= L.part_slices,
                      L.status);
 }
 
@@ -120,10 +106,8 @@ __device__ __forceinline__ constexpr bool item_ok(const WorkItem&, const PairLau
 __device__ __forceinline__ constexpr bool chunk_ok(const Chunk&, int64_t, int, int, unsigned*) { return true; }
 #endif
 
-struct PostLaunch;
-// Returns cudaErrorInvalidConfiguration for an unsupported tiling. P: the O(N)
-// work of the fused epilogue (used when L.fuse; may be NULL otherwise).
-cudaError_t launch_force(int precision, const PairLaunch& L, const PostLaunch* P, cudaStream_t st);
+// Returns cudaErrorInvalidConfiguration for an unsupported tiling.
+cudaError_t launch_force(int precision, const PairLaunch& L, cudaStream_t st);
 cudaError_t launch_vjp(int precision, const PairLaunch& L, cudaStream_t st);
 // CTAs of the force kernel that fit on one SM for the tiling (0 if unsupported).
 int force_ctas_per_sm(int precision, int variant, int block, int ipt, int jtile, int law);

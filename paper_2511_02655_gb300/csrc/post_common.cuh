@@ -1,6 +1,5 @@
-// Device helpers of the O(N) work around the all-pairs passes, shared by the
-// O(N) kernels (post_kernels.cu) and the force kernels' fused step epilogue
-// (force_kernels.cu): the per-body combine / kick / drift / staging / energy
+// Device helpers of the O(N) kernels around the all-pairs passes
+// (post_kernels.cu): the per-body combine / kick / drift / staging / energy
 // terms of one body, the fixed-order CTA and per-system float64 sums, and the
 // last-arrival ticket.
 #pragma once
@@ -71,8 +70,8 @@ __device__ __forceinline__ void stage_store(int precision, void* stage, int i, d
   }
 }
 
-// Final per-system sums of partials [n_parts][kEnergyVals] (one per chunk, or
-// per i-tile in the fused epilogue), one warp per system, lanes striding over
+// Final per-system sums of partials [n_parts][kEnergyVals] (one per chunk of
+// an O(N) kernel), one warp per system, lanes striding over
 // the system's range, then a fixed xor-shuffle reduction: the same order
 // whichever CTA runs it. The partials were written by other CTAs of the same
 // launch, so they are read from L2 (ld.global.cg).
@@ -121,16 +120,15 @@ __device__ __forceinline__ void emit_energy(double* out, const int sy, const dou
   for (int k = 2; k < kEnergyVals; ++k) o[k + 1] = v[k];
 }
 
-// The O(N) work of one body i in the modes of P (PostMode): with kCombine its
+// The O(N) work of one body i in the PostMode bits of `mode`: with kCombine its
 // summed partials (sx, sy, sz, sp) become a = G S (or the Lennard-Jones
 // scaling) and phi; then the closing half-kick, the energy or virial terms
 // (accumulated into e), the opening half-kick and drift of the next step (with
 // the walls), and the staging entry of the new position. cen is the system's
 // staging origin. Returns true if a combined value is not finite.
-__device__ __forceinline__ bool post_body(const PostLaunch& P, const int i, const double* cen, const double sx,
-                                          const double sy, const double sz, const double sp,
+__device__ __forceinline__ bool post_body(const PostLaunch& P, const unsigned mode, const int i, const double* cen,
+                                          const double sx, const double sy, const double sz, const double sp,
                                           double (&e)[kEnergyVals]) {
-  const unsigned mode = P.mode;
   bool bad = false;
   // every load of the body first, so that they are in flight together (x, v, m
   // and a are distinct arrays; nothing below is stored before it is read)
@@ -187,87 +185,6 @@ __device__ __forceinline__ bool post_body(const PostLaunch& P, const int i, cons
   }
   if (mode & kStage) stage_store(P.precision, P.stage, i, x0, x1, x2, m, cen, P.stage_lo);
   return bad;
-}
-
-// float64 quadruple from L2 (data written by other CTAs of the same launch)
-__device__ __forceinline__ double4_32a ldcg_d4(const double4_32a* p) {
-  const double2 a = __ldcg(reinterpret_cast<const double2*>(p));
-  const double2 b = __ldcg(reinterpret_cast<const double2*>(p) + 1);
-  return make_double4_32a(a.x, a.y, b.x, b.y);
-}
-
-// Fused step epilogue of a force kernel, called by every thread of the CTA
-// after it finished work item w, with own[r] = the item's float64 partial of
-// its r-th body (i_begin + threadIdx.x + r BLOCK), already stored to the
-// item's slice unless the system has a single slice. The CTA that completes
-// the tile's last slice adds the tile's slices in slice order (the order of
-// k_post, so the results are the same bit for bit) and runs post_body for its
-// bodies; the energy partials of the tile go to L.tpart, and the last tile's
-// CTA forms the per-system records. No CTA waits on another.
-constexpr int kFuseBatch = 1;  // slice partials loaded together by the fused epilogue
-
-template <int BLOCK, int R>
-__device__ __forceinline__ void fused_epilogue(const PairLaunch& L, const PostLaunch& P, const WorkItem& w,
-                                               const double4_32a (&own)[R]) {
-  __shared__ int s_fin;
-  __syncthreads();  // every partial store of this item is issued
-  if (threadIdx.x == 0) {
-    __threadfence();
-    const unsigned done = atomicAdd(&L.tile_done[w.tile], 1u);
-    s_fin = done == (unsigned)w.n_slices - 1u;
-    if (s_fin) L.tile_done[w.tile] = 0u;  // no other item of this tile is left in this launch
-  }
-  __syncthreads();
-  if (!s_fin) return;
-  __threadfence();
-  const double4_32a* part = reinterpret_cast<const double4_32a*>(L.part);
-  const double* cen = P.centre + 3 * w.sys;
-  double e[kEnergyVals];
-#pragma unroll
-  for (int k = 0; k < kEnergyVals; ++k) e[k] = 0.0;
-  bool bad = false;
-  // one body at a time (a loop the compiler keeps rolled), so that the epilogue
-  // needs fewer registers than the pair loop and leaves the kernel's count alone
-#pragma unroll 1
-  for (int r = 0; r < R; ++r) {
-    const int i = w.i_begin + (int)threadIdx.x + r * BLOCK;
-    if (i >= w.i_end) continue;
-    double sx = 0.0, sy = 0.0, sz = 0.0, sp = 0.0;
-    if (w.n_slices == 1) {  // the item's own partial is the sum
-      double4_32a o = own[0];
-#pragma unroll
-      for (int k = 1; k < R; ++k)
-        if (r == k) o = own[k];
-      sx = o.x, sy = o.y, sz = o.z, sp = o.w;
-    } else {
-      // every slice was stored (this item's too): batches of loads in flight
-      // together, added in slice order
-#pragma unroll 1
-      for (int s0 = 0; s0 < w.n_slices; s0 += kFuseBatch) {
-        double4_32a q[kFuseBatch];
-#pragma unroll
-        for (int u = 0; u < kFuseBatch; ++u)
-          if (s0 + u < w.n_slices) q[u] = ldcg_d4(part + (int64_t)(s0 + u) * L.n_total + i);
-#pragma unroll
-        for (int u = 0; u < kFuseBatch; ++u)
-          if (s0 + u < w.n_slices) sx += q[u].x, sy += q[u].y, sz += q[u].z, sp += q[u].w;
-      }
-    }
-    bad |= post_body(P, i, cen, sx, sy, sz, sp, e);
-  }
-  if (bad) atomicOr(P.status, kFlagNonFinite);
-  if (P.mode & kEnergy) {
-    block_sum<kEnergyVals, BLOCK>(e);
-    if (threadIdx.x == 0) {
-#pragma unroll
-      for (int k = 0; k < kEnergyVals; ++k) L.tpart[(int64_t)w.tile * kEnergyVals + k] = e[k];
-    }
-    if (P.eout && last_of(L.fin_done, (unsigned)L.n_tiles)) {
-      __threadfence();
-      systems_final<kEnergyVals, BLOCK>(L.sys_tile, P.n_sys, L.tpart, L.n_tiles, P.status,
-                                        [&](int sy, const double (&v)[kEnergyVals]) { emit_energy(P.eout, sy, v); });
-    }
-  }
 }
 
 }  // namespace nbody

@@ -35,7 +35,7 @@ __global__ void __launch_bounds__(kPostThreads) k_post(const PostLaunch P) {
         sx += q.x, sy += q.y, sz += q.z, sp += q.w;
       }
     }
-    bad |= post_body(P, i, cen, sx, sy, sz, sp, e);
+    bad |= post_body(P, mode, i, cen, sx, sy, sz, sp, e);
   }
   if (bad) atomicOr(P.status, kFlagNonFinite);
   if (mode & kVirial) {

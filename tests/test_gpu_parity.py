@@ -432,7 +432,7 @@ def test_tuning_cache(nb, tmp_path, monkeypatch):
     # an entry that no longer installs (an uncompiled block size) is ignored and re-tuned
     key = lines[0].split("\t")[0]
     with open(path, "a") as f:
-        f.write(f"{key}\t96 2 256 4096 1\n")
+        f.write(f"{key}\t96 2 256 4096 1 0\n")
     c4, a4 = make()
     assert nb.nbody_get_tuning(c4)["block"] in (128, 256)
     assert torch.equal(a4, a1) or force_rel_err(a4.cpu().numpy(), a1.cpu().numpy()).max() <= 1e-5
