@@ -107,13 +107,14 @@ struct SmemMixed {
   int item;
 };
 
-// Work items of the scalar mixed kernel, taken from `counter` until none is left.
+// Work items of the scalar mixed kernel, taken from `counter` until none is left;
+// each writes its slice's compensated float32 sums (fpair4) per i-body.
 template <int BLOCK, int R, int J>
 __device__ __forceinline__ void items_mixed(const PairLaunch& L, unsigned* counter, SmemMixed<J>& sm) {
   constexpr int LPT = (J + BLOCK - 1) / BLOCK;  // tile entries loaded per thread
   auto& tile = sm.tile;
   const float4* __restrict__ st = static_cast<const float4*>(L.stage_x);
-  double4_32a* __restrict__ part = reinterpret_cast<double4_32a*>(L.part);
+  fpair4* __restrict__ part = reinterpret_cast<fpair4*>(L.part);
   const float eps2 = (float)L.eps2;
   const float r2c = L.r2_near;
   const float4* __restrict__ lo = L.stage_lo;
@@ -182,12 +183,11 @@ __device__ __forceinline__ void items_mixed(const PairLaunch& L, unsigned* count
       __syncthreads();
     }
 
-    double4_32a* out = part + (int64_t)w.slice * L.n_total;
+    fpair4* out = part + (int64_t)w.slice * L.n_total;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       if (ig[r] < w.i_end)
-        out[ig[r]] = make_double4_32a((double)hx[r] + (double)lx[r], (double)hy[r] + (double)ly[r],
-                                      (double)hz[r] + (double)lz[r], (double)hp[r] + (double)lp[r]);
+        out[ig[r]] = fpair4{make_float4(hx[r], lx[r], hy[r], ly[r]), make_float4(hz[r], lz[r], hp[r], lp[r])};
     }
   }
 }
@@ -371,7 +371,8 @@ struct SmemMixed2 {
   int item;
 };
 
-// Work items of the packed mixed kernel, taken from `counter` until none is left.
+// Work items of the packed mixed kernel, taken from `counter` until none is left;
+// each writes its slice's compensated float32 sums (fpair4) per i-body.
 template <int LAW, int BLOCK, int R, int J, bool PHI>
 __device__ __forceinline__ void items_mixed2(const PairLaunch& L, unsigned* counter, SmemMixed2<J>& sm) {
   static_assert(J % 4 == 0, "tiles hold whole quads of j-bodies");
@@ -381,7 +382,7 @@ __device__ __forceinline__ void items_mixed2(const PairLaunch& L, unsigned* coun
   auto& tz = sm.tz;
   auto& tm = sm.tm;
   const float4* __restrict__ st = static_cast<const float4*>(L.stage_x);
-  double4_32a* __restrict__ part = reinterpret_cast<double4_32a*>(L.part);
+  fpair4* __restrict__ part = reinterpret_cast<fpair4*>(L.part);
   const float eps2 = (float)L.eps2;
   const float2 e2 = make_float2(eps2, eps2);
   const float2 s2 = make_float2((float)L.sigma2, (float)L.sigma2);
@@ -470,12 +471,11 @@ __device__ __forceinline__ void items_mixed2(const PairLaunch& L, unsigned* coun
       __syncthreads();
     }
 
-    double4_32a* out = part + (int64_t)w.slice * L.n_total;
+    fpair4* out = part + (int64_t)w.slice * L.n_total;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       if (ig[r] < w.i_end)
-        out[ig[r]] = make_double4_32a((double)hx[r] + (double)lx[r], (double)hy[r] + (double)ly[r],
-                                      (double)hz[r] + (double)lz[r], PHI ? (double)hp[r] + (double)lp[r] : 0.0);
+        out[ig[r]] = fpair4{make_float4(hx[r], lx[r], hy[r], ly[r]), make_float4(hz[r], lz[r], hp[r], lp[r])};
     }
   }
 }

@@ -7,7 +7,7 @@
 //           system's staging origin; each interaction is 3 FADD + 3 FFMA +
 //           1 MUFU.RSQ + 3 FMUL + 3 FFMA + 1 FADD in float32; per j-tile the
 //           float32 partial sums are folded into a compensated (hi, lo) float32
-//           pair per body (TwoSum), converted to float64 per work item.
+//           pair per body (TwoSum), written per work item as it is (fpair4).
 //   fp64  : staged double4_32a (x, y, z, m), every operation in float64.
 //
 // The mixed path has a scalar kernel and a packed one (two j-bodies per
@@ -17,9 +17,10 @@
 // i-bodies live in registers (R per thread, strided by the CTA size so loads
 // and stores coalesce), j-bodies stream through a shared-memory tile that
 // every thread reads with broadcast loads; the next tile is prefetched into
-// registers while the current one is consumed. Each item writes one float64
-// partial (sum m d / s^3, sum m / s) per i-body to its slice; the O(N) post
-// kernel adds the slices in a fixed order, so results are deterministic.
+// registers while the current one is consumed. Each item writes one partial
+// (sum m d / s^3, sum m / s) per i-body to its slice, float64 on the FP64 path
+// and compensated float32 pairs on the mixed path; the O(N) post kernel adds
+// the slices in a fixed order, so results are deterministic.
 // Self pairs are masked in the tiles that overlap the item's own i-range.
 #include <algorithm>
 
@@ -38,13 +39,23 @@ __global__ void __launch_bounds__(BLOCK) k_force_mixed(const PairLaunch L) {
   retire_cta(L.counter);
 }
 
-// MINB > 0 asks the compiler for MINB resident CTAs per SM (a register cap): the
-// 128 x 2 x 256 tiling compiles to 146 registers (3 CTAs per SM) without it, and
-// the 4-CTA build is ~1% faster at N = 65 536 but ~4% slower at N = 262 144, so
-// the tuner gets both (variant 3 of nbody_config). (The same cap on the 512-body
-// tile timed well on the tuner's synthetic sphere but 3% slower on real inputs.)
+// Resident CTAs per SM each packed tiling is compiled for (a register bound of
+// 65 536 / (BLOCK x CTAs)): the occupancy its register use gives anyway, pinned
+// down so that small code changes cannot push a tiling over an allocation edge
+// (the 128 x 2 x 512 kernel once grew from 162 to 170 registers and fell from 3
+// to 2 CTAs per SM, 3% slower).
+constexpr int packed_min_ctas(int block, int r) {
+  return block == 128 ? (r == 1 ? 4 : r == 2 ? 3 : 2) : (r == 1 ? 2 : 1);
+}
+
+// MINB > 0 asks for MINB resident CTAs instead (a tighter register cap): the
+// 128 x 2 x 256 tiling at 4 CTAs per SM is ~1% faster at N = 65 536 but ~4%
+// slower at N = 262 144 than at 3, so the tuner gets both (variant 3 of
+// nbody_config). (The same cap on the 512-body tile timed well on the tuner's
+// synthetic sphere but 3% slower on real inputs.)
 template <int LAW, int BLOCK, int R, int J, bool PHI, int MINB = 0>
-__global__ void __launch_bounds__(BLOCK, (MINB > 0 ? MINB : (NBODY_MIN_CTAS > 0 ? NBODY_MIN_CTAS : 1)))
+__global__ void __launch_bounds__(BLOCK, (MINB > 0 ? MINB
+                                                  : (NBODY_MIN_CTAS > 0 ? NBODY_MIN_CTAS : packed_min_ctas(BLOCK, R))))
     k_force_mixed2(const PairLaunch L) {
   __shared__ fc::SmemMixed2<J> sm;
   fc::items_mixed2<LAW, BLOCK, R, J, PHI>(L, L.counter, sm);

@@ -27,10 +27,33 @@ struct Chunk {
   int32_t n_slices;  // force/VJP slices of this system (partials to combine)
 };
 
-constexpr int kChunk = 256;         // bodies per chunk (one per thread of an O(N) CTA)
-constexpr int kPostThreads = 256;   // threads per O(N) kernel CTA
+// The O(N) kernels do their float64 work on GB300's FP64 pipe (about 1/75 of
+// the FP32 rate), so their time is the float64 operations per SM: chunks of 128
+// bodies spread even small systems (10 000 bodies: 79 CTAs) over many SMs.
+constexpr int kChunk = 128;         // bodies per chunk (one per thread of an O(N) CTA)
+constexpr int kPostThreads = 128;   // threads per O(N) kernel CTA
 constexpr int kEnergyVals = 8;      // K, U, Px, Py, Pz, Lx, Ly, Lz per chunk
 constexpr int kAdjVals = 8;         // VJP partial values per body per slice
+
+// Force partial of one body and slice on the mixed path: the four compensated
+// float32 sums (hi, lo) of the force kernels (sum m d / s^3 per axis and
+// sum m / s), stored as they are: (hx, lx, hy, ly), (hz, lz, hp, lp). The
+// O(N) kernel adds the slices as float32 pairs (TwoSum) and converts the total
+// once, instead of converting each slice and adding on the FP64 pipe.
+struct __align__(32) fpair4 {
+  float4 xy;
+  float4 zp;
+};
+
+// Knuth's TwoSum: hi + lo absorbs t, with the rounding error of hi + t carried
+// into lo (Knuth, TAOCP vol. 2, 4.2.2). Six float32 additions, no branches.
+__device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float t) {
+  const float s = hi + t;
+  const float bp = s - hi;
+  const float err = (hi - (s - bp)) + (t - bp);
+  hi = s;
+  lo += err;
+}
 
 // Device status word bits (latched, read by nbody_sync).
 constexpr unsigned kFlagNonFinite = 1u;
@@ -64,7 +87,7 @@ struct PairLaunch {
   const WorkItem* items;
   int32_t n_items;
   unsigned* counter;     // [2]: next item, CTAs done (zero between launches)
-  double* part;          // force: double4_32a [slices][N]; VJP: (2 or 3 with params) x double4_32a [slices][N]
+  double* part;          // force: fpair4 (mixed) or double4_32a (FP64) [slices][N]; VJP: (2 or 3 with params) x double4_32a [slices][N]
   int64_t n_total;
   double eps2;
   const float4* stage_lo;  // mixed: float32 remainders (x - c) - hi [N], near-pair refinement
@@ -128,7 +151,7 @@ enum PostMode : unsigned {
 struct PostLaunch {
   const Chunk* chunks;
   int32_t n_chunks;
-  const double* part;      // double4_32a [slices][N]
+  const double* part;      // [slices][N] of fpair4 (mixed) or double4_32a (FP64)
   int64_t n_total;
   double G, half_dt, dt;
   double* x;

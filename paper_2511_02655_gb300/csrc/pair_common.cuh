@@ -24,16 +24,6 @@ __device__ __forceinline__ float rcp_approx(float x) {
   return y;
 }
 
-// Knuth's TwoSum: hi + lo absorbs t, with the rounding error of hi + t carried
-// into lo (Knuth, TAOCP vol. 2, 4.2.2). Six float32 additions, no branches.
-__device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float t) {
-  const float s = hi + t;
-  const float bp = s - hi;
-  const float err = (hi - (s - bp)) + (t - bp);
-  hi = s;
-  lo += err;
-}
-
 // d of a near pair from the staged float32 parts x - c = hi + lo (lo is the
 // float32 remainder of the float64 value): the hi difference is exact for close
 // pairs (Sterbenz) and the lo difference restores the bits the staging dropped,

@@ -28,7 +28,22 @@ __global__ void __launch_bounds__(kPostThreads) k_post(const PostLaunch P) {
 
   for (int i = c.begin + (int)threadIdx.x; i < c.end; i += kPostThreads) {
     double sx = 0.0, sy = 0.0, sz = 0.0, sp = 0.0;
-    if (mode & kCombine) {
+    if ((mode & kCombine) && P.precision == 1) {
+      // compensated float32 pairs, added as pairs on the FP32 pipe: TwoSum of
+      // the hi parts, the lo parts and rounding errors summed alongside
+      const fpair4* fp = reinterpret_cast<const fpair4*>(P.part);
+      float hx = 0.f, lx = 0.f, hy = 0.f, ly = 0.f, hz = 0.f, lz = 0.f, hp = 0.f, lp = 0.f;
+#pragma unroll 8
+      for (int s = 0; s < c.n_slices; ++s) {
+        const fpair4 q = fp[(int64_t)s * P.n_total + i];
+        two_sum_acc(hx, lx, q.xy.x), lx += q.xy.y;
+        two_sum_acc(hy, ly, q.xy.z), ly += q.xy.w;
+        two_sum_acc(hz, lz, q.zp.x), lz += q.zp.y;
+        two_sum_acc(hp, lp, q.zp.z), lp += q.zp.w;
+      }
+      sx = (double)hx + (double)lx, sy = (double)hy + (double)ly;
+      sz = (double)hz + (double)lz, sp = (double)hp + (double)lp;
+    } else if (mode & kCombine) {
 #pragma unroll 8
       for (int s = 0; s < c.n_slices; ++s) {
         const double4_32a q = part[(int64_t)s * P.n_total + i];
