@@ -46,7 +46,7 @@ L2_FLUSH_BYTES = 256 << 20
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "force_mixed_n65536_full.md")
 # sources of the timed force kernel: its traffic figure is valid while their hash matches
 FORCE_SRCS = [os.path.join(ROOT, "paper_2511_02655_gb300", "csrc", f)
-              for f in ("force_kernels.cu", "force_common.cuh", "pair_common.cuh")]
+              for f in ("force_kernels.cu", "force_common.cuh", "pair_common.cuh", "nbody_internal.h")]
 
 
 def parse():

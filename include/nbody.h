@@ -228,6 +228,14 @@ nbody_status nbody_get_tuning(const nbody_ctx* ctx, int32_t* block, int32_t* i_p
                               int32_t* slice, int32_t* n_ctas, int32_t* variant);
 
 /*
+ * Work-list shape of the force pass (after init / autotune): tail = 0 when
+ * each system's j-range is cut into equal slices, 1 when it ends in a tail of
+ * halving slices; the number of work items and the largest slice count of any
+ * system. Any pointer may be NULL.
+ */
+nbody_status nbody_get_slicing(const nbody_ctx* ctx, int32_t* tail, int32_t* n_items, int32_t* max_slices);
+
+/*
  * Kernel timing. nbody_profile(ctx, 1) clears the counters and makes the
  * context record a CUDA event pair on its stream around every launch of the
  * all-pairs kernels (eagerly issued calls only; graph replays are not timed);

@@ -26,7 +26,7 @@ __all__ = [
     "nbody_init", "nbody_forces", "nbody_step", "nbody_energy", "nbody_virial", "nbody_adjoint",
     "nbody_adjoint_params",
     "nbody_step_host",
-    "nbody_sync", "nbody_get_tuning", "nbody_launch_count", "nbody_last_error", "nbody_destroy",
+    "nbody_sync", "nbody_get_tuning", "nbody_get_slicing", "nbody_launch_count", "nbody_last_error", "nbody_destroy",
     "nbody_version", "nbody_build_flags", "nbody_profile", "nbody_kernel_time", "nbody_forces_noalloc", "NOALLOC_MAX_BODIES",
     "NBodyAdjoint", "ENERGY_FIELDS",
 ]
@@ -93,6 +93,7 @@ def load():
             "nbody_step_host": (i32, [p, p, p, p, p, i32, i32, p]),
             "nbody_sync": (i32, [p]),
             "nbody_get_tuning": (i32, [p] + [ctypes.POINTER(i32)] * 6),
+            "nbody_get_slicing": (i32, [p] + [ctypes.POINTER(i32)] * 3),
             "nbody_launch_count": (i64, [p]),
             "nbody_profile": (i32, [p, i32]),
             "nbody_kernel_time": (i32, [p, i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)]),
@@ -340,9 +341,19 @@ def nbody_sync(ctx: Context):
 
 
 def nbody_get_tuning(ctx: Context) -> dict:
+    """Tiling in use (nbody_get_tuning) and the work list's shape (nbody_get_slicing)."""
     vals = [ctypes.c_int32() for _ in range(6)]
     _check(load().nbody_get_tuning(ctx._h, *[ctypes.byref(v) for v in vals]), ctx)
-    return dict(zip(("block", "i_per_thread", "j_tile", "slice", "n_ctas", "variant"), (v.value for v in vals)))
+    out = dict(zip(("block", "i_per_thread", "j_tile", "slice", "n_ctas", "variant"), (v.value for v in vals)))
+    out.update(nbody_get_slicing(ctx))
+    return out
+
+
+def nbody_get_slicing(ctx: Context) -> dict:
+    """Work-list shape of the force pass: tail (0 equal slices, 1 halving tail), n_items, max_slices."""
+    sl = [ctypes.c_int32() for _ in range(3)]
+    _check(load().nbody_get_slicing(ctx._h, *[ctypes.byref(v) for v in sl]), ctx)
+    return dict(zip(("tail", "n_items", "max_slices"), (v.value for v in sl)))
 
 
 def nbody_launch_count(ctx: Context) -> int:

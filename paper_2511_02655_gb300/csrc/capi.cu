@@ -857,68 +857,75 @@ nbody_status autotune(nbody_ctx* c, bool vjp) {
     timed.push_back({cost, t0});
   }
   if (timed.empty()) return fail(c, NBODY_EINVAL, "no compiled tiling matches the requested parameters");
-  // the candidates within 5% of the best are timed twice more, interleaved, and
+  // the candidates within 8% of the best (at most four) are timed twice more, interleaved, and
   // keep their best time: single timings differ by 1-3% from run to run
   std::stable_sort(timed.begin(), timed.end(),
                    [](const std::pair<double, Tiling>& a, const std::pair<double, Tiling>& b) { return a.first < b.first; });
   size_t top = 1;
-  while (top < timed.size() && top < 4 && timed[top].first <= 1.05 * timed[0].first) ++top;
+  while (top < timed.size() && top < 4 && timed[top].first <= 1.08 * timed[0].first) ++top;
   for (int round = 0; round < 2 && top > 1; ++round)
     for (size_t k = 0; k < top; ++k) {
       double cost = 0;
       if ((s = measure(timed[k].second, &cost))) return s;
       timed[k].first = std::min(timed[k].first, cost);
     }
-  double best = timed[0].first;
+  // order the re-timed candidates; the first is the choice unless the slice refinement finds better
+  std::stable_sort(timed.begin(), timed.begin() + top,
+                   [](const std::pair<double, Tiling>& a, const std::pair<double, Tiling>& b) { return a.first < b.first; });
   Tiling bt = timed[0].second;
-  for (size_t k = 1; k < top; ++k)
-    if (timed[k].first < best) best = timed[k].first, bt = timed[k].second;
-  // slice-length refinement for the best tiling: the automatic choice, half and
-  // twice it, and (one system) the lengths whose work list fills a whole number
-  // of waves of the persistent grid (equal items, a multiple of the CTA count,
-  // leave no CTA idle at the end of the launch); each timed twice, interleaved
+  // slice-length refinement of the best (up to three) tilings: the automatic
+  // choice, half and twice it, and (one system) the lengths whose work list
+  // fills a whole number of waves of the persistent grid (equal items, a
+  // multiple of the CTA count, leave no CTA idle at the end of the launch),
+  // each with equal slices and with a halving tail. Tilings are refined
+  // together because the tail helps some more than others (it changes how the
+  // last wave ends); every setting is timed twice, interleaved, the best kept.
   if (!vjp && g.slice == 0 && !large) {
-    Tiling base = bt;
-    base.slice = 0;
-    if ((s = install_tiling(c, base, vjp))) return s;
-    const int L0 = c->ft.slice;
-    const int64_t n_ctas = c->ft.n_ctas;
-    std::vector<int> ls = {L0 / 2, L0, L0 * 2};
-    if (c->n_sys == 1) {
-      const int64_t n = c->offsets[1], tiles = (n + (int64_t)base.block * base.ipt - 1) / ((int64_t)base.block * base.ipt);
-      for (int64_t W = 1; W <= 64 && ls.size() < 7; ++W) {
-        const int64_t ns = W * n_ctas / tiles;  // slices per tile with tiles x ns <= W x CTAs
-        if (ns < 1 || (double)(tiles * ns) < 0.98 * (double)(W * n_ctas)) continue;
-        int64_t len = (n + ns - 1) / ns;
-        len = ((len + kSliceQuantum - 1) / kSliceQuantum) * kSliceQuantum;
-        if ((n + len - 1) / len != ns || len < L0 / 4 || len > 4 * (int64_t)L0) continue;
-        if (std::find(ls.begin(), ls.end(), (int)len) == ls.end()) ls.push_back((int)len);
+    std::vector<Tiling> settings;
+    for (size_t f = 0; f < std::min<size_t>(top, 3); ++f) {
+      Tiling base = timed[f].second;
+      base.slice = 0;
+      base.tail = 0;
+      if ((s = install_tiling(c, base, vjp))) return s;
+      const int L0 = c->ft.slice;
+      const int64_t n_ctas = c->ft.n_ctas;
+      std::vector<int> ls = {L0 / 2, L0, L0 * 2};
+      if (c->n_sys == 1) {
+        const int64_t n = c->offsets[1], tiles = (n + (int64_t)base.block * base.ipt - 1) / ((int64_t)base.block * base.ipt);
+        for (int64_t W = 1; W <= 64 && ls.size() < 7; ++W) {
+          const int64_t ns = W * n_ctas / tiles;  // slices per tile with tiles x ns <= W x CTAs
+          if (ns < 1 || (double)(tiles * ns) < 0.98 * (double)(W * n_ctas)) continue;
+          int64_t len = (n + ns - 1) / ns;
+          len = ((len + kSliceQuantum - 1) / kSliceQuantum) * kSliceQuantum;
+          if ((n + len - 1) / len != ns || len < L0 / 4 || len > 4 * (int64_t)L0) continue;
+          if (std::find(ls.begin(), ls.end(), (int)len) == ls.end()) ls.push_back((int)len);
+        }
+      }
+      for (int len : ls) {
+        if (len < kSliceQuantum) continue;
+        for (int tail = 0; tail < 2; ++tail) {
+          Tiling t = base;
+          t.slice = len;
+          t.tail = tail;
+          settings.push_back(t);
+        }
       }
     }
-    // each length with equal slices and with a halving tail
-    const size_t nc = 2 * ls.size();
-    std::vector<double> lc(nc, 1e300);
-    for (int round = 0; round < 2; ++round)  // two interleaved timings each, the best kept
-      for (size_t k = 0; k < nc; ++k) {
-        if (ls[k / 2] < kSliceQuantum) continue;
-        Tiling t = base;
-        t.slice = ls[k / 2];
-        t.tail = (int)(k % 2);
-        if ((s = install_tiling(c, t, vjp))) return s;
+    std::vector<double> lc(settings.size(), 1e300);
+    for (int round = 0; round < 2; ++round)
+      for (size_t k = 0; k < settings.size(); ++k) {
+        if ((s = install_tiling(c, settings[k], vjp))) return s;
         double cost = 0;
         if ((s = time_tiling(c, vjp, &cost))) return s;
         if (verbose)
-          fprintf(stderr, "nbody tune slice=%d tail=%d items=%d -> %.4g ps/pair\n", t.slice, t.tail, c->n_items,
-                  cost * 1e12);
+          fprintf(stderr, "nbody tune variant=%d block=%d ipt=%d jtile=%d slice=%d tail=%d items=%d -> %.4g ps/pair\n",
+                  settings[k].variant, settings[k].block, settings[k].ipt, settings[k].jtile, settings[k].slice,
+                  settings[k].tail, c->n_items, cost * 1e12);
         lc[k] = std::min(lc[k], cost);
       }
     double bc = 1e300;
-    size_t bk = 2;  // L0, equal slices
-    for (size_t k = 0; k < nc; ++k)
-      if (lc[k] < bc) bc = lc[k], bk = k;
-    bt = base;
-    bt.slice = ls[bk / 2];
-    bt.tail = (int)(bk % 2);
+    for (size_t k = 0; k < settings.size(); ++k)
+      if (lc[k] < bc) bc = lc[k], bt = settings[k];
   }
   bt.n_ctas = 0;
   if ((s = install_tiling(c, bt, vjp))) return s;
@@ -1511,6 +1518,14 @@ nbody_status nbody_get_tuning(const nbody_ctx* c, int32_t* block, int32_t* ipt, 
   if (slice) *slice = c->ft.slice;
   if (n_ctas) *n_ctas = c->ft.n_ctas;
   if (variant) *variant = c->ft.variant + 1;
+  return NBODY_OK;
+}
+
+nbody_status nbody_get_slicing(const nbody_ctx* c, int32_t* tail, int32_t* n_items, int32_t* max_slices) {
+  if (!c) return NBODY_EINVAL;
+  if (tail) *tail = c->ft.tail;
+  if (n_items) *n_items = c->n_items;
+  if (max_slices) *max_slices = c->max_slices;
   return NBODY_OK;
 }
 
