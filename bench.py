@@ -57,6 +57,8 @@ def parse():
     p.add_argument("--impl", choices=("ours", "reference"), default="ours")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-aux", action="store_true", help="skip the other workloads' short measurements")
+    p.add_argument("--aux-only", choices=("two_spheres", "ensemble", "lj", "adjoint"),
+                   help="run only this one of the other workloads' measurements and print it (for profiling)")
     return p.parse_args()
 
 
@@ -420,6 +422,25 @@ def aux_lj(dev, stream):
             xt, vt, at = x2, v2, a2
         sec = _event_time(lambda: nb.nbody_step(ctx, xt, vt, mt, at, False, steps, logt), stream, f"aux_lj_{name}")
         nb.nbody_sync(ctx)
+        kernel = None
+        if prec == nb.MIXED:  # the force kernel alone: CUDA events around it in 200 eagerly issued steps
+            tun = nb.nbody_get_tuning(ctx)
+            ce = nb.nbody_init(law=nb.LENNARD_JONES, precision=prec, n=n, dt=dt, box=box, energy_every=1,
+                               block=tun["block"], i_per_thread=tun["i_per_thread"], j_tile=tun["j_tile"],
+                               variant=tun["variant"])
+            xe, ve, ae = (torch.from_numpy(a).to(dev) for a in (x, v, np.zeros_like(x)))
+            le = torch.empty((200, 1, 9), dtype=torch.float64, device=dev)
+            nb.nbody_step(ce, xe, ve, mt, ae, False, 20, le[:20])
+            nb.nbody_profile(ce, True)
+            eager = _event_time(lambda: nb.nbody_step(ce, xe, ve, mt, ae, True, 200, le), stream, "aux_lj_mixed_eager")
+            ms, k = nb.nbody_kernel_time(ce, 0)
+            nb.nbody_profile(ce, False)
+            nb.nbody_sync(ce)
+            ce.close()
+            us = ms * 1e3 / max(1, k)
+            kernel = {"tuning": tun, "force_kernel_us": us, "eager_step_us": eager / 200 * 1e6,
+                      "ops_per_interaction": 17,
+                      "frac_fp32_roofline_force_kernel": 17.0 * n * n / (us * 1e-6) / (fp32_peak_tops() * 1e12)}
         e = logt.cpu().numpy()[:, 0, 0]
         xf, af = xt.cpu().numpy(), at.cpu().numpy()
         idx = inputs.sample_indices(n, 2048, seed=29)
@@ -430,6 +451,8 @@ def aux_lj(dev, stream):
                     "energy_err_vs_oracle_first_20_steps": float(np.abs(e[:k20] - log_or[:, 0]).max() / abs(E_or0)),
                     "force_err_vs_oracle_at_end": dict(_err_stats(rel_force_error(af[idx], ref)),
                                                        sample="2048 seeded particles after 2500 steps, FP64 oracle")}
+        if kernel:
+            lj[name]["force_kernel"] = kernel
         ctx.close()
     return dict(lj, oracle_energy_drift_first_20_steps=float(np.abs(log_or[:, 0] - E_or0).max() / abs(E_or0)),
                 cpu_baseline={"value": float(n) * n * (k20 + 1) / t_or, "unit": UNIT, "cores": threads,
@@ -553,6 +576,23 @@ def aux_measurements(dev):
     out["paper_lj_gas_10000x2500"] = aux_lj(dev, stream)
     out.update(aux_adjoint(dev, stream))
     return out
+
+
+def run_aux_only(args):
+    """One of the other workloads' measurements alone (rank 0, one GPU), printed as one JSON line."""
+    import torch
+    import paper_2511_02655_gb300 as nb
+    rank, world, local = dist_env()
+    if rank != 0:
+        return 0
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    nb.load()
+    stream = torch.cuda.current_stream()
+    fn = {"two_spheres": aux_two_spheres, "ensemble": aux_ensemble, "lj": aux_lj}.get(args.aux_only)
+    out = fn(dev, stream) if fn else aux_adjoint(dev, stream)
+    print(json.dumps({"aux_only": args.aux_only, "result": out}), flush=True)
+    return 0
 
 
 def run_reference(args):
@@ -765,6 +805,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.aux_only:
+        return run_aux_only(args)
     return run_ours(args)
 
 

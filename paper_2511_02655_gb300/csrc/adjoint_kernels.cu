@@ -12,7 +12,9 @@
 // With P (the gradients with respect to G and eps requested) two more sums,
 //   Pg = sum m_j (d.w_k) / s^3   (w_k . da_k/dG),
 //   Pe = sum m_j (d.w_k) / s^5   (w_k . da_k/deps = -3 G eps Pe),
-// cost two float32 operations more per pair and a third double4 per body and slice.
+// cost two float32 operations more per pair and a third partial per body and slice.
+// Partials are written per work item and slice: on the mixed path as the
+// compensated float32 sums themselves (fpair4), float64 on the FP64 path.
 // Tiling, work distribution, self-pair masking, the compensated per-tile fold
 // and the near-pair refinement (pairs with s^2 below r2_near recomputed from the
 // staged float32 remainders, found through a running minimum of s^2 per
@@ -164,7 +166,7 @@ __global__ void __launch_bounds__(BLOCK) k_vjp_mixed(const PairLaunch L) {
   __shared__ int s_item;
   const float4* __restrict__ sx = static_cast<const float4*>(L.stage_x);
   const float4* __restrict__ sw = static_cast<const float4*>(L.stage_w);
-  double4_32a* __restrict__ part = reinterpret_cast<double4_32a*>(L.part);
+  fpair4* __restrict__ part = reinterpret_cast<fpair4*>(L.part);
   const float eps2 = (float)L.eps2;
   const float r2c = L.r2_near;
   const float4* __restrict__ slo = L.stage_lo;
@@ -265,20 +267,18 @@ __global__ void __launch_bounds__(BLOCK) k_vjp_mixed(const PairLaunch L) {
       }
     }
 
-    constexpr int kW = P ? 3 : 2;  // double4 per body and slice
-    double4_32a* out = part + kW * ((int64_t)w.slice * L.n_total);
+    constexpr int kW = P ? 3 : 2;  // fpair4 per body and slice
+    fpair4* out = part + kW * ((int64_t)w.slice * L.n_total);
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       if (ig[r] < w.i_end) {
-        out[kW * (int64_t)ig[r]] =
-            make_double4_32a((double)hi[r].a1x + lo[r].a1x, (double)hi[r].a1y + lo[r].a1y,
-                         (double)hi[r].a1z + lo[r].a1z, (double)hi[r].a2 + lo[r].a2);
-        out[kW * (int64_t)ig[r] + 1] =
-            make_double4_32a((double)hi[r].gbx + lo[r].gbx, (double)hi[r].gby + lo[r].gby,
-                         (double)hi[r].gbz + lo[r].gbz, (double)hi[r].gm + lo[r].gm);
+        out[kW * (int64_t)ig[r]] = fpair4{make_float4(hi[r].a1x, lo[r].a1x, hi[r].a1y, lo[r].a1y),
+                                          make_float4(hi[r].a1z, lo[r].a1z, hi[r].a2, lo[r].a2)};
+        out[kW * (int64_t)ig[r] + 1] = fpair4{make_float4(hi[r].gbx, lo[r].gbx, hi[r].gby, lo[r].gby),
+                                              make_float4(hi[r].gbz, lo[r].gbz, hi[r].gm, lo[r].gm)};
         if (P)
           out[kW * (int64_t)ig[r] + 2] =
-              make_double4_32a((double)hi[r].pg + lo[r].pg, (double)hi[r].pe + lo[r].pe, 0.0, 0.0);
+              fpair4{make_float4(hi[r].pg, lo[r].pg, hi[r].pe, lo[r].pe), make_float4(0.f, 0.f, 0.f, 0.f)};
       }
     }
   }
@@ -434,7 +434,7 @@ __global__ void __launch_bounds__(BLOCK) k_vjp_mixed2(const PairLaunch L) {
   __shared__ int s_item;
   const float4* __restrict__ sx = static_cast<const float4*>(L.stage_x);
   const float4* __restrict__ sw = static_cast<const float4*>(L.stage_w);
-  double4_32a* __restrict__ part = reinterpret_cast<double4_32a*>(L.part);
+  fpair4* __restrict__ part = reinterpret_cast<fpair4*>(L.part);
   const float eps2 = (float)L.eps2;
   const float2 e2 = make_float2(eps2, eps2);
   const float r2c = L.r2_near;
@@ -584,17 +584,19 @@ __global__ void __launch_bounds__(BLOCK) k_vjp_mixed2(const PairLaunch L) {
       __syncthreads();
     }
 
-    constexpr int kW = P ? 3 : 2;  // double4 per body and slice
-    double4_32a* out = part + kW * ((int64_t)w.slice * L.n_total);
+    constexpr int kW = P ? 3 : 2;  // fpair4 per body and slice
+    fpair4* out = part + kW * ((int64_t)w.slice * L.n_total);
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       if (ig[r] < w.i_end) {
-        double d[NC];
-#pragma unroll
-        for (int c = 0; c < NC; ++c) d[c] = (double)hi[r][c] + (double)lo[r][c];
-        out[kW * (int64_t)ig[r]] = make_double4_32a(d[0], d[1], d[2], d[3]);
-        out[kW * (int64_t)ig[r] + 1] = make_double4_32a(d[4], d[5], d[6], d[7]);
-        if constexpr (P) out[kW * (int64_t)ig[r] + 2] = make_double4_32a(d[8], d[9], 0.0, 0.0);
+        const float(&h)[NC] = hi[r];
+        const float(&l)[NC] = lo[r];
+        out[kW * (int64_t)ig[r]] =
+            fpair4{make_float4(h[0], l[0], h[1], l[1]), make_float4(h[2], l[2], h[3], l[3])};
+        out[kW * (int64_t)ig[r] + 1] =
+            fpair4{make_float4(h[4], l[4], h[5], l[5]), make_float4(h[6], l[6], h[7], l[7])};
+        if constexpr (P)
+          out[kW * (int64_t)ig[r] + 2] = fpair4{make_float4(h[8], l[8], h[9], l[9]), make_float4(0.f, 0.f, 0.f, 0.f)};
       }
     }
   }

@@ -87,7 +87,7 @@ struct PairLaunch {
   const WorkItem* items;
   int32_t n_items;
   unsigned* counter;     // [2]: next item, CTAs done (zero between launches)
-  double* part;          // force: fpair4 (mixed) or double4_32a (FP64) [slices][N]; VJP: (2 or 3 with params) x double4_32a [slices][N]
+  double* part;          // [slices][N] x (force: 1, VJP: 2, or 3 with params) of fpair4 (mixed) or double4_32a (FP64)
   int64_t n_total;
   double eps2;
   const float4* stage_lo;  // mixed: float32 remainders (x - c) - hi [N], near-pair refinement
@@ -189,7 +189,7 @@ cudaError_t launch_centre(const Chunk* chunks, int n_chunks, const int32_t* sys_
 struct AdjLaunch {
   const Chunk* chunks;
   int32_t n_chunks;
-  const double* part;      // 2 (3 with g_params) x double4_32a [slices][N]
+  const double* part;      // 2 (3 with g_params) x fpair4 (mixed) or double4_32a (FP64) [slices][N]
   int64_t n_total;
   double G, coef, dt;      // lam_x += coef * gx ; g_m += coef * gm ; lam_v += dt lam_x
   const double* m;

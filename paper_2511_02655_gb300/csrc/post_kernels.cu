@@ -133,15 +133,41 @@ __global__ void __launch_bounds__(kPostThreads) k_adj_update(const AdjLaunch A) 
   bool bad = false;
   for (int i = c.begin + (int)threadIdx.x; i < c.end; i += kPostThreads) {
     double a1x = 0, a1y = 0, a1z = 0, a2 = 0, gbx = 0, gby = 0, gbz = 0, gm = 0;
+    if (A.precision == 1) {
+      // compensated float32 pairs (fpair4), added as pairs on the FP32 pipe
+      const fpair4* fp = reinterpret_cast<const fpair4*>(A.part);
+      float h[10], l[10];
+#pragma unroll
+      for (int q = 0; q < 10; ++q) h[q] = l[q] = 0.f;
+      auto add = [&](const int q, const float hv, const float lv) {
+        two_sum_acc(h[q], l[q], hv);
+        l[q] += lv;
+      };
 #pragma unroll 4
-    for (int s = 0; s < c.n_slices; ++s) {
-      const int64_t k = kw * ((int64_t)s * A.n_total + i);
-      const double4_32a p = part[k], q = part[k + 1];
-      a1x += p.x, a1y += p.y, a1z += p.z, a2 += p.w;
-      gbx += q.x, gby += q.y, gbz += q.z, gm += q.w;
-      if (A.g_params) {
-        const double4_32a r = part[k + 2];
-        pv[0] += r.x, pv[1] += r.y;
+      for (int s = 0; s < c.n_slices; ++s) {
+        const int64_t k = kw * ((int64_t)s * A.n_total + i);
+        const fpair4 p = fp[k], q = fp[k + 1];
+        add(0, p.xy.x, p.xy.y), add(1, p.xy.z, p.xy.w), add(2, p.zp.x, p.zp.y), add(3, p.zp.z, p.zp.w);
+        add(4, q.xy.x, q.xy.y), add(5, q.xy.z, q.xy.w), add(6, q.zp.x, q.zp.y), add(7, q.zp.z, q.zp.w);
+        if (A.g_params) {
+          const fpair4 r = fp[k + 2];
+          add(8, r.xy.x, r.xy.y), add(9, r.xy.z, r.xy.w);
+        }
+      }
+      auto d = [&](const int q) { return (double)h[q] + (double)l[q]; };
+      a1x = d(0), a1y = d(1), a1z = d(2), a2 = d(3), gbx = d(4), gby = d(5), gbz = d(6), gm = d(7);
+      if (A.g_params) pv[0] += d(8), pv[1] += d(9);
+    } else {
+#pragma unroll 4
+      for (int s = 0; s < c.n_slices; ++s) {
+        const int64_t k = kw * ((int64_t)s * A.n_total + i);
+        const double4_32a p = part[k], q = part[k + 1];
+        a1x += p.x, a1y += p.y, a1z += p.z, a2 += p.w;
+        gbx += q.x, gby += q.y, gbz += q.z, gm += q.w;
+        if (A.g_params) {
+          const double4_32a r = part[k + 2];
+          pv[0] += r.x, pv[1] += r.y;
+        }
       }
     }
     const double mi = A.m[i];
