@@ -439,8 +439,8 @@ def aux_lj(dev, stream):
             ce.close()
             us = ms * 1e3 / max(1, k)
             kernel = {"tuning": tun, "force_kernel_us": us, "eager_step_us": eager / 200 * 1e6,
-                      "ops_per_interaction": 17,
-                      "frac_fp32_roofline_force_kernel": 17.0 * n * n / (us * 1e-6) / (fp32_peak_tops() * 1e12)}
+                      "ops_per_interaction": 16,
+                      "frac_fp32_roofline_force_kernel": 16.0 * n * n / (us * 1e-6) / (fp32_peak_tops() * 1e12)}
         e = logt.cpu().numpy()[:, 0, 0]
         xf, af = xt.cpu().numpy(), at.cpu().numpy()
         idx = inputs.sample_indices(n, 2048, seed=29)

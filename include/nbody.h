@@ -84,10 +84,11 @@ typedef struct {
   int32_t slice;        /* force kernel: j-bodies per work item, multiple of j_tile (0 = autotune) */
   uint32_t flags;       /* NBODY_FLAG_* */
   int32_t variant;      /* mixed force and adjoint-VJP kernels: 1 = scalar float32, 2 = packed
-                           float32x2, 3 = packed force kernel compiled for 4 CTAs per SM (a
-                           register cap; softened gravity, tiling 128 x 2 x 256; the VJP
-                           then uses 2), 0 = autotune (each kernel separately); must be 0 or 1
-                           for NBODY_FP64; NBODY_LAW_LJ with NBODY_MIXED uses 2 */
+                           float32x2, 3 = packed force kernel under a register cap (softened
+                           gravity: 4 CTAs per SM, tiling 128 x 2 x 256; Lennard-Jones: 6 CTAs
+                           per SM, tilings 128 x 1 x 256 and 128 x 1 x 512; the VJP then uses
+                           2), 0 = autotune (each kernel separately); must be 0 or 1 for
+                           NBODY_FP64; NBODY_LAW_LJ with NBODY_MIXED takes 0, 2 or 3 */
   int32_t law;          /* nbody_law */
   int32_t reserved;     /* must be 0 */
   double lj_epsilon;    /* Lennard-Jones well depth (finite; law = NBODY_LAW_LJ) */

@@ -197,8 +197,9 @@ def nbody_init(*, G=1.0, eps=0.0, dt=0.0, precision=MIXED, offsets=None, n=None,
                box=0.0, stream=None) -> Context:
     """Creates a context for systems with row ranges ``offsets`` (or one system of ``n`` bodies).
 
-    Tile parameters (and the mixed kernel ``variant``: 1 scalar, 2 packed, 3 packed with
-    a 4-CTA register cap) left at 0 are chosen by the autotuner during init. ``law``: GRAVITY (G, eps) or
+    Tile parameters (and the mixed kernel ``variant``: 1 scalar, 2 packed, 3 packed under
+    a register cap: 4 CTAs per SM for gravity, 6 for Lennard-Jones) left at 0 are chosen by
+    the autotuner during init. ``law``: GRAVITY (G, eps) or
     LENNARD_JONES (lj_epsilon, lj_sigma; eps softens r^2); ``box`` > 0 adds
     reflecting walls of the cube [0, box]^3.
     ``stream``: a torch.cuda.Stream (default: the current stream).

@@ -104,6 +104,9 @@ bool allocation_holds(const void* p, size_t bytes, size_t* avail) {
 
 struct nbody_ctx {
   nbody_config cfg{};
+  // mixed Lennard-Jones: positions are staged in units of sigma, (x - c) / sigma,
+  // so that u = sigma^2 / r^2 is the reciprocal itself; 1 everywhere else
+  double stage_scale = 1.0;
   int device = 0;
   int sm_count = 0;
   std::string dev_name;  // cudaDeviceProp::name, part of the tuning-cache key
@@ -432,11 +435,12 @@ PairLaunch pair_launch(nbody_ctx* c, bool vjp, bool refine = true, bool phi = tr
   const bool lo = refine && c->cfg.precision == NBODY_MIXED && c->stage_lo.p;
   L.stage_lo = lo ? static_cast<const float4*>(c->stage_lo.p) : nullptr;
   L.law = vjp ? 0 : c->cfg.law;
-  L.sigma2 = c->cfg.lj_sigma * c->cfg.lj_sigma;
+  const double sc2 = c->stage_scale * c->stage_scale;  // staged length units: sigma (mixed LJ) or 1
+  L.sigma2 = c->cfg.lj_sigma * c->cfg.lj_sigma * sc2;   // 1 for mixed Lennard-Jones
   L.r2_near = 0.f;
   if (lo)
     L.r2_near = c->cfg.law == NBODY_LAW_LJ
-                    ? (float)(kNearRadiusSigma * kNearRadiusSigma * L.sigma2 + c->cfg.eps * c->cfg.eps)
+                    ? (float)(kNearRadiusSigma * kNearRadiusSigma * L.sigma2 + c->cfg.eps * c->cfg.eps * sc2)
                     : (float)(kNearRadiusEps * kNearRadiusEps * c->cfg.eps * c->cfg.eps);
   L.stage_x = c->stage.p;
   L.stage_w = c->stage_w.p;
@@ -445,7 +449,7 @@ PairLaunch pair_launch(nbody_ctx* c, bool vjp, bool refine = true, bool phi = tr
   L.counter = c->counter;
   L.part = static_cast<double*>(c->part.p);
   L.n_total = c->n_total;
-  L.eps2 = c->cfg.eps * c->cfg.eps;
+  L.eps2 = c->cfg.eps * c->cfg.eps * sc2;
   const Tiling& t = vjp ? c->vt : c->ft;
   L.block = t.block, L.ipt = t.ipt, L.jtile = t.jtile, L.n_ctas = t.n_ctas;
   L.variant = t.variant;
@@ -519,6 +523,7 @@ PostLaunch post_launch(nbody_ctx* c, unsigned mode, double* x, double* v, const 
   P.precision = c->cfg.precision;
   P.law = c->cfg.law;
   P.lj_eps = c->cfg.lj_epsilon;
+  P.stage_scale = c->stage_scale;
   P.box = c->cfg.box;
   P.stage = c->stage.p;
   P.stage_lo = c->stage_lo.p;
@@ -630,9 +635,11 @@ nbody_status fill_synthetic(nbody_ctx* c, bool with_w) {
   if (c->cfg.precision == NBODY_MIXED) {
     std::vector<float4> h(n), hl(n);
     for (int64_t i = 0; i < n; ++i) {
-      const float hx = (float)pos[3 * i], hy = (float)pos[3 * i + 1], hz = (float)pos[3 * i + 2];
+      const double X = pos[3 * i] * c->stage_scale, Y = pos[3 * i + 1] * c->stage_scale,
+                   Z = pos[3 * i + 2] * c->stage_scale;
+      const float hx = (float)X, hy = (float)Y, hz = (float)Z;
       h[i] = make_float4(hx, hy, hz, (float)mass[i]);
-      hl[i] = make_float4((float)(pos[3 * i] - hx), (float)(pos[3 * i + 1] - hy), (float)(pos[3 * i + 2] - hz), 0.f);
+      hl[i] = make_float4((float)(X - hx), (float)(Y - hy), (float)(Z - hz), 0.f);
     }
     NB_CUDA(c, cudaMemcpy(c->stage.p, h.data(), n * sizeof(float4), cudaMemcpyHostToDevice));
     if (c->stage_lo.p) NB_CUDA(c, cudaMemcpy(c->stage_lo.p, hl.data(), n * sizeof(float4), cudaMemcpyHostToDevice));
@@ -799,7 +806,8 @@ nbody_status autotune(nbody_ctx* c, bool vjp) {
       variants = g.variant ? std::vector<int>{std::min(g.variant - 1, 1)} : std::vector<int>{0, 1};
     else
       variants = g.variant ? std::vector<int>{g.variant - 1} : std::vector<int>{0, 1, 2};
-    if (!vjp && g.law == NBODY_LAW_LJ) variants = {1};  // Lennard-Jones: packed kernel only
+    // Lennard-Jones: the packed kernel, uncapped and capped (6 CTAs per SM)
+    if (!vjp && g.law == NBODY_LAW_LJ) variants = g.variant ? std::vector<int>{g.variant - 1} : std::vector<int>{1, 2};
   }
   for (int var : variants)
     for (int b : blocks) {
@@ -954,7 +962,7 @@ nbody_status validate_cfg(const nbody_config* g) {
   if (!finite(g->box) || g->box < 0) return NBODY_EINVAL;
   if (g->law == NBODY_LAW_LJ) {
     if (!finite(g->lj_epsilon) || !finite(g->lj_sigma) || !(g->lj_sigma > 0)) return NBODY_EINVAL;
-    if (g->precision == NBODY_MIXED && (g->variant == 1 || g->variant == 3)) return NBODY_EINVAL;
+    if (g->precision == NBODY_MIXED && g->variant == 1) return NBODY_EINVAL;  // no scalar Lennard-Jones kernel
   }
   return NBODY_OK;
 }
@@ -1216,6 +1224,7 @@ nbody_status nbody_init(nbody_ctx** out, const nbody_config* cfg, int64_t n_syst
   nbody_ctx* c = new (std::nothrow) nbody_ctx();
   if (!c) return fail(nullptr, NBODY_ENOMEM, "host allocation failed");
   c->cfg = *cfg;
+  if (cfg->precision == NBODY_MIXED && cfg->law == NBODY_LAW_LJ) c->stage_scale = 1.0 / cfg->lj_sigma;
   c->device = dev;
   c->sm_count = prop.multiProcessorCount;
   c->dev_name = prop.name;
@@ -1283,7 +1292,7 @@ nbody_status nbody_init(nbody_ctx** out, const nbody_config* cfg, int64_t n_syst
     t.ipt = cfg->i_per_thread ? cfg->i_per_thread : 2;
     t.jtile = cfg->j_tile ? cfg->j_tile : 128;
     t.slice = cfg->slice;
-    t.variant = cfg->precision != NBODY_MIXED ? 0 : cfg->law == NBODY_LAW_LJ ? 1 : cfg->variant == 3 ? 2 : cfg->variant == 2 ? 1 : 0;
+    t.variant = cfg->precision != NBODY_MIXED ? 0 : cfg->law == NBODY_LAW_LJ ? (cfg->variant == 3 ? 2 : 1) : cfg->variant == 3 ? 2 : cfg->variant == 2 ? 1 : 0;
     if ((s = install_tiling(c, t, false))) return bail(s);
   }
   if (cudaDeviceSynchronize() != cudaSuccess) return bail(fail(c, NBODY_ECUDA, "init synchronisation failed"));

@@ -229,10 +229,12 @@ __device__ __forceinline__ void pair2_f32x2(const float2 xj, const float2 yj, co
   if (PHI) pp = __fadd2_rn(pp, ms);
 }
 
-// Lennard-Jones pair (Eq. 1) on two j-bodies: with u = sigma^2 / r^2,
-//   sum (u^3 - 2 u^6) / r^2 d  (a_i = 24 eps / m_i times this)
-//   sum (u^6 - u^3)            (phi_i = 4 eps / m_i times this),
-// 17 float32 operations (8.5 packed) and one MUFU.RCP per interaction.
+// Lennard-Jones pair (Eq. 1) on two j-bodies. The mixed path stages positions
+// in units of sigma, so u = sigma^2 / r^2 is the reciprocal of the staged s^2
+// itself (eps is scaled alike) and the kernel sums
+//   sum (u^3 - 2 u^6) u d'    (a_i = 24 eps / (m_i sigma) times this)
+//   sum (u^6 - u^3)           (phi_i = 4 eps / m_i times this),
+// 16 float32 operations (8 packed) and one MUFU.RCP per interaction.
 // Near pairs are common in a gas (a dozen neighbours inside the 4 sigma
 // refinement radius per particle), so instead of a running minimum each pair
 // sets its bit in the sub-block's near mask (bit0 for the first j-body, the
@@ -240,23 +242,22 @@ __device__ __forceinline__ void pair2_f32x2(const float2 xj, const float2 yj, co
 template <bool MASK, bool PHI>
 __device__ __forceinline__ void pair2_lj_f32x2(const float2 xj, const float2 yj, const float2 zj, const int jg0,
                                                const int ig, const float2 nx, const float2 ny, const float2 nz,
-                                               const float2 e2, const float2 s2, float2& ax, float2& ay, float2& az,
-                                               float2& pp, unsigned& near, const unsigned bit0, const float r2c) {
+                                               const float2 e2, float2& ax, float2& ay, float2& az, float2& pp,
+                                               unsigned& near, const unsigned bit0, const float r2c) {
   const float2 dx = __fadd2_rn(xj, nx);
   const float2 dy = __fadd2_rn(yj, ny);
   const float2 dz = __fadd2_rn(zj, nz);
   const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __ffma2_rn(dz, dz, e2)));
   if (r2.x < r2c) near |= bit0;
   if (r2.y < r2c) near |= bit0 << 1;
-  float2 inv2 = make_float2(rcp_approx(r2.x), rcp_approx(r2.y));
+  float2 u = make_float2(rcp_approx(r2.x), rcp_approx(r2.y));  // sigma^2 / r^2
   if (MASK) {
-    inv2.x = (jg0 == ig) ? 0.f : inv2.x;
-    inv2.y = (jg0 + 1 == ig) ? 0.f : inv2.y;
+    u.x = (jg0 == ig) ? 0.f : u.x;
+    u.y = (jg0 + 1 == ig) ? 0.f : u.y;
   }
-  const float2 u = __fmul2_rn(s2, inv2);
   const float2 u3 = __fmul2_rn(u, __fmul2_rn(u, u));
   const float2 u6 = __fmul2_rn(u3, u3);
-  const float2 w = __fmul2_rn(__ffma2_rn(u6, make_float2(-2.f, -2.f), u3), inv2);
+  const float2 w = __fmul2_rn(__ffma2_rn(u6, make_float2(-2.f, -2.f), u3), u);
   ax = __ffma2_rn(dx, w, ax);
   ay = __ffma2_rn(dy, w, ay);
   az = __ffma2_rn(dz, w, az);
@@ -289,9 +290,9 @@ __device__ __forceinline__ void quad_f32x2(const float* tx, const float* ty, con
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       pair2_lj_f32x2<MASK, PHI>(make_float2(X.x, X.y), make_float2(Y.x, Y.y), make_float2(Z.x, Z.y), jg, ig[r], nx[r],
-                           ny[r], nz[r], e2, s2, ax[r], ay[r], az[r], pp[r], near[r], qbit, r2c);
+                                ny[r], nz[r], e2, ax[r], ay[r], az[r], pp[r], near[r], qbit, r2c);
       pair2_lj_f32x2<MASK, PHI>(make_float2(X.z, X.w), make_float2(Y.z, Y.w), make_float2(Z.z, Z.w), jg + 2, ig[r],
-                           nx[r], ny[r], nz[r], e2, s2, ax[r], ay[r], az[r], pp[r], near[r], qbit << 2, r2c);
+                                nx[r], ny[r], nz[r], e2, ax[r], ay[r], az[r], pp[r], near[r], qbit << 2, r2c);
     }
   }
 }
@@ -604,6 +605,8 @@ __device__ __forceinline__ void items_fp64(const PairLaunch& L, unsigned* counte
   NBODY_FORCE_TILINGS(X) X(128, 1, 512) X(128, 2, 512) X(128, 4, 512) X(256, 1, 512) X(256, 2, 512) X(256, 4, 512)
 // The register-capped packed variant (4 CTAs per SM): softened gravity only.
 #define NBODY_CAPPED_TILINGS(X) X(128, 2, 256)
+// The register-capped Lennard-Jones variant (6 CTAs per SM, <= 85 registers).
+#define NBODY_LJ_CAPPED_TILINGS(X) X(128, 1, 256) X(128, 1, 512)
 #define NBODY_LJ_MIXED_TILINGS(X) \
   X(128, 1, 256) X(256, 1, 256) X(128, 2, 256) X(128, 1, 512) X(256, 1, 512) X(256, 2, 512)
 #define NBODY_LJ_FP64_TILINGS(X) X(128, 1, 128) X(256, 1, 128) X(128, 2, 128) X(256, 2, 128)

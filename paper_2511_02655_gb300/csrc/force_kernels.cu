@@ -31,11 +31,16 @@ namespace nbody {
 namespace {
 
 // Standalone force kernels: one pass over the work list, then the last CTA to
-// retire resets the item counter for the next launch.
+// retire resets the item counter for the next launch. They are launched as
+// programmatic dependents (launch_pdl): pdl_wait() holds every CTA until the
+// kernel before them on the stream has completed, so only the launch latency
+// overlaps with that kernel's tail.
 template <int BLOCK, int R, int J>
 __global__ void __launch_bounds__(BLOCK) k_force_mixed(const PairLaunch L) {
   __shared__ fc::SmemMixed<J> sm;
+  pdl_wait();
   fc::items_mixed<BLOCK, R, J>(L, L.counter, sm);
+  pdl_trigger();
   retire_cta(L.counter);
 }
 
@@ -58,14 +63,18 @@ __global__ void __launch_bounds__(BLOCK, (MINB > 0 ? MINB
                                                   : (NBODY_MIN_CTAS > 0 ? NBODY_MIN_CTAS : packed_min_ctas(BLOCK, R))))
     k_force_mixed2(const PairLaunch L) {
   __shared__ fc::SmemMixed2<J> sm;
+  pdl_wait();
   fc::items_mixed2<LAW, BLOCK, R, J, PHI>(L, L.counter, sm);
+  pdl_trigger();
   retire_cta(L.counter);
 }
 
 template <int LAW, int BLOCK, int R, int J>
 __global__ void __launch_bounds__(BLOCK) k_force_fp64(const PairLaunch L) {
   __shared__ fc::SmemFp64<J> sm;
+  pdl_wait();
   fc::items_fp64<LAW, BLOCK, R, J>(L, L.counter, sm);
+  pdl_trigger();
   retire_cta(L.counter);
 }
 
@@ -81,24 +90,34 @@ int occupancy_of(K kern, int block) {
 cudaError_t launch_force(int precision, const PairLaunch& L, cudaStream_t st) {
   if (L.n_ctas <= 0) return cudaErrorInvalidConfiguration;
   if (L.law == 1) {
+    if (precision == 1 && L.variant == 2) {  // register-capped: 6 CTAs per SM
 #define NBODY_X(B, R, J)                                               \
   if (L.block == B && L.ipt == R && L.jtile == J) {                    \
     if (L.phi)                                                         \
-      k_force_mixed2<1, B, R, J, true><<<L.n_ctas, B, 0, st>>>(L);     \
+      return launch_pdl(k_force_mixed2<1, B, R, J, true, 6>, L.n_ctas, B, st, L);  \
     else                                                               \
-      k_force_mixed2<1, B, R, J, false><<<L.n_ctas, B, 0, st>>>(L);    \
-    return cudaGetLastError();                                         \
+      return launch_pdl(k_force_mixed2<1, B, R, J, false, 6>, L.n_ctas, B, st, L); \
   }
-    if (precision == 1) {
-      if (L.variant != 1) return cudaErrorInvalidConfiguration;
-      NBODY_LJ_MIXED_TILINGS(NBODY_X)
+      NBODY_LJ_CAPPED_TILINGS(NBODY_X)
+#undef NBODY_X
       return cudaErrorInvalidConfiguration;
     }
-#undef NBODY_X
+    if (precision == 1) {
+      if (L.variant != 1) return cudaErrorInvalidConfiguration;
 #define NBODY_X(B, R, J)                                               \
   if (L.block == B && L.ipt == R && L.jtile == J) {                    \
-    k_force_fp64<1, B, R, J><<<L.n_ctas, B, 0, st>>>(L);               \
-    return cudaGetLastError();                                         \
+    if (L.phi)                                                         \
+      return launch_pdl(k_force_mixed2<1, B, R, J, true>, L.n_ctas, B, st, L);     \
+    else                                                               \
+      return launch_pdl(k_force_mixed2<1, B, R, J, false>, L.n_ctas, B, st, L);    \
+  }
+      NBODY_LJ_MIXED_TILINGS(NBODY_X)
+#undef NBODY_X
+      return cudaErrorInvalidConfiguration;
+    }
+#define NBODY_X(B, R, J)                                               \
+  if (L.block == B && L.ipt == R && L.jtile == J) {                    \
+    return launch_pdl(k_force_fp64<1, B, R, J>, L.n_ctas, B, st, L);               \
   }
     if (L.variant != 0) return cudaErrorInvalidConfiguration;
     NBODY_LJ_FP64_TILINGS(NBODY_X)
@@ -111,10 +130,9 @@ cudaError_t launch_force(int precision, const PairLaunch& L, cudaStream_t st) {
 #define NBODY_X(B, R, J)                                                \
   if (L.block == B && L.ipt == R && L.jtile == J) {                     \
     if (L.phi)                                                          \
-      k_force_mixed2<0, B, R, J, true, 4><<<L.n_ctas, B, 0, st>>>(L);   \
+      return launch_pdl(k_force_mixed2<0, B, R, J, true, 4>, L.n_ctas, B, st, L);   \
     else                                                                \
-      k_force_mixed2<0, B, R, J, false, 4><<<L.n_ctas, B, 0, st>>>(L);  \
-    return cudaGetLastError();                                          \
+      return launch_pdl(k_force_mixed2<0, B, R, J, false, 4>, L.n_ctas, B, st, L);  \
   }
       NBODY_CAPPED_TILINGS(NBODY_X)
 #undef NBODY_X
@@ -124,12 +142,11 @@ cudaError_t launch_force(int precision, const PairLaunch& L, cudaStream_t st) {
 #define NBODY_X(B, R, J)                                               \
   if (L.block == B && L.ipt == R && L.jtile == J) {                    \
     if (L.variant == 1 && L.phi)                                       \
-      k_force_mixed2<0, B, R, J, true><<<L.n_ctas, B, 0, st>>>(L);     \
+      return launch_pdl(k_force_mixed2<0, B, R, J, true>, L.n_ctas, B, st, L);     \
     else if (L.variant == 1)                                           \
-      k_force_mixed2<0, B, R, J, false><<<L.n_ctas, B, 0, st>>>(L);    \
+      return launch_pdl(k_force_mixed2<0, B, R, J, false>, L.n_ctas, B, st, L);    \
     else                                                               \
-      k_force_mixed<B, R, J><<<L.n_ctas, B, 0, st>>>(L);               \
-    return cudaGetLastError();                                         \
+      return launch_pdl(k_force_mixed<B, R, J>, L.n_ctas, B, st, L);               \
   }
     NBODY_MIXED_TILINGS(NBODY_X)
 #undef NBODY_X
@@ -138,8 +155,7 @@ cudaError_t launch_force(int precision, const PairLaunch& L, cudaStream_t st) {
   if (L.variant != 0) return cudaErrorInvalidConfiguration;
 #define NBODY_X(B, R, J)                                               \
   if (L.block == B && L.ipt == R && L.jtile == J) {                    \
-    k_force_fp64<0, B, R, J><<<L.n_ctas, B, 0, st>>>(L);               \
-    return cudaGetLastError();                                         \
+    return launch_pdl(k_force_fp64<0, B, R, J>, L.n_ctas, B, st, L);               \
   }
   NBODY_FORCE_TILINGS(NBODY_X)
 #undef NBODY_X
@@ -148,6 +164,14 @@ cudaError_t launch_force(int precision, const PairLaunch& L, cudaStream_t st) {
 
 int force_ctas_per_sm(int precision, int variant, int block, int ipt, int jtile, int law) {
   if (law == 1) {
+    if (precision == 1 && variant == 2) {
+#define NBODY_X(B, R, J)                                                                                     \
+  if (block == B && ipt == R && jtile == J)                                                                  \
+    return std::min(occupancy_of(k_force_mixed2<1, B, R, J, true, 6>, B), occupancy_of(k_force_mixed2<1, B, R, J, false, 6>, B));
+      NBODY_LJ_CAPPED_TILINGS(NBODY_X)
+#undef NBODY_X
+      return 0;
+    }
     if (precision == 1) {
       if (variant != 1) return 0;
 #define NBODY_X(B, R, J) \

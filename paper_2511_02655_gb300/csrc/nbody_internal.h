@@ -55,6 +55,32 @@ __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float t) {
   lo += err;
 }
 
+// Programmatic dependent launch (sm_90 and later) between the kernels of a
+// step: a kernel launched with launch_pdl may be scheduled while the kernel
+// before it on the stream is still finishing; pdl_wait(), its first
+// statement, waits (in hardware) until that grid has completed and its memory
+// is visible, so data dependences are exactly those of plain stream order and
+// only the launch latency overlaps. pdl_trigger() lets the next such kernel be
+// scheduled once every CTA of this one has passed it. Both are no-ops for a
+// kernel launched without the attribute.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kern)(KArgs...), unsigned grid, unsigned block, cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 // Device status word bits (latched, read by nbody_sync).
 constexpr unsigned kFlagNonFinite = 1u;
 constexpr unsigned kFlagTimeout = 2u;
@@ -164,6 +190,7 @@ struct PostLaunch {
   int precision;
   int law;                 // 0 gravity: a = G S, phi = -G S_phi; 1 Lennard-Jones: a = 24 eps S / m, phi = 4 eps S_phi / m
   double lj_eps;
+  double stage_scale;      // mixed: staged positions are (x - c) * stage_scale (1 / sigma for Lennard-Jones)
   double box;              // > 0: reflecting walls of [0, box]^3 applied after the drift
   void* stage;             // float4 / double4_32a [N]
   void* stage_lo;          // mixed: float4 remainders of the staged coordinates [N] (nullable)

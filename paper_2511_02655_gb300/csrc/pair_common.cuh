@@ -38,41 +38,12 @@ __device__ __forceinline__ void refine_pair(const float4* __restrict__ lo, const
   r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
 }
 
-// The Lennard-Jones pair correction of correct_pair<1> with the remainders
-// given (lj of the j-body from the shared-memory tile, li of the i-body from
-// registers) instead of read from the staging remainders in global memory:
-// the gas has a dozen near pairs per particle, and the loads' latency would
-// stall the warp at every one.
-__device__ __forceinline__ void correct_pair_lj(const float qx, const float qy, const float qz, const int jg,
-                                                const int ig, const int i_end, const float xi, const float yi,
-                                                const float zi, const float eps2, const float r2c, const float ljx,
-                                                const float ljy, const float ljz, const float lix, const float liy,
-                                                const float liz, const float s2, float& ax, float& ay, float& az,
-                                                float& pp) {
-  const float dx = qx - xi;
-  const float dy = qy - yi;
-  const float dz = qz - zi;
-  const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
-  if (!(r2 < r2c) || ig >= i_end || ig == jg) return;
-  const float rx = dx + (ljx - lix), ry = dy + (ljy - liy), rz = dz + (ljz - liz);
-  const float rr2 = fmaf(rx, rx, fmaf(ry, ry, fmaf(rz, rz, eps2)));
-  const float iu = rcp_approx(r2);
-  const float su2 = s2 * iu, su6 = su2 * (su2 * su2), su12 = su6 * su6;
-  const float wu = fmaf(su12, -2.f, su6) * iu;
-  const float ir = rcp_approx(rr2);
-  const float sr2 = s2 * ir, sr6 = sr2 * (sr2 * sr2), sr12 = sr6 * sr6;
-  const float wr = fmaf(sr12, -2.f, sr6) * ir;
-  ax += fmaf(rx, wr, -(dx * wu));
-  ay += fmaf(ry, wr, -(dy * wu));
-  az += fmaf(rz, wr, -(dz * wu));
-  pp += fmaf(sr6, -1.f, sr12) - fmaf(su6, -1.f, su12);
-}
-
 // Second look at one pair (j-body q at global index jg, i-body at ig) of a
 // flagged sub-block: if it is near and not the self pair, replace its
 // unrefined contribution in (ax, ay, az, pp) by the refined one. The
 // unrefined terms are recomputed with exactly the first pass's operations.
-// LAW 0: softened gravity (q.w = m_j); LAW 1: Lennard-Jones (s2 = sigma^2).
+// LAW 0: softened gravity (q.w = m_j); LAW 1: Lennard-Jones (s2 = sigma^2 in the
+// staged length unit, i.e. 1 on the mixed path).
 template <int LAW = 0>
 __device__ __forceinline__ void correct_pair(const float4 q, const int jg, const int ig, const int i_end,
                                              const float xi, const float yi, const float zi, const float eps2,

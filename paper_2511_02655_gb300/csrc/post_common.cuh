@@ -67,13 +67,14 @@ __device__ __forceinline__ void reflect(double& x, double& v, const double box) 
   }
 }
 
-// Staging entry of body i. Mixed: float4 (x - c, m) rounded to float32 and,
-// when lo is given, the float32 remainders (x - c) - hi used by the near-pair
-// refinement of the force kernels. FP64: double4 (x, m).
+// Staging entry of body i. Mixed: float4 ((x - c) * scale, m) rounded to
+// float32 and, when lo is given, the float32 remainders of the scaled
+// coordinates used by the near-pair refinement of the force kernels (scale is
+// 1, or 1 / sigma for Lennard-Jones). FP64: double4 (x, m).
 __device__ __forceinline__ void stage_store(int precision, void* stage, int i, double x, double y, double z,
-                                            double m, const double* c, void* lo = nullptr) {
+                                            double m, const double* c, void* lo = nullptr, double scale = 1.0) {
   if (precision == 1) {
-    const double X = x - c[0], Y = y - c[1], Z = z - c[2];
+    const double X = (x - c[0]) * scale, Y = (y - c[1]) * scale, Z = (z - c[2]) * scale;
     const float hx = (float)X, hy = (float)Y, hz = (float)Z;
     static_cast<float4*>(stage)[i] = make_float4(hx, hy, hz, (float)m);
     if (lo)
@@ -177,8 +178,9 @@ __device__ __forceinline__ bool post_body(const PostLaunch& P, const unsigned mo
   if (mode & kCombine) {
     if (P.law == 0) {  // softened gravity
       ax = P.G * sx, ay = P.G * sy, az = P.G * sz, ph = -P.G * sp;
-    } else {  // Lennard-Jones: per unit mass of body i
-      const double im = 1.0 / m, ca = 24.0 * P.lj_eps * im, cp = 4.0 * P.lj_eps * im;
+    } else {  // Lennard-Jones: per unit mass of body i (sums over staged coordinates in units of sigma
+              // carry one factor sigma: S = sigma * sum (u^3 - 2 u^6) d / r^2, hence the stage_scale)
+      const double im = 1.0 / m, ca = 24.0 * P.lj_eps * P.stage_scale * im, cp = 4.0 * P.lj_eps * im;
       ax = ca * sx, ay = ca * sy, az = ca * sz, ph = cp * sp;
     }
     P.a[3 * i + 0] = ax, P.a[3 * i + 1] = ay, P.a[3 * i + 2] = az;
@@ -217,7 +219,7 @@ __device__ __forceinline__ bool post_body(const PostLaunch& P, const unsigned mo
     }
     if (mode & (kKickEnd | kDrift)) P.v[3 * i + 0] = v0, P.v[3 * i + 1] = v1, P.v[3 * i + 2] = v2;
   }
-  if (mode & kStage) stage_store(P.precision, P.stage, i, x0, x1, x2, m, cen, P.stage_lo);
+  if (mode & kStage) stage_store(P.precision, P.stage, i, x0, x1, x2, m, cen, P.stage_lo, P.stage_scale);
   return bad;
 }
 

@@ -15,6 +15,8 @@ namespace nbody {
 namespace {
 
 __global__ void __launch_bounds__(kPostThreads) k_post(const PostLaunch P) {
+  pdl_wait();     // the force kernel before it has finished writing the partials
+  pdl_trigger();  // the next force kernel may be scheduled once every CTA has started
   Chunk c = P.chunks[blockIdx.x];
   if (!chunk_ok(c, P.n_total, P.n_sys, (P.mode & kCombine) ? P.part_slices : 0, P.status))
     c.begin = c.end = 0;  // NBODY_DEBUG builds only: processed as an empty chunk
@@ -257,8 +259,7 @@ cudaError_t launch_copy4(const Copy4& C, int n_sms, cudaStream_t st) {
 
 cudaError_t launch_post(const PostLaunch& P, cudaStream_t st) {
   if (P.n_chunks <= 0) return cudaSuccess;
-  k_post<<<P.n_chunks, kPostThreads, 0, st>>>(P);
-  return cudaGetLastError();
+  return launch_pdl(k_post, (unsigned)P.n_chunks, kPostThreads, st, P);
 }
 
 cudaError_t launch_centre(const Chunk* chunks, int n_chunks, const int32_t* sys_chunk, const int64_t* off, int n_sys,

@@ -61,7 +61,7 @@ def _cfg(**kw):
                                  dict(j_tile=100), dict(energy_every=-1), dict(flags=64), dict(G=float("nan")),
                                  dict(variant=4), dict(variant=2, precision=0), dict(variant=3, precision=0),
                                  dict(law=2), dict(reserved=1), dict(box=-1.0), dict(law=1, lj_sigma=0.0),
-                                 dict(law=1, variant=1), dict(law=1, variant=3)])
+                                 dict(law=1, variant=1)])
 def test_init_rejects_bad_config_before_touching_a_device(lib, bad):
     h = ctypes.c_void_p(123)
     offs = (ctypes.c_int64 * 2)(0, 16)

@@ -39,6 +39,34 @@ def test_lj_forces(nb, prec, density):
         assert_elem_close(phi, phi_ref, MIX_MAX, "phi")
 
 
+@pytest.mark.parametrize("variant,j_tile", [(2, 256), (2, 512), (3, 256), (3, 512)])
+def test_lj_packed_variants_forces_and_steps(nb, variant, j_tile):
+    """The packed Lennard-Jones kernel, uncapped (variant 2) and compiled for 6 CTAs per SM
+    (variant 3), at both j-tiles the capped build has: forces and 20 steps between walls."""
+    import torch
+    x, v, m, box = inputs.lj_gas(3001, seed=21, density=0.05, temperature=2.0)
+    kw = dict(block=128, i_per_thread=1, j_tile=j_tile, variant=variant)
+    a, phi = _lj_forces(nb, nb.MIXED, x, m, **kw)
+    a_ref, phi_ref = oracle.lj_forces(x, m)
+    e = force_rel_err(a, a_ref)
+    assert np.median(e) <= MIX_MED and e.max() <= MIX_MAX, (np.median(e), e.max())
+    assert_elem_close(phi, phi_ref, MIX_MAX, "phi")
+    dt, T = 5e-3, 20
+    ctx = nb.nbody_init(law=nb.LENNARD_JONES, precision=nb.MIXED, n=len(m), dt=dt, box=box, energy_every=5, **kw)
+    assert nb.nbody_get_tuning(ctx)["variant"] == variant
+    xt, vt, mt = to_dev(x, v, m)
+    at = torch.empty_like(xt)
+    log = nb.nbody_step(ctx, xt, vt, mt, at, False, T)
+    nb.nbody_sync(ctx)
+    xr, vr, ar, logr = oracle.lj_kdk(x, v, m, 1.0, 1.0, 0.0, box, dt, T, energy_every=5)
+    xg, vg, ag, lg = to_np(xt, vt, at, log)
+    assert xg.min() >= 0 and xg.max() <= box
+    assert np.abs(xg - xr).max() <= 1e-5
+    e = force_rel_err(ag, ar)
+    assert np.median(e) <= MIX_MED and e.max() <= MIX_MAX, (np.median(e), e.max())
+    np.testing.assert_allclose(lg[:, 0, 0], logr[:, 0], rtol=1e-5)
+
+
 @pytest.mark.parametrize("prec", [0, 1])
 def test_lj_kdk_with_walls(nb, prec):
     import torch
