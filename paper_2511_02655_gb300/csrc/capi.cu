@@ -462,7 +462,7 @@ PairLaunch pair_launch(nbody_ctx* c, bool vjp, bool refine = true, bool phi = tr
   return L;
 }
 
-// Slices of float64 partials (bytes_per_body each) the partial-sum buffer holds.
+// Slices of partials (bytes_per_body each) the partial-sum buffer holds.
 int32_t part_slices(const nbody_ctx* c, size_t bytes_per_body) {
   if (c->n_total <= 0) return 0;
   return (int32_t)std::min<size_t>(INT32_MAX, c->part.bytes / ((size_t)c->n_total * bytes_per_body));

@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(kPostThreads) k_adj_update(const AdjLaunch A) 
   if (!chunk_ok(c, A.n_total, A.n_sys, A.part_slices, A.status)) c.begin = c.end = 0;  // NBODY_DEBUG builds only
   const double4_32a* part = reinterpret_cast<const double4_32a*>(A.part);
   const double* cen = A.centre + 3 * c.sys;
-  const int kw = A.g_params ? 3 : 2;  // double4 per body and slice
+  const int kw = A.g_params ? 3 : 2;  // partials (fpair4 / double4_32a) per body and slice
   double pv[2] = {0.0, 0.0};          // this thread's w.da/dG and sum m (d.w) / s^5
   bool bad = false;
   for (int i = c.begin + (int)threadIdx.x; i < c.end; i += kPostThreads) {

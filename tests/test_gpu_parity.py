@@ -353,7 +353,7 @@ def test_virial_lennard_jones_matches_oracle(nb, prec, tol):
 @pytest.mark.parametrize("prec", [0, 1])
 def test_ring_schedule_passes_agree(nb, prec):
     """The paper's ring exchange (Sec. V-B, Fig. 1) as a blocked schedule on one GPU: P j-slices
-    play the P ranks' blocks, each an (i-tile, j-block) pass with its own float64 partial folded
+    play the P ranks' blocks, each an (i-tile, j-block) pass with its own partial folded
     in a fixed order. Every P gives the oracle's forces; FP64 results agree across P to rounding."""
     n = 4096
     x, v, m = inputs.plummer(n, seed=23)
