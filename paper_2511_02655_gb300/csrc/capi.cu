@@ -568,6 +568,15 @@ nbody_status enqueue_step(nbody_ctx* c, double* x, double* v, const double* m, d
   if (n_steps == 0) return NBODY_OK;
   if ((s = run_post(c, post_launch(c, kDrift | kStage, x, v, m, a, nullptr), st))) return s;
   const int every = c->cfg.energy_every;
+  // With up to four systems a step's energy record, except the call's last, is
+  // finished by one extra CTA of the next step's k_post (same fixed-order sum)
+  // instead of by the last CTA of its own: the ticket and the serial per-system
+  // sum leave the step's critical path. The chunk partials alternate between two
+  // sets so that the pending set survives the next step's own record.
+  const bool defer = c->n_sys <= 4;
+  const size_t eset = std::max<size_t>(1, c->chunks.size()) * kEnergyVals;
+  const double* pend_part = nullptr;
+  double* pend_out = nullptr;
   int rec = 0;
   for (int k = 0; k < n_steps; ++k) {
     const bool rec_now = elog && every > 0 && (k + 1) % every == 0;
@@ -576,7 +585,17 @@ nbody_status enqueue_step(nbody_ctx* c, double* x, double* v, const double* m, d
     if (rec_now) mode |= kEnergy;
     if (k + 1 < n_steps) mode |= kDrift | kStage;
     PostLaunch P = post_launch(c, mode, x, v, m, a, nullptr);
-    if (rec_now) P.eout = elog + (int64_t)rec++ * c->n_sys * 9;
+    P.eprev = pend_part, P.eprev_out = pend_out;
+    pend_part = nullptr, pend_out = nullptr;
+    if (rec_now) {
+      double* out = elog + (int64_t)rec * c->n_sys * 9;
+      P.epart = static_cast<double*>(c->epart.p) + (size_t)(rec % 2) * eset;
+      ++rec;
+      if (defer && k + 1 < n_steps)
+        pend_part = P.epart, pend_out = out;  // the next k_post finishes it
+      else
+        P.eout = out;
+    }
     if ((s = run_post(c, P, st))) return s;
   }
   return NBODY_OK;
@@ -1268,7 +1287,8 @@ nbody_status nbody_init(nbody_ctx** out, const nbody_config* cfg, int64_t n_syst
   if ((s = ensure(c, c->stage, stage_bytes))) return bail(s);
   if (cfg->precision == NBODY_MIXED && (s = ensure(c, c->stage_lo, n * sizeof(float4)))) return bail(s);
   if ((s = ensure(c, c->centre, (size_t)c->n_sys * 3 * sizeof(double)))) return bail(s);
-  if ((s = ensure(c, c->epart, std::max<size_t>(1, c->chunks.size()) * kEnergyVals * sizeof(double)))) return bail(s);
+  // two sets of chunk partials: a step's energy record may be finished by the next step's k_post
+  if ((s = ensure(c, c->epart, 2 * std::max<size_t>(1, c->chunks.size()) * kEnergyVals * sizeof(double)))) return bail(s);
   // [0..1] work counter, [2] status word, [4] energy ticket, [5] centre ticket, [6] adjoint-parameter ticket
   if ((s = ensure(c, c->status_counter, 8 * sizeof(unsigned)))) return bail(s);
   c->counter = static_cast<unsigned*>(c->status_counter.p);

@@ -197,7 +197,9 @@ struct PostLaunch {
   const double* centre;    // [n_sys][3] staging origin (mixed)
   double* epart;           // [n_chunks][kEnergyVals]
   unsigned* status;        // device status word
-  double* eout;            // kEnergy: nullable [n_sys][9] record formed by the last CTA
+  double* eout;            // kEnergy: nullable [n_sys][9] record formed by the last CTA (null: partials only)
+  const double* eprev;     // nullable: chunk partials [n_chunks][kEnergyVals] of the previous step's record,
+  double* eprev_out;       //   finished into eprev_out [n_sys][9] by one extra CTA (blockIdx.x == n_chunks)
   double* vout;            // kVirial: [n_sys][3] record {K, W, -2K/W} formed by the last CTA
   const int32_t* sys_chunk;  // [n_sys + 1] chunk range of each system
   int n_sys;

@@ -17,6 +17,14 @@ namespace {
 __global__ void __launch_bounds__(kPostThreads) k_post(const PostLaunch P) {
   pdl_wait();     // the force kernel before it has finished writing the partials
   pdl_trigger();  // the next force kernel may be scheduled once every CTA has started
+  if ((int)blockIdx.x == P.n_chunks) {
+    // the extra CTA: the previous step's energy record from its chunk partials
+    systems_final<kEnergyVals, kPostThreads>(P.sys_chunk, P.n_sys, P.eprev, P.n_chunks, P.status,
+                                             [&](int sy, const double (&v)[kEnergyVals]) {
+                                               emit_energy(P.eprev_out, sy, v);
+                                             });
+    return;
+  }
   Chunk c = P.chunks[blockIdx.x];
   if (!chunk_ok(c, P.n_total, P.n_sys, (P.mode & kCombine) ? P.part_slices : 0, P.status))
     c.begin = c.end = 0;  // NBODY_DEBUG builds only: processed as an empty chunk
@@ -60,9 +68,9 @@ __global__ void __launch_bounds__(kPostThreads) k_post(const PostLaunch P) {
     block_sum<2, kPostThreads>(kw);
     if (threadIdx.x == 0) P.epart[(int64_t)blockIdx.x * kEnergyVals + 0] = kw[0],
                           P.epart[(int64_t)blockIdx.x * kEnergyVals + 1] = kw[1];
-    if (last_of(P.done, gridDim.x)) {
+    if (last_of(P.done, (unsigned)P.n_chunks)) {
       __threadfence();
-      systems_final<2, kPostThreads>(P.sys_chunk, P.n_sys, P.epart, gridDim.x, P.status,
+      systems_final<2, kPostThreads>(P.sys_chunk, P.n_sys, P.epart, P.n_chunks, P.status,
                                      [&](int sy, const double (&v)[2]) {
                                        double* o = P.vout + 3 * (int64_t)sy;
                                        o[0] = v[0];
@@ -78,10 +86,11 @@ __global__ void __launch_bounds__(kPostThreads) k_post(const PostLaunch P) {
 #pragma unroll
       for (int k = 0; k < kEnergyVals; ++k) P.epart[(int64_t)blockIdx.x * kEnergyVals + k] = e[k];
     }
-    // the last CTA to finish forms the per-system records (no separate launch)
-    if (P.eout && last_of(P.done, gridDim.x)) {
+    // the last chunk CTA to finish forms the per-system records (no separate launch); with
+    // eout null the partials wait for the next step's k_post
+    if (P.eout && last_of(P.done, (unsigned)P.n_chunks)) {
       __threadfence();
-      systems_final<kEnergyVals, kPostThreads>(P.sys_chunk, P.n_sys, P.epart, gridDim.x, P.status,
+      systems_final<kEnergyVals, kPostThreads>(P.sys_chunk, P.n_sys, P.epart, P.n_chunks, P.status,
                                                [&](int sy, const double (&v)[kEnergyVals]) {
                                                  emit_energy(P.eout, sy, v);
                                                });
@@ -259,7 +268,7 @@ cudaError_t launch_copy4(const Copy4& C, int n_sms, cudaStream_t st) {
 
 cudaError_t launch_post(const PostLaunch& P, cudaStream_t st) {
   if (P.n_chunks <= 0) return cudaSuccess;
-  return launch_pdl(k_post, (unsigned)P.n_chunks, kPostThreads, st, P);
+  return launch_pdl(k_post, (unsigned)P.n_chunks + (P.eprev_out ? 1u : 0u), kPostThreads, st, P);
 }
 
 cudaError_t launch_centre(const Chunk* chunks, int n_chunks, const int32_t* sys_chunk, const int64_t* off, int n_sys,
